@@ -13,8 +13,8 @@ c0 + c1*sk = delta*m + e (mod Q) and
 
 Q = prod q_i is odd and t = 2^37 is a power of two, so t*x/Q is never a
 half-integer for x != 0: rounding has no ties.  CRT and rounding use exact
-Python integers; the products c1*sk and a*sk use the oracle's sparse
-schoolbook (sk has small integer coefficients).
+Python integers; the products c1*sk and a*sk use the oracle's ternary
+schoolbook (sk has coefficients in {-1, 0, 1}).
 
 Parity: pinned by decrypt(encrypt(m)) == m, by the additive and
 plaintext-multiplicative homomorphisms against plain integer arithmetic, and
@@ -54,13 +54,13 @@ def encrypt(params: Params, sk, m, a, e):
     """m: [N] ints in [0, t); a: [L][N] uniform residues; e: [N] small ints.
     Returns ct [2][L][N] uint64 = (c0, c1) with c0 = -a*sk + delta*m + e, c1 = a."""
     N, L = params.N, len(params.moduli)
-    sparse_sk = core.sparse_of(sk)
+    tern_sk = core.ternary_of(sk)
     m_obj = np.asarray(m, dtype=np.int64).astype(object)
     e = np.asarray(e, dtype=np.int64)
     ct = np.zeros((2, L, N), dtype=np.uint64)
     for li, q in enumerate(params.moduli):
         a_l = np.ascontiguousarray(a[li], dtype=np.uint64)
-        as_ = core.negacyclic_sparse(a_l, sparse_sk, N, q).astype(object)
+        as_ = core.negacyclic_ternary(a_l, tern_sk, N, q).astype(object)
         d = params.delta % q
         c0 = (-as_ + d * m_obj + e.astype(object)) % q
         ct[0, li] = c0.astype(np.uint64)
@@ -89,10 +89,10 @@ def crt(residues, moduli):
 
 def phase_at(params: Params, sk, ct, ks):
     """[c0 + c1*sk]_Q at coefficient indices ks, as Python ints in [0, Q)."""
-    sparse_sk = core.sparse_of(sk)
+    tern_sk = core.ternary_of(sk)
     res = []
     for li, q in enumerate(params.moduli):
-        c1s = core.negacyclic_sparse(ct[1, li], sparse_sk, params.N, q, ks)
+        c1s = core.negacyclic_ternary(ct[1, li], tern_sk, params.N, q, ks)
         c0 = np.asarray(ct[0, li])[np.asarray(ks, dtype=np.int64)]
         res.append((c0.astype(object) + c1s.astype(object)) % q)
     return crt(res, params.moduli)

@@ -232,26 +232,31 @@ def conv2d_mod_t(x, K, pad, t):
 
 # ---- ct x pt convolution by schoolbook products ------------------------------
 
-def conv_ct_pt(ct_in, Kpoly, p: Partition, moduli, ks=None):
+def conv_ct_pt(ct_in, Kpoly, p: Partition, moduli, ks=None, outputs=None):
     """out[o=(m,b)][comp][limb] = sum_g ct_in[g*B+b][comp][limb] * Kpoly[m*G+g]  in R_q.
 
-    ct_in : [I][2][L][N] uint64 residues; Kpoly: [P][N] small signed ints.
-    ks    : coefficient indices to compute (all N if None).
+    ct_in  : [I][2][L][N] uint64 residues; Kpoly: [P][N] small signed ints.
+    ks     : coefficient indices to compute (all N if None).
+    outputs: output ciphertext indices o to compute (all O if None); the
+             result then has len(outputs) rows in that order.
     Uses the sparse-aware schoolbook product (same definition, visits only the
     nonzero weight coefficients).  Returns [O][2][L][len(ks) or N] uint64."""
     L = len(moduli)
     nk = p.N if ks is None else len(ks)
-    out = np.zeros((p.O, 2, L, nk), dtype=np.uint64)
-    sparse = [core.sparse_of(Kpoly[i]) for i in range(p.P)]
-    for m in range(p.M):
-        for b in range(p.B):
-            o = m * p.B + b
-            for comp in range(2):
-                for li, q in enumerate(moduli):
-                    acc = np.zeros(nk, dtype=object)
-                    for g in range(p.G):
-                        prod = core.negacyclic_sparse(ct_in[g * p.B + b, comp, li], sparse[m * p.G + g],
-                                                      p.N, q, ks)
-                        acc += prod.astype(object)
-                    out[o, comp, li] = np.mod(acc, q).astype(np.uint64)
+    outs = list(range(p.O)) if outputs is None else [int(o) for o in outputs]
+    out = np.zeros((len(outs), 2, L, nk), dtype=np.uint64)
+    sparse = {}
+    for row, o in enumerate(outs):
+        m, b = divmod(o, p.B)
+        for g in range(p.G):
+            if m * p.G + g not in sparse:
+                sparse[m * p.G + g] = core.sparse_of(Kpoly[m * p.G + g])
+        for comp in range(2):
+            for li, q in enumerate(moduli):
+                acc = np.zeros(nk, dtype=object)
+                for g in range(p.G):
+                    prod = core.negacyclic_sparse(ct_in[g * p.B + b, comp, li], sparse[m * p.G + g],
+                                                  p.N, q, ks)
+                    acc += prod.astype(object)
+                out[row, comp, li] = np.mod(acc, q).astype(np.uint64)
     return out

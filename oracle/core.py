@@ -42,6 +42,8 @@ def lib():
         L.or_negacyclic_batch.argtypes = [p64, p64, sz, u32, p64, u32, p64]
         L.or_negacyclic_sparse_at.restype = None
         L.or_negacyclic_sparse_at.argtypes = [p64, p32, pi64, sz, u32, u64, p32, sz, p64]
+        L.or_negacyclic_ternary_at.restype = None
+        L.or_negacyclic_ternary_at.argtypes = [p64, p32, sz, p32, sz, u32, u64, p32, sz, p64]
         _lib = L
     return _lib
 
@@ -173,4 +175,23 @@ def lift_small(b_small, q):
     out = np.where(b >= 0, b, 0).astype(np.uint64)
     neg = b < 0
     out[neg] = np.uint64(q) - (-b[neg]).astype(np.uint64)
+    return out
+
+
+def ternary_of(b_ternary):
+    """(+1 index list, -1 index list) of a polynomial with coefficients in {-1, 0, 1}."""
+    b = np.asarray(b_ternary, dtype=np.int64)
+    assert np.all(np.abs(b) <= 1)
+    return (np.nonzero(b == 1)[0].astype(np.uint32), np.nonzero(b == -1)[0].astype(np.uint32))
+
+
+def negacyclic_ternary(a, tern, N, q, ks=None):
+    """a * b mod (X^N+1, q) for ternary b given as ternary_of(b); additions only."""
+    a = _u64(a)
+    assert a.size == 0 or int(a.max()) < q, "ternary product needs canonical residues"
+    pos, neg = (np.ascontiguousarray(x, dtype=np.uint32) for x in tern)
+    k, nk = _idx(ks)
+    out = np.zeros(nk if k is not None else N, dtype=np.uint64)
+    lib().or_negacyclic_ternary_at(_p64(a), _p32(pos), pos.size, _p32(neg), neg.size, N, q,
+                                   _p32(k) if k is not None else None, nk, _p64(out))
     return out

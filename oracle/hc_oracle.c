@@ -272,3 +272,28 @@ void or_negacyclic_sparse_at(const uint64_t *a, const uint32_t *idx, const int64
         out[ii] = acc;
     }
 }
+
+/* The same schoolbook sum when b is ternary (coefficients in {-1, 0, 1}),
+ * given as the index lists of its +1 and -1 coefficients: every term is
+ * +-a[.], so the sum needs additions only.  a must hold canonical residues
+ * (< q).  Coefficients listed in ks (all N when ks == NULL). */
+void or_negacyclic_ternary_at(const uint64_t *a, const uint32_t *pos, size_t npos,
+                              const uint32_t *neg, size_t nneg, uint32_t N, uint64_t q,
+                              const uint32_t *ks, size_t nk, uint64_t *out)
+{
+    size_t cnt = ks ? nk : N;
+    #pragma omp parallel for schedule(static)
+    for (size_t ii = 0; ii < cnt; ++ii) {
+        uint32_t k = ks ? ks[ii] : (uint32_t)ii;
+        u128 plus = 0, minus = 0;
+        for (size_t t = 0; t < npos; ++t) {
+            uint32_t j = pos[t];
+            if (j <= k) plus += a[k - j]; else minus += a[k + N - j];
+        }
+        for (size_t t = 0; t < nneg; ++t) {
+            uint32_t j = neg[t];
+            if (j <= k) minus += a[k - j]; else plus += a[k + N - j];
+        }
+        out[ii] = or_submod((uint64_t)(plus % q), (uint64_t)(minus % q), q);
+    }
+}

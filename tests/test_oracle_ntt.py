@@ -186,3 +186,15 @@ def test_sparse_and_batch_agree_with_dense():
     batch = core.negacyclic_batch(a[None], b[None], moduli)[0]
     for li, q in enumerate(moduli):
         assert np.array_equal(batch[li], core.negacyclic(a[li], b[li], q))
+
+
+def test_ternary_agrees_with_dense():
+    N = 256
+    s = Stream(12, 0)
+    for q in CANONICAL_PRIMES[:2]:
+        a = s.below(q, N)
+        t = s.ternary(N)
+        dense = core.negacyclic(a, core.lift_small(t, q), q)
+        assert np.array_equal(core.negacyclic_ternary(a, core.ternary_of(t), N, q), dense)
+        ks = [0, 3, 255]
+        assert np.array_equal(core.negacyclic_ternary(a, core.ternary_of(t), N, q, ks), dense[ks])
