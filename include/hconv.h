@@ -1,0 +1,241 @@
+/*
+ * hconv.h -- C ABI of the GB300 (sm_103a) library for the homomorphic
+ * convolution hot path of SecONNds (arXiv 2506.11586): RLWE ciphertext x
+ * plaintext polynomial products computed as forward NTT -> NTT-domain
+ * multiply-accumulate -> inverse NTT over RNS limbs (Sec. 6.2, App. C.1).
+ *
+ * Conventions shared by every call
+ *   - Status: every call returns hc_status (HC_OK == 0); none aborts, throws
+ *     or exits.  hc_last_error() returns a thread-local detail string for the
+ *     most recent failing call on the calling thread.
+ *   - Pointers prefixed d_ are device memory, h_ are host memory.  Buffers
+ *     passed in are owned by the caller; handles (hc_ctx, hc_weights,
+ *     hc_plan) are owned by the library and released only by hc_free().
+ *   - Layout: little-endian uint64 residues, [item][component][limb][coeff];
+ *     a ciphertext is [2][L][N] (components c0, c1), a plaintext [L][N].
+ *     Coefficient-domain arrays are in natural order.  NTT-domain arrays hold
+ *     slot k = a(psi_i^(2*rev(k)+1)) mod q_i, where rev reverses log2(N) bits
+ *     and psi_i is the smallest primitive 2N-th root of unity mod q_i.
+ *   - Ranges: inputs must be canonical residues in [0, q_i); outputs are
+ *     canonical.  Inputs are not range-checked unless the context was created
+ *     with HC_CTX_CHECKED, in which case an out-of-range input makes the call
+ *     return HC_ERR_RANGE (the call then also synchronises the stream).
+ *   - Asynchrony: compute calls are enqueued on the given cudaStream_t
+ *     (passed as void*, NULL = legacy default stream) and return before the
+ *     GPU finishes; launch errors are reported by the call, execution errors
+ *     by a later call or by stream synchronisation.
+ *   - Supported parameters: N in {4096, 8192, 16384}; 1 <= L <= 8 distinct
+ *     primes q_i < 2^50 with q_i = 1 (mod 2N).
+ *   - A context is immutable after creation and may be used from several
+ *     streams and host threads at once; weights likewise.  A plan is not
+ *     thread-safe: run one plan on one stream at a time.
+ */
+#ifndef HCONV_H
+#define HCONV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hc_ctx hc_ctx;
+typedef struct hc_weights hc_weights;
+typedef struct hc_plan hc_plan;
+
+typedef enum {
+    HC_OK = 0,
+    HC_ERR_INVALID_ARG = 1,  /* null pointer, zero/oversized count, bad shape */
+    HC_ERR_BAD_MODULUS = 2,  /* not prime, >= 2^50, != 1 mod 2N, duplicate */
+    HC_ERR_RANGE = 3,        /* checked mode: an input residue >= q_i */
+    HC_ERR_OOM = 4,          /* device or host allocation failed */
+    HC_ERR_BUDGET = 5,       /* admission: request exceeds the memory budget */
+    HC_ERR_TIMEOUT = 6,      /* a bounded device-side wait expired */
+    HC_ERR_CUDA = 7,         /* a CUDA runtime call failed (see hc_last_error) */
+    HC_ERR_UNSUPPORTED = 8   /* valid but not supported here (e.g. stride != 1) */
+} hc_status;
+
+/* Context flags. */
+#define HC_CTX_CHECKED 1u    /* range-check every input residue (debug mode) */
+
+/* ---------------------------------------------------------------- context --
+ * The RLWE ring R_Q = Z_Q[X]/(X^N+1) with Q = prod q_i in RNS form
+ * (Sec. 2.1, App. C), plus the plaintext modulus t (informational; the
+ * server-side hot path never reduces mod t).
+ *
+ * hc_ctx_create: validates (N, moduli[0..L), t) on the host, then builds and
+ * uploads per-limb twiddle tables (psi^rev(k), psi^-rev(k) with Shoup
+ * companions) and constants.  moduli is a host array, copied.  *out receives
+ * a new handle; on failure *out is set to NULL.
+ * Errors: HC_ERR_INVALID_ARG (null out/moduli, N unsupported, L == 0 or > 8,
+ * t < 2), HC_ERR_BAD_MODULUS, HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_ctx_create(uint32_t N, const uint64_t *moduli, uint32_t L, uint64_t t,
+                        hc_ctx **out);
+hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint64_t t,
+                           uint32_t flags, hc_ctx **out);
+
+/* Host-only validation of hc_ctx_create's arguments; touches no GPU. */
+hc_status hc_ctx_validate(uint32_t N, const uint64_t *moduli, uint32_t L, uint64_t t);
+
+/* Ring parameters of a context.  Any output pointer may be NULL; moduli_out
+ * and psi_out (host arrays of L entries) receive q_i and the psi_i used. */
+hc_status hc_ctx_info(const hc_ctx *ctx, uint32_t *N, uint32_t *L, uint64_t *t,
+                      uint64_t *moduli_out, uint64_t *psi_out);
+
+/* -------------------------------------------------------------- transforms --
+ * Negacyclic NTT over each RNS limb (App. C.1): the point-value form in which
+ * the ring product becomes the slot-wise product (App. C.1).
+ *
+ * hc_ntt_fwd: in place on d_polys, n_polys polynomials of layout [n][L][N];
+ * coefficient domain (natural order) in, NTT domain (order above) out.
+ * hc_ntt_inv: the exact inverse, N^-1 folded in.
+ * n_polys == 0 is a no-op.  Errors: HC_ERR_INVALID_ARG (null ctx, null
+ * d_polys with n_polys > 0), HC_ERR_RANGE (checked mode), HC_ERR_CUDA. */
+hc_status hc_ntt_fwd(const hc_ctx *ctx, uint64_t *d_polys, size_t n_polys, void *cuda_stream);
+hc_status hc_ntt_inv(const hc_ctx *ctx, uint64_t *d_polys, size_t n_polys, void *cuda_stream);
+
+/* ------------------------------------------------------------ convolution --
+ * Cheetah-style coefficient-encoded convolution (Sec. 2.3, Sec. 6.1) with
+ * weights NTT-preprocessed offline (Sec. 6.2, Sec. 7).  The paper prints no
+ * packing; the library's packing of a stride-1 convolution with zero padding
+ * `pad` is:
+ *   channel groups of Cw, spatial blocks of Hw x Ww over the padded input,
+ *   overlapping by kh-1 rows and kw-1 columns; G = ceil(C/Cw) groups,
+ *   B = Bh*Bw blocks with Bh = ceil(Ho/(Hw-kh+1)), Bw = ceil(Wo/(Ww-kw+1));
+ *   input ct  i = g*B + b : coeff [c*Hw*Ww + i*Ww + j] = x_pad[g*Cw+c][i0+i][j0+j]
+ *   weight pt p = m*G + g : coeff [O - c*Hw*Ww - l*Ww - l'] = K[m][g*Cw+c][l][l']
+ *                           (int8 lifted to w mod q_i), O = (Cw-1)HwWw + (kh-1)Ww + kw-1
+ *   output ct o = m*B + b : coeff [O + i*Ww + j] encrypts y[m][i0+i][j0+j]
+ *   with block b = bh*Bw + bw at padded origin (i0, j0) = (bh(Hw-kh+1), bw(Ww-kw+1)).
+ * Cw = Hw = Ww = 0 in the descriptor selects the canonical partition: the
+ * one minimising 2I + P + 2O polynomials moved (I = G*B inputs, P = M*G
+ * weights, O = M*B outputs), ties to larger Hw*Ww, then larger Cw, then
+ * larger Ww, over Cw <= C, kh <= Hw <= H+2pad, kw <= Ww <= W+2pad,
+ * Cw*Hw*Ww <= N. */
+typedef struct {
+    uint32_t C, H, W;       /* input channels, height, width */
+    uint32_t M;             /* output channels */
+    uint32_t kh, kw;        /* kernel height, width */
+    uint32_t stride, pad;   /* stride must be 1 */
+    uint32_t Cw, Hw, Ww;    /* 0,0,0 = canonical partition */
+} hc_conv_desc;
+
+/* Host-only: resolve the partition of `desc` for ring degree N.  *resolved
+ * gets desc with Cw/Hw/Ww filled in; counts may be NULL.
+ * Errors: HC_ERR_INVALID_ARG (null desc/resolved, zero dims, kernel larger
+ * than the padded input, a given partition with Cw*Hw*Ww > N),
+ * HC_ERR_UNSUPPORTED (stride != 1). */
+hc_status hc_conv_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *resolved,
+                            uint32_t *n_in_ct, uint32_t *n_pt, uint32_t *n_out_ct);
+
+/* Offline weight preprocessing (Sec. 6.2, Sec. 8.1): pack h_K (host int8,
+ * [M][C][kh][kw], copied) into P = M*G plaintext polynomials, lift to every
+ * q_i, forward-NTT and keep them resident on the device in a new handle
+ * (*out).  Enqueued on cuda_stream; the handle is usable by later calls on
+ * any stream once that work completes (the call synchronises the stream
+ * before returning, so it is immediately usable).
+ * Errors: HC_ERR_INVALID_ARG, HC_ERR_UNSUPPORTED, HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K,
+                                hc_weights **out, void *cuda_stream);
+
+/* Geometry of preprocessed weights.  Any output pointer may be NULL. */
+hc_status hc_conv_geometry(const hc_weights *w, uint32_t *n_in_ct, uint32_t *n_out_ct,
+                           uint32_t *Cw, uint32_t *Hw, uint32_t *Ww);
+
+/* Read-only view of the resident NTT-domain weights, [P][L][N] (p = m*G+g).
+ * The pointer stays owned by the handle. */
+hc_status hc_weights_data(const hc_weights *w, const uint64_t **d_pt_ntt, size_t *n_pt);
+
+/* Copy the resident NTT-domain weights ([P][L][N]) into the caller's device
+ * buffer d_dst (P*L*N words), enqueued on cuda_stream.  Lets a server save
+ * preprocessed weights or inspect them.  Errors: HC_ERR_INVALID_ARG,
+ * HC_ERR_CUDA. */
+hc_status hc_weights_export(const hc_weights *w, uint64_t *d_dst, void *cuda_stream);
+
+/* Online server computation of one convolution layer (Sec. 6.2): NTT every
+ * input ciphertext, run all multiply-accumulates in the NTT domain, inverse
+ * NTT only the final sums:
+ *   d_ct_out[m*B+b] = INTT( sum_g NTT(d_ct_in[g*B+b]) . pt_ntt[m*G+g] )
+ * for both components and every limb.  d_ct_in: [I][2][L][N] coefficient
+ * domain (not modified); d_ct_out: [O][2][L][N] coefficient domain, fully
+ * overwritten.  The buffers must not overlap.  Device scratch of
+ * I*2*L*N*8 bytes is taken from the allocator (hc_set_allocator) on the
+ * stream and returned after the work is enqueued.
+ * Errors: HC_ERR_INVALID_ARG (null args, ctx/weights mismatch),
+ * HC_ERR_RANGE (checked mode), HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_conv_ct_pt(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in,
+                        uint64_t *d_ct_out, void *cuda_stream);
+
+/* The same result computed the plain way: one kernel launch per ct x pt
+ * product (forward NTT of the ciphertext, slot-wise product, inverse NTT,
+ * add into the output), no fusion and no batching.  Comparison path. */
+hc_status hc_conv_ct_pt_plain(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in,
+                              uint64_t *d_ct_out, void *cuda_stream);
+
+/* hc_conv_ct_pt on HOST buffers: copies h_ct_in ([I][2][L][N]) to the
+ * device, runs the layer, copies the result to h_ct_out ([O][2][L][N]) and
+ * synchronises the stream before returning.  Pinned host memory gives the
+ * fastest copies; pageable memory works.  Device buffers come from the
+ * allocator.  Errors as hc_conv_ct_pt. */
+hc_status hc_conv_ct_pt_host(const hc_ctx *ctx, const hc_weights *w, const uint64_t *h_ct_in,
+                             uint64_t *h_ct_out, void *cuda_stream);
+
+/* --------------------------------------------------- generic ct x pt MAC --
+ * The NTT-domain multiply-accumulate of Sec. 6.2 for arbitrary products:
+ *   d_out[s] = sum_{j : h_slot[j] == s} INTT( NTT(d_ct[j]) . d_pt_ntt[j] )
+ * for every s < n_out (slots with no product are set to zero).
+ * d_ct: [n][2][L][N] coefficient domain; d_pt_ntt: [n][L][N] NTT domain;
+ * h_slot: host array of n slot indices (< n_out); d_out: [n_out][2][L][N]
+ * coefficient domain, fully overwritten, must not overlap the inputs.
+ * Device scratch of n*2*L*N*8 bytes (only when some slot has more than one
+ * product) plus a small work list come from the allocator.
+ * Errors: HC_ERR_INVALID_ARG (null args, slot >= n_out), HC_ERR_RANGE
+ * (checked mode), HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_ctpt_mac(const hc_ctx *ctx, const uint64_t *d_ct, const uint64_t *d_pt_ntt,
+                      const uint32_t *h_slot, size_t n, uint64_t *d_out, size_t n_out,
+                      void *cuda_stream);
+
+/* ------------------------------------------------------------- allocation --
+ * Device memory used by the library: handles' resident tables and weights,
+ * and per-call scratch.  alloc(bytes, stream, user) must return device memory
+ * usable in stream order on `stream` (NULL on failure); free(ptr, stream,
+ * user) releases it in stream order.  Passing alloc == NULL restores the
+ * default (cudaMallocAsync / cudaFreeAsync on the stream's device pool).
+ * Not thread-safe with respect to concurrent library calls: set it once at
+ * start-up. */
+typedef void *(*hc_alloc_fn)(size_t bytes, void *cuda_stream, void *user);
+typedef void (*hc_free_fn)(void *ptr, void *cuda_stream, void *user);
+void hc_set_allocator(hc_alloc_fn alloc, hc_free_fn free_fn, void *user);
+
+/* ---------------------------------------------------------------- tracing --
+ * Per-kernel device timing.  While enabled, every kernel launch the library
+ * enqueues is bracketed by CUDA events recorded on the launch's own stream.
+ * hc_profile_collect synchronises on the recorded events, then reports for
+ * each kernel name its launch count and summed device time (ms) since the
+ * last collect, and clears the record.  entries: caller array of cap
+ * elements; *n_out receives the number of kernel names (which may exceed
+ * cap; only cap are written).  Not for use inside CUDA-graph capture. */
+typedef struct {
+    char name[48];
+    uint64_t launches;
+    double total_ms;
+} hc_kernel_time;
+void hc_profile_enable(int on);
+hc_status hc_profile_collect(hc_kernel_time *entries, size_t cap, size_t *n_out);
+
+/* Release a handle of any kind (context, weights, plan).  NULL is a no-op.
+ * A handle must not be in use by queued GPU work when it is freed. */
+void hc_free(void *handle);
+
+const char *hc_status_str(hc_status s);
+const char *hc_last_error(void);
+
+/* Library version, for diagnostics. */
+const char *hc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HCONV_H */

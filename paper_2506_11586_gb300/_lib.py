@@ -1,0 +1,302 @@
+"""Thin ctypes binding of libhconv's C ABI (include/hconv.h).
+
+Every function here has the name of the C entry point it wraps and only
+marshals arguments: device buffers are torch CUDA tensors (int64 or uint64,
+contiguous; their bytes are the uint64 residues), host buffers are numpy
+arrays or pinned CPU tensors, streams are torch.cuda.Stream objects (None =
+torch's current stream).  Every step of the computation runs in libhconv's
+kernels; there is no Python or CPU fallback.  A non-OK status raises HcError.
+
+The library must have been built (``paper_2506_11586_gb300.build.build()``);
+if it is missing, loading fails loudly.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+HC_OK = 0
+HC_ERR_INVALID_ARG = 1
+HC_ERR_BAD_MODULUS = 2
+HC_ERR_RANGE = 3
+HC_ERR_OOM = 4
+HC_ERR_BUDGET = 5
+HC_ERR_TIMEOUT = 6
+HC_ERR_CUDA = 7
+HC_ERR_UNSUPPORTED = 8
+HC_CTX_CHECKED = 1
+
+STATUS_NAMES = {0: "HC_OK", 1: "HC_ERR_INVALID_ARG", 2: "HC_ERR_BAD_MODULUS", 3: "HC_ERR_RANGE",
+                4: "HC_ERR_OOM", 5: "HC_ERR_BUDGET", 6: "HC_ERR_TIMEOUT", 7: "HC_ERR_CUDA",
+                8: "HC_ERR_UNSUPPORTED"}
+
+
+class HcError(RuntimeError):
+    def __init__(self, status, detail):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), detail))
+
+
+class hc_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
+class hc_conv_desc(C.Structure):
+    _fields_ = [(n, C.c_uint32) for n in ("C", "H", "W", "M", "kh", "kw", "stride", "pad", "Cw", "Hw", "Ww")]
+
+
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/hconv.h
+_P = C.c_void_p
+_SIGS = {
+    "hc_ctx_create": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64, C.POINTER(_P)]),
+    "hc_ctx_create_ex": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(_P)]),
+    "hc_ctx_validate": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64]),
+    "hc_ctx_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), _P, _P]),
+    "hc_ntt_fwd": (C.c_int, [_P, _P, C.c_size_t, _P]),
+    "hc_ntt_inv": (C.c_int, [_P, _P, C.c_size_t, _P]),
+    "hc_conv_partition": (C.c_int, [C.POINTER(hc_conv_desc), C.c_uint32, C.POINTER(hc_conv_desc),
+                                    C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+    "hc_weights_preprocess": (C.c_int, [_P, C.POINTER(hc_conv_desc), _P, C.POINTER(_P), _P]),
+    "hc_conv_geometry": (C.c_int, [_P] + [C.POINTER(C.c_uint32)] * 5),
+    "hc_weights_data": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_size_t)]),
+    "hc_weights_export": (C.c_int, [_P, _P, _P]),
+    "hc_conv_ct_pt": (C.c_int, [_P, _P, _P, _P, _P]),
+    "hc_conv_ct_pt_plain": (C.c_int, [_P, _P, _P, _P, _P]),
+    "hc_conv_ct_pt_host": (C.c_int, [_P, _P, _P, _P, _P]),
+    "hc_ctpt_mac": (C.c_int, [_P, _P, _P, _P, C.c_size_t, _P, C.c_size_t, _P]),
+    "hc_set_allocator": (None, [_P, _P, _P]),
+    "hc_profile_enable": (None, [C.c_int]),
+    "hc_profile_collect": (C.c_int, [_P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "hc_free": (None, [_P]),
+    "hc_status_str": (C.c_char_p, [C.c_int]),
+    "hc_last_error": (C.c_char_p, []),
+    "hc_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libhconv.so (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("libhconv.so is not built (%s); run paper_2506_11586_gb300.build.build()" % LIB)
+        L = C.CDLL(LIB)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != HC_OK:
+        raise HcError(status, lib().hc_last_error().decode(errors="replace"))
+
+
+def _dptr(t):
+    """Device pointer of a contiguous CUDA tensor of 8-byte integers."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if t.element_size() != 8:
+        raise ValueError("expected 8-byte integer elements (int64/uint64)")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    """Host pointer of a C-contiguous numpy array or CPU tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous array")
+        return C.c_void_p(a.ctypes.data)
+    if a.is_cuda or not a.is_contiguous():
+        raise ValueError("expected a contiguous CPU tensor")
+    return C.c_void_p(a.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class _Handle:
+    """Owns a library handle; hc_free on close()/garbage collection."""
+
+    def __init__(self, ptr, keep=None):
+        self.ptr = ptr
+        self._keep = keep
+
+    def close(self):
+        if self.ptr:
+            lib().hc_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ctx(_Handle):
+    def __init__(self, ptr, N, moduli, t):
+        super().__init__(ptr)
+        self.N, self.moduli, self.t = N, tuple(moduli), t
+        self.L = len(moduli)
+
+
+class Weights(_Handle):
+    def __init__(self, ptr, ctx, resolved, I, O):
+        super().__init__(ptr, keep=ctx)
+        self.ctx, self.desc, self.I, self.O = ctx, resolved, I, O
+
+
+# ---------------------------------------------------------------- context ---
+
+def hc_ctx_validate(N, moduli, t):
+    """Host-only validation; returns the hc_status code (no exception)."""
+    m = np.ascontiguousarray(moduli, dtype=np.uint64)
+    return lib().hc_ctx_validate(N, C.c_void_p(m.ctypes.data), m.size, t)
+
+
+def hc_ctx_create(N, moduli, t, flags=0):
+    m = np.ascontiguousarray(moduli, dtype=np.uint64)
+    out = C.c_void_p()
+    _check(lib().hc_ctx_create_ex(N, C.c_void_p(m.ctypes.data), m.size, t, flags, C.byref(out)))
+    return Ctx(out, N, [int(x) for x in m], t)
+
+
+def hc_ctx_info(ctx):
+    N, L, t = C.c_uint32(), C.c_uint32(), C.c_uint64()
+    q = np.zeros(8, dtype=np.uint64)
+    psi = np.zeros(8, dtype=np.uint64)
+    _check(lib().hc_ctx_info(ctx.ptr, C.byref(N), C.byref(L), C.byref(t), C.c_void_p(q.ctypes.data),
+                             C.c_void_p(psi.ctypes.data)))
+    n = L.value
+    return {"N": N.value, "L": n, "t": t.value, "moduli": [int(x) for x in q[:n]],
+            "psi": [int(x) for x in psi[:n]]}
+
+
+# ------------------------------------------------------------- transforms ---
+
+def _npolys(ctx, t):
+    per = ctx.L * ctx.N
+    if t.numel() % per:
+        raise ValueError("tensor size is not a multiple of L*N")
+    return t.numel() // per
+
+
+def hc_ntt_fwd(ctx, polys, stream=None):
+    _check(lib().hc_ntt_fwd(ctx.ptr, _dptr(polys), _npolys(ctx, polys), _stream(stream)))
+
+
+def hc_ntt_inv(ctx, polys, stream=None):
+    _check(lib().hc_ntt_inv(ctx.ptr, _dptr(polys), _npolys(ctx, polys), _stream(stream)))
+
+
+# ------------------------------------------------------------ convolution ---
+
+def make_desc(C_, H, W, M, kh, kw, pad=0, stride=1, Cw=0, Hw=0, Ww=0):
+    return hc_conv_desc(C_, H, W, M, kh, kw, stride, pad, Cw, Hw, Ww)
+
+
+def hc_conv_partition(desc, N):
+    """Host-only: (resolved desc, n_in_ct, n_pt, n_out_ct)."""
+    res = hc_conv_desc()
+    i, p, o = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    _check(lib().hc_conv_partition(C.byref(desc), N, C.byref(res), C.byref(i), C.byref(p), C.byref(o)))
+    return res, i.value, p.value, o.value
+
+
+def hc_weights_preprocess(ctx, desc, K, stream=None):
+    K = np.ascontiguousarray(K, dtype=np.int8)
+    if K.size != desc.M * desc.C * desc.kh * desc.kw:
+        raise ValueError("K must have M*C*kh*kw entries")
+    out = C.c_void_p()
+    _check(lib().hc_weights_preprocess(ctx.ptr, C.byref(desc), C.c_void_p(K.ctypes.data), C.byref(out),
+                                       _stream(stream)))
+    i, o, cw, hw, ww = (C.c_uint32() for _ in range(5))
+    _check(lib().hc_conv_geometry(out, C.byref(i), C.byref(o), C.byref(cw), C.byref(hw), C.byref(ww)))
+    res = hc_conv_desc(desc.C, desc.H, desc.W, desc.M, desc.kh, desc.kw, desc.stride, desc.pad,
+                       cw.value, hw.value, ww.value)
+    return Weights(out, ctx, res, i.value, o.value)
+
+
+def hc_conv_geometry(w):
+    i, o, cw, hw, ww = (C.c_uint32() for _ in range(5))
+    _check(lib().hc_conv_geometry(w.ptr, C.byref(i), C.byref(o), C.byref(cw), C.byref(hw), C.byref(ww)))
+    return i.value, o.value, cw.value, hw.value, ww.value
+
+
+def hc_weights_data(w):
+    """(device pointer as int, number of plaintext polys) of the resident NTT-domain weights."""
+    p, n = C.c_void_p(), C.c_size_t()
+    _check(lib().hc_weights_data(w.ptr, C.byref(p), C.byref(n)))
+    return p.value, n.value
+
+
+def hc_weights_export(w, dst, stream=None):
+    """Copy the resident NTT-domain weights [P][L][N] into the CUDA tensor dst."""
+    if dst.numel() != w.ctx.L * w.ctx.N * hc_weights_data(w)[1]:
+        raise ValueError("dst must hold P*L*N words")
+    _check(lib().hc_weights_export(w.ptr, _dptr(dst), _stream(stream)))
+
+
+def hc_conv_ct_pt(ctx, w, ct_in, ct_out, stream=None):
+    _check(lib().hc_conv_ct_pt(ctx.ptr, w.ptr, _dptr(ct_in), _dptr(ct_out), _stream(stream)))
+
+
+def hc_conv_ct_pt_plain(ctx, w, ct_in, ct_out, stream=None):
+    _check(lib().hc_conv_ct_pt_plain(ctx.ptr, w.ptr, _dptr(ct_in), _dptr(ct_out), _stream(stream)))
+
+
+def hc_conv_ct_pt_host(ctx, w, h_in, h_out, stream=None):
+    _check(lib().hc_conv_ct_pt_host(ctx.ptr, w.ptr, _hptr(h_in), _hptr(h_out), _stream(stream)))
+
+
+def hc_ctpt_mac(ctx, ct, pt_ntt, slots, out, stream=None):
+    sl = np.ascontiguousarray(slots, dtype=np.uint32)
+    n_out = _npolys(ctx, out) // 2
+    _check(lib().hc_ctpt_mac(ctx.ptr, _dptr(ct), _dptr(pt_ntt), C.c_void_p(sl.ctypes.data), sl.size,
+                             _dptr(out), n_out, _stream(stream)))
+
+
+def hc_profile_enable(on=True):
+    lib().hc_profile_enable(1 if on else 0)
+
+
+def hc_profile_collect():
+    """{kernel name: (launches, total device ms)} since the last collect."""
+    cap = 64
+    arr = (hc_kernel_time * cap)()
+    n = C.c_size_t()
+    _check(lib().hc_profile_collect(C.cast(arr, C.c_void_p), cap, C.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, cap))}
+
+
+def hc_free(handle):
+    if isinstance(handle, _Handle):
+        handle.close()
+    elif handle:
+        lib().hc_free(handle)
+
+
+def hc_status_str(status):
+    return lib().hc_status_str(status).decode()
+
+
+def hc_last_error():
+    return lib().hc_last_error().decode(errors="replace")
+
+
+def hc_version():
+    return lib().hc_version().decode()

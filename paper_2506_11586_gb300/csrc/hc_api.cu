@@ -1,0 +1,577 @@
+// hc_api.cu -- the C ABI of libhconv (include/hconv.h).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hc_internal.h"
+
+namespace hc {
+const char *last_error();
+void set_allocator(hc_alloc_fn a, hc_free_fn f, void *user);
+}  // namespace hc
+
+using namespace hc;
+
+namespace {
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool ctx_ok(const hc_ctx *c) { return c && c->magic == kMagicCtx; }
+inline bool weights_ok(const hc_weights *w) { return w && w->magic == kMagicWeights; }
+
+uint32_t log2_exact(uint32_t n)
+{
+    uint32_t l = 0;
+    while ((1u << l) < n) ++l;
+    return ((1u << l) == n) ? l : 0xffffffffu;
+}
+
+// ---- partition of a stride-1 convolution --------------------------------------
+struct Geom {
+    uint32_t Cw, Hw, Ww, G, Bh, Bw, B, I, P, O;
+    uint64_t cost;
+};
+
+Geom geom_of(const hc_conv_desc &d, uint32_t Cw, uint32_t Hw, uint32_t Ww)
+{
+    Geom g{};
+    g.Cw = Cw;
+    g.Hw = Hw;
+    g.Ww = Ww;
+    const uint32_t Ho = d.H + 2 * d.pad - d.kh + 1, Wo = d.W + 2 * d.pad - d.kw + 1;
+    g.G = (d.C + Cw - 1) / Cw;
+    const uint32_t oh = Hw - d.kh + 1, ow = Ww - d.kw + 1;
+    g.Bh = (Ho + oh - 1) / oh;
+    g.Bw = (Wo + ow - 1) / ow;
+    g.B = g.Bh * g.Bw;
+    g.I = g.G * g.B;
+    g.P = d.M * g.G;
+    g.O = d.M * g.B;
+    g.cost = 2ull * g.I + g.P + 2ull * g.O;
+    return g;
+}
+
+hc_status resolve_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *res, Geom *geo)
+{
+    if (!desc || !res) return set_error(HC_ERR_INVALID_ARG, "null descriptor");
+    const hc_conv_desc d = *desc;
+    if (d.stride != 1) return set_error(HC_ERR_UNSUPPORTED, "only stride 1 is supported (got %u)", d.stride);
+    if (!d.C || !d.H || !d.W || !d.M || !d.kh || !d.kw)
+        return set_error(HC_ERR_INVALID_ARG, "zero dimension in convolution descriptor");
+    const uint32_t Hp = d.H + 2 * d.pad, Wp = d.W + 2 * d.pad;
+    if (d.kh > Hp || d.kw > Wp) return set_error(HC_ERR_INVALID_ARG, "kernel larger than padded input");
+    if ((uint64_t)d.kh * d.kw > N) return set_error(HC_ERR_INVALID_ARG, "kernel does not fit in N");
+    Geom best{};
+    bool have = false;
+    if (d.Cw || d.Hw || d.Ww) {
+        if (!d.Cw || !d.Hw || !d.Ww || d.Cw > d.C || d.Hw < d.kh || d.Ww < d.kw || d.Hw > Hp || d.Ww > Wp ||
+            (uint64_t)d.Cw * d.Hw * d.Ww > N)
+            return set_error(HC_ERR_INVALID_ARG, "invalid explicit partition Cw=%u Hw=%u Ww=%u", d.Cw, d.Hw, d.Ww);
+        best = geom_of(d, d.Cw, d.Hw, d.Ww);
+        have = true;
+    } else {
+        // exhaustive search: minimal 2I + P + 2O, then larger Hw*Ww, larger Cw, larger Ww
+        for (uint32_t Cw = 1; Cw <= d.C && (uint64_t)Cw * d.kh * d.kw <= N; ++Cw) {
+            for (uint32_t Hw = d.kh; Hw <= Hp && (uint64_t)Cw * Hw * d.kw <= N; ++Hw) {
+                const uint32_t wmax = std::min<uint64_t>(Wp, N / ((uint64_t)Cw * Hw));
+                for (uint32_t Ww = d.kw; Ww <= wmax; ++Ww) {
+                    const Geom g = geom_of(d, Cw, Hw, Ww);
+                    bool better;
+                    if (!have) {
+                        better = true;
+                    } else if (g.cost != best.cost) {
+                        better = g.cost < best.cost;
+                    } else if (g.Hw * g.Ww != best.Hw * best.Ww) {
+                        better = g.Hw * g.Ww > best.Hw * best.Ww;
+                    } else if (g.Cw != best.Cw) {
+                        better = g.Cw > best.Cw;
+                    } else {
+                        better = g.Ww > best.Ww;
+                    }
+                    if (better) {
+                        best = g;
+                        have = true;
+                    }
+                }
+            }
+        }
+    }
+    if (!have) return set_error(HC_ERR_INVALID_ARG, "no partition fits N = %u", N);
+    *res = d;
+    res->Cw = best.Cw;
+    res->Hw = best.Hw;
+    res->Ww = best.Ww;
+    if (geo) *geo = best;
+    return HC_OK;
+}
+
+// Pack int8 weights [M][C][kh][kw] into P = M*G polynomials of N int8 coefficients:
+// poly (m, g) coefficient O - c*Hw*Ww - l*Ww - l' = K[m][g*Cw + c][l][l'].
+void pack_weights(const hc_conv_desc &d, const Geom &g, uint32_t N, const int8_t *K, std::vector<int8_t> &out)
+{
+    out.assign((size_t)g.P * N, 0);
+    const uint32_t HW = g.Hw * g.Ww;
+    const uint32_t off = (g.Cw - 1) * HW + (d.kh - 1) * g.Ww + (d.kw - 1);
+    for (uint32_t m = 0; m < d.M; ++m)
+        for (uint32_t gi = 0; gi < g.G; ++gi) {
+            int8_t *poly = out.data() + ((size_t)m * g.G + gi) * N;
+            for (uint32_t c = 0; c < g.Cw; ++c) {
+                const uint32_t ch = gi * g.Cw + c;
+                if (ch >= d.C) break;
+                for (uint32_t l = 0; l < d.kh; ++l)
+                    for (uint32_t l2 = 0; l2 < d.kw; ++l2)
+                        poly[off - c * HW - l * g.Ww - l2] = K[(((size_t)m * d.C + ch) * d.kh + l) * d.kw + l2];
+            }
+        }
+}
+
+hc_status check_inputs(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cudaStream_t s)
+{
+    if (!(ctx->flags & HC_CTX_CHECKED) || n_polys == 0) return HC_OK;
+    HC_CUDA_TRY(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+    hc_status st = launch_range_check(ctx, p, n_polys, ctx->d_flag, s);
+    if (st != HC_OK) return st;
+    int h = 0;
+    HC_CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) return set_error(HC_ERR_RANGE, "input residue out of range [0, q_i)");
+    return HC_OK;
+}
+
+struct ScratchGuard {
+    void *p = nullptr;
+    cudaStream_t s;
+    explicit ScratchGuard(cudaStream_t st) : s(st) {}
+    ~ScratchGuard() { dev_free(p, s); }
+};
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+const char *hc_version(void) { return "hconv 0.1 (sm_103a)"; }
+
+const char *hc_status_str(hc_status s)
+{
+    switch (s) {
+    case HC_OK: return "HC_OK";
+    case HC_ERR_INVALID_ARG: return "HC_ERR_INVALID_ARG";
+    case HC_ERR_BAD_MODULUS: return "HC_ERR_BAD_MODULUS";
+    case HC_ERR_RANGE: return "HC_ERR_RANGE";
+    case HC_ERR_OOM: return "HC_ERR_OOM";
+    case HC_ERR_BUDGET: return "HC_ERR_BUDGET";
+    case HC_ERR_TIMEOUT: return "HC_ERR_TIMEOUT";
+    case HC_ERR_CUDA: return "HC_ERR_CUDA";
+    case HC_ERR_UNSUPPORTED: return "HC_ERR_UNSUPPORTED";
+    }
+    return "HC_ERR_UNKNOWN";
+}
+
+const char *hc_last_error(void) { return hc::last_error(); }
+
+void hc_set_allocator(hc_alloc_fn alloc, hc_free_fn free_fn, void *user) { hc::set_allocator(alloc, free_fn, user); }
+
+hc_status hc_ctx_validate(uint32_t N, const uint64_t *moduli, uint32_t L, uint64_t t)
+{
+    if (!moduli) return set_error(HC_ERR_INVALID_ARG, "moduli is NULL");
+    if (N != 4096 && N != 8192 && N != 16384) return set_error(HC_ERR_INVALID_ARG, "unsupported N = %u", N);
+    if (L == 0 || L > kMaxLimbs) return set_error(HC_ERR_INVALID_ARG, "L = %u outside [1, %u]", L, kMaxLimbs);
+    if (t < 2) return set_error(HC_ERR_INVALID_ARG, "plaintext modulus t < 2");
+    for (uint32_t i = 0; i < L; ++i) {
+        const uint64_t q = moduli[i];
+        if (q >= (1ull << 50)) return set_error(HC_ERR_BAD_MODULUS, "q[%u] = %llu >= 2^50", i, (unsigned long long)q);
+        if (q % (2ull * N) != 1)
+            return set_error(HC_ERR_BAD_MODULUS, "q[%u] = %llu is not 1 mod 2N", i, (unsigned long long)q);
+        if (!is_prime_u64(q)) return set_error(HC_ERR_BAD_MODULUS, "q[%u] = %llu is not prime", i, (unsigned long long)q);
+        for (uint32_t j = 0; j < i; ++j)
+            if (moduli[j] == q) return set_error(HC_ERR_BAD_MODULUS, "q[%u] duplicates q[%u]", i, j);
+    }
+    return HC_OK;
+}
+
+hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint64_t t, uint32_t flags,
+                           hc_ctx **out)
+{
+    if (!out) return set_error(HC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    hc_status st = hc_ctx_validate(N, moduli, L, t);
+    if (st != HC_OK) return st;
+
+    hc_ctx *c = new (std::nothrow) hc_ctx();
+    if (!c) return set_error(HC_ERR_OOM, "host allocation failed");
+    c->magic = kMagicCtx;
+    c->N = N;
+    c->logN = log2_exact(N);
+    c->L = L;
+    c->t = t;
+    c->flags = flags;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return set_error(HC_ERR_CUDA, "no CUDA device");
+    }
+
+    // host tables: per limb, forward and inverse twiddles with Shoup companions
+    std::vector<ulonglong2> tw((size_t)2 * L * N);
+    std::vector<LimbConst> lcs(L);
+    for (uint32_t i = 0; i < L; ++i) {
+        const uint64_t q = moduli[i];
+        const uint64_t psi = min_primitive_2n_root(q, N);
+        if (!psi) {
+            delete c;
+            return set_error(HC_ERR_BAD_MODULUS, "no primitive 2N-th root mod q[%u]", i);
+        }
+        const uint64_t psi_inv = powmod_u64(psi, q - 2, q);
+        c->q[i] = q;
+        c->psi[i] = psi;
+        ulonglong2 *f = tw.data() + (size_t)(2 * i) * N;
+        ulonglong2 *b = tw.data() + (size_t)(2 * i + 1) * N;
+        // powers psi^j and psi^-j in natural order, then scattered to bit-reversed slots
+        uint64_t pf = 1, pb = 1;
+        for (uint32_t j = 0; j < N; ++j) {
+            const uint32_t k = bit_reverse(j, c->logN);
+            f[k].x = pf;
+            f[k].y = shoup_companion(pf, q);
+            b[k].x = pb;
+            b[k].y = shoup_companion(pb, q);
+            pf = mulmod_u64(pf, psi, q);
+            pb = mulmod_u64(pb, psi_inv, q);
+        }
+        LimbConst &lc = lcs[i];
+        memset(&lc, 0, sizeof(lc));
+        lc.q = q;
+        lc.r64 = (uint64_t)(((unsigned __int128)1 << 64) % q);
+        lc.r64_s = shoup_companion(lc.r64, q);
+        lc.one_s = shoup_companion(1, q);
+        lc.ninv = powmod_u64(N, q - 2, q);
+        lc.ninv_s = shoup_companion(lc.ninv, q);
+        lc.ninvw = mulmod_u64(lc.ninv, b[1].x, q);
+        lc.ninvw_s = shoup_companion(lc.ninvw, q);
+    }
+
+    c->table_bytes = tw.size() * sizeof(ulonglong2);
+    c->d_tables = dev_alloc_persistent(c->table_bytes);
+    c->d_limbs = (LimbConst *)dev_alloc_persistent(sizeof(LimbConst) * L);
+    c->d_flag = (int *)dev_alloc_persistent(sizeof(int) * 4);
+    if (!c->d_tables || !c->d_limbs || !c->d_flag) {
+        dev_free_persistent(c->d_tables);
+        dev_free_persistent(c->d_limbs);
+        dev_free_persistent(c->d_flag);
+        delete c;
+        return set_error(HC_ERR_OOM, "device allocation of context tables failed");
+    }
+    for (uint32_t i = 0; i < L; ++i) {
+        lcs[i].tw_f = (const ulonglong2 *)c->d_tables + (size_t)(2 * i) * N;
+        lcs[i].tw_i = (const ulonglong2 *)c->d_tables + (size_t)(2 * i + 1) * N;
+    }
+    cudaError_t e = cudaMemcpy(c->d_tables, tw.data(), c->table_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_limbs, lcs.data(), sizeof(LimbConst) * L, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, sizeof(int) * 4);
+    if (e != cudaSuccess) {
+        hc_status s2 = cuda_error(e, "uploading context tables");
+        dev_free_persistent(c->d_tables);
+        dev_free_persistent(c->d_limbs);
+        dev_free_persistent(c->d_flag);
+        delete c;
+        return s2;
+    }
+    *out = c;
+    return HC_OK;
+}
+
+hc_status hc_ctx_create(uint32_t N, const uint64_t *moduli, uint32_t L, uint64_t t, hc_ctx **out)
+{
+    return hc_ctx_create_ex(N, moduli, L, t, 0, out);
+}
+
+hc_status hc_ctx_info(const hc_ctx *ctx, uint32_t *N, uint32_t *L, uint64_t *t, uint64_t *moduli_out,
+                      uint64_t *psi_out)
+{
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (N) *N = ctx->N;
+    if (L) *L = ctx->L;
+    if (t) *t = ctx->t;
+    for (uint32_t i = 0; i < ctx->L; ++i) {
+        if (moduli_out) moduli_out[i] = ctx->q[i];
+        if (psi_out) psi_out[i] = ctx->psi[i];
+    }
+    return HC_OK;
+}
+
+hc_status hc_ntt_fwd(const hc_ctx *ctx, uint64_t *d_polys, size_t n_polys, void *cuda_stream)
+{
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (n_polys == 0) return HC_OK;
+    if (!d_polys) return set_error(HC_ERR_INVALID_ARG, "d_polys is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    hc_status st = check_inputs(ctx, d_polys, n_polys, s);
+    if (st != HC_OK) return st;
+    return launch_ntt_fwd(ctx, d_polys, d_polys, n_polys, s);
+}
+
+hc_status hc_ntt_inv(const hc_ctx *ctx, uint64_t *d_polys, size_t n_polys, void *cuda_stream)
+{
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (n_polys == 0) return HC_OK;
+    if (!d_polys) return set_error(HC_ERR_INVALID_ARG, "d_polys is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    hc_status st = check_inputs(ctx, d_polys, n_polys, s);
+    if (st != HC_OK) return st;
+    return launch_ntt_inv(ctx, d_polys, d_polys, n_polys, s);
+}
+
+hc_status hc_conv_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *resolved, uint32_t *n_in_ct,
+                            uint32_t *n_pt, uint32_t *n_out_ct)
+{
+    Geom g{};
+    hc_status st = resolve_partition(desc, N, resolved, &g);
+    if (st != HC_OK) return st;
+    if (n_in_ct) *n_in_ct = g.I;
+    if (n_pt) *n_pt = g.P;
+    if (n_out_ct) *n_out_ct = g.O;
+    return HC_OK;
+}
+
+hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K, hc_weights **out,
+                                void *cuda_stream)
+{
+    if (!out) return set_error(HC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (!h_K) return set_error(HC_ERR_INVALID_ARG, "h_K is NULL");
+    hc_conv_desc res{};
+    Geom g{};
+    hc_status st = resolve_partition(desc, ctx->N, &res, &g);
+    if (st != HC_OK) return st;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    const uint32_t N = ctx->N, L = ctx->L;
+
+    std::vector<int8_t> packed;
+    pack_weights(res, g, N, h_K, packed);
+    // CSR of output terms: output o = m*B + b sums g < G of (ct g*B + b, pt m*G + g)
+    std::vector<uint32_t> term_ptr((size_t)g.O + 1), terms((size_t)2 * g.O * g.G);
+    for (uint32_t m = 0; m < res.M; ++m)
+        for (uint32_t b = 0; b < g.B; ++b) {
+            const uint32_t o = m * g.B + b;
+            term_ptr[o] = o * g.G;
+            for (uint32_t gi = 0; gi < g.G; ++gi) {
+                terms[2 * ((size_t)o * g.G + gi)] = gi * g.B + b;
+                terms[2 * ((size_t)o * g.G + gi) + 1] = m * g.G + gi;
+            }
+        }
+    term_ptr[g.O] = g.O * g.G;
+
+    hc_weights *w = new (std::nothrow) hc_weights();
+    if (!w) return set_error(HC_ERR_OOM, "host allocation failed");
+    w->magic = kMagicWeights;
+    w->ctx = ctx;
+    w->device = ctx->device;
+    w->desc = res;
+    w->G = g.G;
+    w->B = g.B;
+    w->I = g.I;
+    w->P = g.P;
+    w->O = g.O;
+    w->d_pt = (uint64_t *)dev_alloc_persistent((size_t)g.P * L * N * sizeof(uint64_t));
+    w->d_term_ptr = (uint32_t *)dev_alloc_persistent(term_ptr.size() * sizeof(uint32_t));
+    w->d_terms = (uint32_t *)dev_alloc_persistent(terms.size() * sizeof(uint32_t));
+    int8_t *d_packed = (int8_t *)dev_alloc(packed.size(), s);
+    auto fail = [&](hc_status e) {
+        dev_free(d_packed, s);
+        cudaStreamSynchronize(s);
+        hc_free(w);
+        return e;
+    };
+    if (!w->d_pt || !w->d_term_ptr || !w->d_terms || !d_packed)
+        return fail(set_error(HC_ERR_OOM, "device allocation of weights failed"));
+    cudaError_t e = cudaMemcpyAsync(d_packed, packed.data(), packed.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->d_term_ptr, term_ptr.data(), term_ptr.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_terms, terms.data(), terms.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(cuda_error(e, "uploading weights"));
+    st = launch_lift_int8(ctx, d_packed, w->d_pt, g.P, s);
+    if (st == HC_OK) st = launch_ntt_fwd(ctx, w->d_pt, w->d_pt, g.P, s);
+    if (st != HC_OK) return fail(st);
+    dev_free(d_packed, s);
+    d_packed = nullptr;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_error(e, "weights preprocessing"));
+    *out = w;
+    return HC_OK;
+}
+
+hc_status hc_conv_geometry(const hc_weights *w, uint32_t *n_in_ct, uint32_t *n_out_ct, uint32_t *Cw, uint32_t *Hw,
+                           uint32_t *Ww)
+{
+    if (!weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid weights handle");
+    if (n_in_ct) *n_in_ct = w->I;
+    if (n_out_ct) *n_out_ct = w->O;
+    if (Cw) *Cw = w->desc.Cw;
+    if (Hw) *Hw = w->desc.Hw;
+    if (Ww) *Ww = w->desc.Ww;
+    return HC_OK;
+}
+
+hc_status hc_weights_data(const hc_weights *w, const uint64_t **d_pt_ntt, size_t *n_pt)
+{
+    if (!weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid weights handle");
+    if (d_pt_ntt) *d_pt_ntt = w->d_pt;
+    if (n_pt) *n_pt = w->P;
+    return HC_OK;
+}
+
+hc_status hc_weights_export(const hc_weights *w, uint64_t *d_dst, void *cuda_stream)
+{
+    if (!weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid weights handle");
+    if (!d_dst) return set_error(HC_ERR_INVALID_ARG, "d_dst is NULL");
+    DeviceGuard g(w->device);
+    const size_t bytes = (size_t)w->P * w->ctx->L * w->ctx->N * sizeof(uint64_t);
+    HC_CUDA_TRY(cudaMemcpyAsync(d_dst, w->d_pt, bytes, cudaMemcpyDeviceToDevice, as_stream(cuda_stream)));
+    return HC_OK;
+}
+
+hc_status hc_conv_ct_pt(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in, uint64_t *d_ct_out,
+                        void *cuda_stream)
+{
+    if (!ctx_ok(ctx) || !weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid context or weights");
+    if (w->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "weights were preprocessed for another context");
+    if (!d_ct_in || !d_ct_out) return set_error(HC_ERR_INVALID_ARG, "null ciphertext buffer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    hc_status st = check_inputs(ctx, d_ct_in, (size_t)2 * w->I, s);
+    if (st != HC_OK) return st;
+    ScratchGuard scratch(s);
+    scratch.p = dev_alloc((size_t)w->I * 2 * ctx->L * ctx->N * sizeof(uint64_t), s);
+    if (!scratch.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+    uint64_t *ct_ntt = (uint64_t *)scratch.p;
+    st = launch_ntt_fwd_ct(ctx, d_ct_in, ct_ntt, w->I, s);
+    if (st != HC_OK) return st;
+    return launch_mac_intt(ctx, ct_ntt, w->d_pt, MacTerms{w->d_term_ptr, w->d_terms}, d_ct_out, w->O, s);
+}
+
+hc_status hc_conv_ct_pt_plain(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in, uint64_t *d_ct_out,
+                              void *cuda_stream)
+{
+    if (!ctx_ok(ctx) || !weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid context or weights");
+    if (w->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "weights were preprocessed for another context");
+    if (!d_ct_in || !d_ct_out) return set_error(HC_ERR_INVALID_ARG, "null ciphertext buffer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    hc_status st = check_inputs(ctx, d_ct_in, (size_t)2 * w->I, s);
+    if (st != HC_OK) return st;
+    const size_t ct_words = (size_t)2 * ctx->L * ctx->N, pt_words = (size_t)ctx->L * ctx->N;
+    HC_CUDA_TRY(cudaMemsetAsync(d_ct_out, 0, (size_t)w->O * ct_words * sizeof(uint64_t), s));
+    const uint32_t M = w->desc.M;
+    for (uint32_t m = 0; m < M; ++m)
+        for (uint32_t gi = 0; gi < w->G; ++gi)
+            for (uint32_t b = 0; b < w->B; ++b) {
+                st = launch_product(ctx, d_ct_in + (size_t)(gi * w->B + b) * ct_words,
+                                    w->d_pt + (size_t)(m * w->G + gi) * pt_words, nullptr,
+                                    d_ct_out + (size_t)(m * w->B + b) * ct_words, 1, true, s);
+                if (st != HC_OK) return st;
+            }
+    return HC_OK;
+}
+
+hc_status hc_conv_ct_pt_host(const hc_ctx *ctx, const hc_weights *w, const uint64_t *h_ct_in, uint64_t *h_ct_out,
+                             void *cuda_stream)
+{
+    if (!ctx_ok(ctx) || !weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid context or weights");
+    if (!h_ct_in || !h_ct_out) return set_error(HC_ERR_INVALID_ARG, "null ciphertext buffer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    const size_t ct_bytes = (size_t)2 * ctx->L * ctx->N * sizeof(uint64_t);
+    ScratchGuard din(s), dout(s);
+    din.p = dev_alloc(w->I * ct_bytes, s);
+    dout.p = dev_alloc(w->O * ct_bytes, s);
+    if (!din.p || !dout.p) return set_error(HC_ERR_OOM, "device buffer allocation failed");
+    HC_CUDA_TRY(cudaMemcpyAsync(din.p, h_ct_in, w->I * ct_bytes, cudaMemcpyHostToDevice, s));
+    hc_status st = hc_conv_ct_pt(ctx, w, (const uint64_t *)din.p, (uint64_t *)dout.p, cuda_stream);
+    if (st != HC_OK) return st;
+    HC_CUDA_TRY(cudaMemcpyAsync(h_ct_out, dout.p, w->O * ct_bytes, cudaMemcpyDeviceToHost, s));
+    HC_CUDA_TRY(cudaStreamSynchronize(s));
+    return HC_OK;
+}
+
+hc_status hc_ctpt_mac(const hc_ctx *ctx, const uint64_t *d_ct, const uint64_t *d_pt_ntt, const uint32_t *h_slot,
+                      size_t n, uint64_t *d_out, size_t n_out, void *cuda_stream)
+{
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (n_out == 0) return HC_OK;
+    if (!d_out) return set_error(HC_ERR_INVALID_ARG, "d_out is NULL");
+    if (n > 0 && (!d_ct || !d_pt_ntt || !h_slot)) return set_error(HC_ERR_INVALID_ARG, "null input");
+    if (n > 0xffffffffull || n_out > 0xffffffffull) return set_error(HC_ERR_INVALID_ARG, "batch too large");
+    std::vector<uint32_t> count(n_out, 0);
+    for (size_t j = 0; j < n; ++j) {
+        if (h_slot[j] >= n_out) return set_error(HC_ERR_INVALID_ARG, "slot[%zu] = %u >= n_out", j, h_slot[j]);
+        ++count[h_slot[j]];
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    hc_status st = check_inputs(ctx, d_ct, 2 * n, s);
+    if (st == HC_OK) st = check_inputs(ctx, d_pt_ntt, n, s);
+    if (st != HC_OK) return st;
+    const size_t ct_words = (size_t)2 * ctx->L * ctx->N;
+    const bool single = std::all_of(count.begin(), count.end(), [](uint32_t c) { return c <= 1; });
+
+    if (single) {
+        // every slot has at most one product: fused NTT -> product -> INTT per product
+        if (n < n_out) HC_CUDA_TRY(cudaMemsetAsync(d_out, 0, n_out * ct_words * sizeof(uint64_t), s));
+        ScratchGuard idx(s);
+        idx.p = dev_alloc(n * sizeof(uint32_t), s);
+        if (!idx.p) return set_error(HC_ERR_OOM, "slot list allocation failed");
+        if (n) HC_CUDA_TRY(cudaMemcpyAsync(idx.p, h_slot, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        return launch_product(ctx, d_ct, d_pt_ntt, (const uint32_t *)idx.p, d_out, n, false, s);
+    }
+
+    // general case: NTT all ciphertexts once, then per slot MAC + INTT
+    std::vector<uint32_t> term_ptr(n_out + 1, 0), terms(2 * n);
+    for (size_t o = 0; o < n_out; ++o) term_ptr[o + 1] = term_ptr[o] + count[o];
+    std::vector<uint32_t> fill(term_ptr.begin(), term_ptr.end() - 1);
+    for (size_t j = 0; j < n; ++j) {
+        const uint32_t t = fill[h_slot[j]]++;
+        terms[2 * t] = (uint32_t)j;
+        terms[2 * t + 1] = (uint32_t)j;
+    }
+    ScratchGuard ctn(s), tp(s), tm(s);
+    ctn.p = dev_alloc(n * ct_words * sizeof(uint64_t), s);
+    tp.p = dev_alloc(term_ptr.size() * 4, s);
+    tm.p = dev_alloc(terms.size() * 4, s);
+    if (!ctn.p || !tp.p || !tm.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+    HC_CUDA_TRY(cudaMemcpyAsync(tp.p, term_ptr.data(), term_ptr.size() * 4, cudaMemcpyHostToDevice, s));
+    HC_CUDA_TRY(cudaMemcpyAsync(tm.p, terms.data(), terms.size() * 4, cudaMemcpyHostToDevice, s));
+    st = launch_ntt_fwd_ct(ctx, d_ct, (uint64_t *)ctn.p, n, s);
+    if (st != HC_OK) return st;
+    return launch_mac_intt(ctx, (const uint64_t *)ctn.p, d_pt_ntt,
+                           MacTerms{(const uint32_t *)tp.p, (const uint32_t *)tm.p}, d_out, n_out, s);
+}
+
+void hc_free(void *handle)
+{
+    if (!handle) return;
+    const uint32_t magic = *(const uint32_t *)handle;
+    if (magic == kMagicCtx) {
+        hc_ctx *c = (hc_ctx *)handle;
+        DeviceGuard g(c->device);
+        dev_free_persistent(c->d_tables);
+        dev_free_persistent(c->d_limbs);
+        dev_free_persistent(c->d_flag);
+        c->magic = kMagicDead;
+        delete c;
+    } else if (magic == kMagicWeights) {
+        hc_weights *w = (hc_weights *)handle;
+        DeviceGuard g(w->device);
+        dev_free_persistent(w->d_pt);
+        dev_free_persistent(w->d_term_ptr);
+        dev_free_persistent(w->d_terms);
+        w->magic = kMagicDead;
+        delete w;
+    }
+}
+
+}  // extern "C"

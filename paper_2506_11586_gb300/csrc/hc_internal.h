@@ -1,0 +1,142 @@
+// hc_internal.h -- internal types of libhconv (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "hconv.h"
+
+namespace hc {
+
+constexpr uint32_t kMaxLimbs = 8;
+constexpr uint32_t kMagicCtx = 0x48435458u;      // 'HCTX'
+constexpr uint32_t kMagicWeights = 0x48435754u;  // 'HCWT'
+constexpr uint32_t kMagicPlan = 0x4843504Cu;     // 'HCPL'
+constexpr uint32_t kMagicDead = 0xDEADDEADu;
+
+// Per-limb constants and twiddle tables, device-resident, read through the
+// read-only path.  Every Shoup companion w' = floor(w * 2^64 / q).
+struct LimbConst {
+    uint64_t q;
+    uint64_t r64, r64_s;      // 2^64 mod q, companion
+    uint64_t one_s;           // companion of 1: floor(2^64 / q)
+    uint64_t ninv, ninv_s;    // N^-1 mod q, companion
+    uint64_t ninvw, ninvw_s;  // N^-1 * psi^-rev(1) mod q, companion (last GS stage)
+    const ulonglong2 *tw_f;   // [N] {psi^rev(k), companion}, rev over log2 N bits
+    const ulonglong2 *tw_i;   // [N] {psi^-rev(k), companion}
+    uint64_t pad_[6];         // 128-byte stride
+};
+static_assert(sizeof(LimbConst) == 128, "LimbConst is 128 bytes");
+
+}  // namespace hc
+
+struct hc_ctx {
+    uint32_t magic;
+    uint32_t N, logN, L;
+    uint64_t t;
+    uint32_t flags;
+    int device;
+    uint64_t q[hc::kMaxLimbs];
+    uint64_t psi[hc::kMaxLimbs];
+    hc::LimbConst *d_limbs;   // [L]
+    void *d_tables;           // twiddle storage (owned)
+    size_t table_bytes;
+    int *d_flag;              // device error flag for checked mode (owned)
+};
+
+struct hc_weights {
+    uint32_t magic;
+    const hc_ctx *ctx;
+    int device;
+    hc_conv_desc desc;        // resolved partition
+    uint32_t G, B, I, P, O;
+    uint64_t *d_pt;           // [P][L][N] NTT domain (owned)
+    uint32_t *d_terms;        // CSR of output terms (owned): see mac kernels
+    uint32_t *d_term_ptr;     // [O+1]
+};
+
+namespace hc {
+
+// ---- error reporting ------------------------------------------------------
+hc_status set_error(hc_status s, const char *fmt, ...);
+hc_status cuda_error(cudaError_t e, const char *what);
+
+#define HC_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) return hc::cuda_error(e__, #expr); \
+    } while (0)
+
+// ---- allocation -------------------------------------------------------------
+void *dev_alloc(size_t bytes, cudaStream_t s);            // per-call scratch, stream ordered
+void dev_free(void *p, cudaStream_t s);
+void *dev_alloc_persistent(size_t bytes);                 // handle-owned memory
+void dev_free_persistent(void *p);
+
+// ---- device guard -------------------------------------------------------------
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+};
+
+// ---- tracing: CUDA events around one launch when hc_profile_enable(1) ----------
+bool profile_enabled();
+class ProfileScope {
+   public:
+    ProfileScope(const char *name, cudaStream_t s);
+    ~ProfileScope();
+    ProfileScope(const ProfileScope &) = delete;
+    ProfileScope &operator=(const ProfileScope &) = delete;
+
+   private:
+    const char *name_;
+    cudaStream_t s_;
+    cudaEvent_t start_ = nullptr, stop_ = nullptr;
+    bool active_ = false;
+};
+
+// ---- host-side number theory (independent of any test code) -----------------
+bool is_prime_u64(uint64_t n);
+uint64_t mulmod_u64(uint64_t a, uint64_t b, uint64_t q);
+uint64_t powmod_u64(uint64_t a, uint64_t e, uint64_t q);
+uint64_t min_primitive_2n_root(uint64_t q, uint32_t N);
+uint64_t shoup_companion(uint64_t w, uint64_t q);
+uint32_t bit_reverse(uint32_t k, uint32_t logn);
+
+// ---- kernel launchers (hc_kernels.cu) -------------------------------------------
+struct MacTerms {
+    const uint32_t *term_ptr;  // [n_out + 1] CSR offsets into terms
+    const uint32_t *terms;     // pairs (ct index, pt index), 2 per term
+};
+
+// in-place / out-of-place forward NTT of n_polys polys [n][L][N] (canonical in, canonical out)
+hc_status launch_ntt_fwd(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_polys,
+                         cudaStream_t s);
+hc_status launch_ntt_inv(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_polys,
+                         cudaStream_t s);
+// forward NTT of n_ct ciphertexts [n][2][L][N] into out (both components per CTA)
+hc_status launch_ntt_fwd_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_ct,
+                            cudaStream_t s);
+// out[o] = INTT(sum_t ct_ntt[terms.ct] . pt_ntt[terms.pt]) for o < n_out
+hc_status launch_mac_intt(const hc_ctx *ctx, const uint64_t *ct_ntt, const uint64_t *pt_ntt,
+                          MacTerms terms, uint64_t *out, size_t n_out, cudaStream_t s);
+// out[j] (+)= INTT(NTT(ct[j]) . pt_ntt[j]) for j < n (standalone products)
+hc_status launch_product(const hc_ctx *ctx, const uint64_t *ct, const uint64_t *pt_ntt,
+                         const uint32_t *out_index, uint64_t *out, size_t n, bool accumulate,
+                         cudaStream_t s);
+// weights: lift int8 packed polys [P][N] to [P][L][N] residues
+hc_status launch_lift_int8(const hc_ctx *ctx, const int8_t *packed, uint64_t *out, size_t n_polys,
+                           cudaStream_t s);
+// checked mode: set *flag if any of count residues of [n][L][N] is >= its q
+hc_status launch_range_check(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, int *flag,
+                             cudaStream_t s);
+
+hc_status check_range_now(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cudaStream_t s);
+
+}  // namespace hc

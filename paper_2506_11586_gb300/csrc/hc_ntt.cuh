@@ -1,0 +1,263 @@
+// hc_ntt.cuh -- register-resident negacyclic NTT engine for one CTA.
+//
+// A CTA transforms NP polynomials of N = 2^LOGN residues (NP = 2: both
+// components of one ciphertext limb, sharing every twiddle load) with
+// T = N / C threads; each thread holds C = 2^LOGC residues of every
+// polynomial in registers.  The log2 N butterfly stages run in rounds of
+// LOGC stages entirely inside registers; between rounds the CTA exchanges
+// data through shared memory (one write, one read per element).
+//
+// Forward (App. C.1, natural order in, slot order out): Cooley-Tukey stages
+// with the psi powers merged into the twiddles (Longa & Naehrig 2016); stage
+// s has 2^s groups of 2t = N / 2^s elements, group i uses psi^rev(2^s + i).
+// Inverse: Gentleman-Sande stages, stage s (half distance 2^s) has
+// N / 2^(s+1) groups, group i uses psi^-rev(N/2^(s+1) + i); N^-1 is merged
+// into the last stage.
+//
+// Lazy bounds (q < 2^50, N <= 2^14):
+//   forward: inputs < q; each stage adds 2q  -> outputs < (2 log2 N + 1) q < 2^55
+//   inverse: inputs < q; stage s inputs < 2^s q, X - Y + 2^s q < 2^(s+1) q <= 2^64;
+//            the last stage's Shoup steps and one correction give canonical output.
+//
+// Shared-memory layout: element e of polynomial p lives at word
+// p * N + (e ^ ((e >> LOGC) & 15)); the XOR swizzle makes every 8-byte
+// access pattern below conflict-free (the 16 threads of each half-warp touch
+// 16 distinct bank pairs) without padding.
+#pragma once
+
+#include <type_traits>
+
+#include "hc_arith.cuh"
+#include "hc_internal.h"
+
+namespace hc {
+
+template <int LOGN_, int LOGC_, int NP_>
+struct NttCfg {
+    static constexpr int LOGN = LOGN_;
+    static constexpr int LOGC = LOGC_;
+    static constexpr int NP = NP_;
+    static constexpr int N = 1 << LOGN;
+    static constexpr int C = 1 << LOGC;
+    static constexpr int T = N / C;
+    static constexpr int NROUNDS = (LOGN + LOGC - 1) / LOGC;
+    static constexpr int SW = N;  // shared words per polynomial
+    static constexpr size_t SMEM_BYTES = (size_t)NP * SW * sizeof(uint64_t);
+    static_assert(LOGC >= 2 && LOGC <= LOGN, "bad radix");
+};
+
+template <class Cfg>
+__device__ __forceinline__ int spos(int e)
+{
+    return e ^ ((e >> Cfg::LOGC) & 15);
+}
+
+template <class Cfg, int R>
+struct RoundShape {
+    static constexpr int S0 = R * Cfg::LOGC;
+    static constexpr int K = (Cfg::LOGN - S0) < Cfg::LOGC ? (Cfg::LOGN - S0) : Cfg::LOGC;
+    static constexpr int KK = 1 << K;
+    static constexpr int SUBS = Cfg::C >> K;  // sub-transforms per thread
+};
+
+// ---- element owned by (thread, register slot r) in each round ----------------
+// forward round: sub-transform u = tid*SUBS + v covers, at stride S = N >> (S0+K),
+// the KK elements (u / S) * (N >> S0) + (u % S) + j*S.
+template <class Cfg, int R>
+__device__ __forceinline__ int fwd_elem(int tid, int r)
+{
+    using RS = RoundShape<Cfg, R>;
+    constexpr int S = Cfg::N >> (RS::S0 + RS::K);
+    const int v = r >> RS::K, j = r & (RS::KK - 1);
+    const int u = tid * RS::SUBS + v;
+    return (u / S) * (Cfg::N >> RS::S0) + (u % S) + j * S;
+}
+
+// inverse round: sub-transform u = tid + v*T covers, at stride S = 2^S0, the KK
+// elements (u / S) * (S << K) + (u % S) + j*S.
+template <class Cfg, int R>
+__device__ __forceinline__ int inv_elem(int tid, int r)
+{
+    using RS = RoundShape<Cfg, R>;
+    constexpr int S = 1 << RS::S0;
+    const int v = r >> RS::K, j = r & (RS::KK - 1);
+    const int u = tid + v * Cfg::T;
+    return (u / S) * (S << RS::K) + (u % S) + j * S;
+}
+
+// ---- compile-time loop -------------------------------------------------------------
+template <int I, int END, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (I < END) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, END>(f);
+    }
+}
+
+// ---- one forward round: K Cooley-Tukey stages in registers ---------------------
+template <class Cfg, int R, int SIG>
+__device__ __forceinline__ void fwd_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const ulonglong2 *__restrict__ tw,
+                                          uint64_t q, int v, int g0)
+{
+    using RS = RoundShape<Cfg, R>;
+    constexpr int half = RS::KK >> (SIG + 1);
+    const uint64_t q2 = 2 * q;
+#pragma unroll
+    for (int lam = 0; lam < (1 << SIG); ++lam) {
+        const ulonglong2 w = __ldg(tw + (1 << (RS::S0 + SIG)) + (g0 << SIG) + lam);
+#pragma unroll
+        for (int jj = 0; jj < half; ++jj) {
+            const int j = v * RS::KK + lam * 2 * half + jj;
+#pragma unroll
+            for (int p = 0; p < Cfg::NP; ++p) {
+                const uint64_t X = x[p][j];
+                const uint64_t t = shoup_mul(x[p][j + half], w.x, w.y, q);
+                x[p][j] = X + t;
+                x[p][j + half] = X - t + q2;
+            }
+        }
+    }
+}
+
+template <class Cfg, int R>
+__device__ __forceinline__ void fwd_round(uint64_t (&x)[Cfg::NP][Cfg::C],
+                                          const ulonglong2 *__restrict__ tw, uint64_t q, int tid)
+{
+    using RS = RoundShape<Cfg, R>;
+    constexpr int S = Cfg::N >> (RS::S0 + RS::K);
+    static_for<0, RS::SUBS>([&](auto vc) {
+        constexpr int v = decltype(vc)::value;
+        const int g0 = (tid * RS::SUBS + v) / S;
+        static_for<0, RS::K>([&](auto sc) { fwd_stage<Cfg, R, decltype(sc)::value>(x, tw, q, v, g0); });
+    });
+}
+
+// ---- one inverse round: K Gentleman-Sande stages in registers ------------------
+template <class Cfg, int R, int SIG>
+__device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const LimbConst &lc,
+                                          const ulonglong2 *__restrict__ tw, int v, int blk)
+{
+    using RS = RoundShape<Cfg, R>;
+    constexpr int s = RS::S0 + SIG;  // global stage
+    constexpr int dist = 1 << SIG;
+    constexpr int ngrp = RS::KK >> (SIG + 1);
+    const uint64_t q = lc.q;
+    const uint64_t qs = q << s;
+    if constexpr (s == Cfg::LOGN - 1) {
+        // last stage: N^-1 merged into both outputs, canonical result
+#pragma unroll
+        for (int grp = 0; grp < ngrp; ++grp) {
+#pragma unroll
+            for (int jj = 0; jj < dist; ++jj) {
+                const int j = v * RS::KK + grp * 2 * dist + jj;
+#pragma unroll
+                for (int p = 0; p < Cfg::NP; ++p) {
+                    const uint64_t X = x[p][j], Y = x[p][j + dist];
+                    const uint64_t a = shoup_mul(X + Y, lc.ninv, lc.ninv_s, q);
+                    const uint64_t b = shoup_mul(X - Y + qs, lc.ninvw, lc.ninvw_s, q);
+                    x[p][j] = csub(a, q);
+                    x[p][j + dist] = csub(b, q);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int grp = 0; grp < ngrp; ++grp) {
+            const ulonglong2 w = __ldg(tw + (Cfg::N >> (s + 1)) + blk * ngrp + grp);
+#pragma unroll
+            for (int jj = 0; jj < dist; ++jj) {
+                const int j = v * RS::KK + grp * 2 * dist + jj;
+#pragma unroll
+                for (int p = 0; p < Cfg::NP; ++p) {
+                    const uint64_t X = x[p][j], Y = x[p][j + dist];
+                    x[p][j] = X + Y;
+                    x[p][j + dist] = shoup_mul(X - Y + qs, w.x, w.y, q);
+                }
+            }
+        }
+    }
+}
+
+template <class Cfg, int R>
+__device__ __forceinline__ void inv_round(uint64_t (&x)[Cfg::NP][Cfg::C], const LimbConst &lc,
+                                          const ulonglong2 *__restrict__ tw, int tid)
+{
+    using RS = RoundShape<Cfg, R>;
+    constexpr int S = 1 << RS::S0;
+    static_for<0, RS::SUBS>([&](auto vc) {
+        constexpr int v = decltype(vc)::value;
+        const int blk = (tid + v * Cfg::T) / S;
+        static_for<0, RS::K>([&](auto sc) { inv_stage<Cfg, R, decltype(sc)::value>(x, lc, tw, v, blk); });
+    });
+}
+
+// ---- exchanges through shared memory ---------------------------------------------
+template <class Cfg, int RFROM>
+__device__ __forceinline__ void fwd_exchange(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm, int tid)
+{
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < Cfg::C; ++r) {
+        const int e = spos<Cfg>(fwd_elem<Cfg, RFROM>(tid, r));
+#pragma unroll
+        for (int p = 0; p < Cfg::NP; ++p) sm[p * Cfg::SW + e] = x[p][r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < Cfg::C; ++r) {
+        const int e = spos<Cfg>(fwd_elem<Cfg, RFROM + 1>(tid, r));
+#pragma unroll
+        for (int p = 0; p < Cfg::NP; ++p) x[p][r] = sm[p * Cfg::SW + e];
+    }
+}
+
+template <class Cfg, int RFROM>
+__device__ __forceinline__ void inv_exchange(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm, int tid)
+{
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < Cfg::C; ++r) {
+        const int e = spos<Cfg>(inv_elem<Cfg, RFROM>(tid, r));
+#pragma unroll
+        for (int p = 0; p < Cfg::NP; ++p) sm[p * Cfg::SW + e] = x[p][r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < Cfg::C; ++r) {
+        const int e = spos<Cfg>(inv_elem<Cfg, RFROM + 1>(tid, r));
+#pragma unroll
+        for (int p = 0; p < Cfg::NP; ++p) x[p][r] = sm[p * Cfg::SW + e];
+    }
+}
+
+// ---- whole transforms -----------------------------------------------------------
+// forward: x holds the round-0 layout (element tid + r*T) on entry and the
+// last-round layout (element tid*C + r, contiguous) on exit.
+template <class Cfg, int R = 0>
+__device__ __forceinline__ void fwd_transform(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm,
+                                              const ulonglong2 *__restrict__ tw, uint64_t q, int tid)
+{
+    fwd_round<Cfg, R>(x, tw, q, tid);
+    if constexpr (R + 1 < Cfg::NROUNDS) {
+        fwd_exchange<Cfg, R>(x, sm, tid);
+        fwd_transform<Cfg, R + 1>(x, sm, tw, q, tid);
+    }
+}
+
+// inverse: x holds element tid*C + r (contiguous) on entry, canonical values
+// < q; on exit the last-round layout (element tid + r'*T for the slot order of
+// inv_elem), canonical.
+template <class Cfg, int R = 0>
+__device__ __forceinline__ void inv_transform(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm,
+                                              const LimbConst &lc, const ulonglong2 *__restrict__ tw,
+                                              int tid)
+{
+    inv_round<Cfg, R>(x, lc, tw, tid);
+    if constexpr (R + 1 < Cfg::NROUNDS) {
+        inv_exchange<Cfg, R>(x, sm, tid);
+        inv_transform<Cfg, R + 1>(x, sm, lc, tw, tid);
+    }
+}
+
+}  // namespace hc

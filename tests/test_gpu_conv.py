@@ -1,0 +1,163 @@
+"""GPU parity of the convolution path: hc_weights_preprocess (offline NTT of
+packed weights, Sec. 6.2 / Sec. 8.1) and hc_conv_ct_pt (online NTT -> MAC ->
+INTT, Sec. 6.2) against the oracle's schoolbook convolution, bit-exact, and
+end to end through BFV: encrypt -> GPU conv -> decrypt == plaintext conv mod t."""
+import numpy as np
+import pytest
+
+from gpu_util import sample_indices, to_dev, to_host
+from oracle import bfv, conv, core
+from paper_2506_11586_gb300.inputs import (CANONICAL_PRIMES, CONV_56x56x64, T_PLAIN, Stream, conv_tensors)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_11586_gb300 import _lib
+    from paper_2506_11586_gb300.build import build
+    build()
+    return _lib
+
+
+def _encrypted_layer(C_, H, W, M, kh, kw, pad, N, nl, seed, x=None, K=None):
+    s = Stream(seed, 3)
+    if x is None:
+        x = s.below(T_PLAIN, C_ * H * W).astype(np.int64).reshape(C_, H, W)
+        K = s.int8(M * C_ * kh * kw).astype(np.int64).reshape(M, C_, kh, kw)
+    p = conv.canonical_partition(C_, H, W, M, kh, kw, pad, N)
+    params = bfv.Params(N, CANONICAL_PRIMES[:nl], T_PLAIN)
+    sk = s.ternary(N)
+    xin = conv.pack_input(x, p)
+    ct = np.zeros((p.I, 2, nl, N), dtype=np.uint64)
+    for i in range(p.I):
+        a = np.stack([s.below(q, N) for q in params.moduli])
+        ct[i] = bfv.encrypt(params, sk, xin[i], a, s.rounded_gaussian(N))
+    return x, np.asarray(K, dtype=np.int64), p, params, sk, ct
+
+
+def _gpu_layer(L, p, params, K):
+    ctx = L.hc_ctx_create(p.N, params.moduli, T_PLAIN)
+    d = L.make_desc(p.C, p.H, p.W, p.M, p.kh, p.kw, pad=p.pad)
+    w = L.hc_weights_preprocess(ctx, d, K.astype(np.int8))
+    assert (w.desc.Cw, w.desc.Hw, w.desc.Ww, w.I, w.O) == (p.Cw, p.Hw, p.Ww, p.I, p.O)
+    return ctx, w
+
+
+def _check_decrypt(p, params, sk, out, y, ms):
+    for m in ms:
+        for b in range(p.B):
+            slots = conv.output_slots(p, b)
+            ks = [k for k, _, _ in slots]
+            got = bfv.decrypt_at(params, sk, out[m * p.B + b], ks)
+            want = np.array([y[m, r, c] for _, r, c in slots])
+            assert np.array_equal(got, want), (m, b)
+
+
+@pytest.mark.parametrize("shape", [
+    (5, 7, 6, 3, 3, 3, 1, 4096, 2),     # ragged channel group, edge blocks
+    (12, 9, 9, 4, 1, 1, 0, 8192, 3),    # 1x1 convolution
+    (6, 20, 20, 3, 3, 3, 1, 16384, 4),  # N = 16384, four limbs
+])
+def test_small_layer_full_parity(L, shape):
+    x, K, p, params, sk, ct = _encrypted_layer(*shape, seed=sum(shape))
+    ctx, w = _gpu_layer(L, p, params, K)
+    d_in = to_dev(ct)
+    d_out = torch.empty(p.O * 2 * len(params.moduli) * p.N, dtype=torch.int64, device="cuda")
+    L.hc_conv_ct_pt(ctx, w, d_in, d_out)
+    torch.cuda.synchronize()
+    got = to_host(d_out).reshape(p.O, 2, len(params.moduli), p.N)
+    Kp = conv.pack_weights(K, p)
+    want = conv.conv_ct_pt(ct, Kp, p, params.moduli)
+    assert np.array_equal(got, want)
+    assert np.array_equal(to_host(d_in).reshape(ct.shape), ct)        # input untouched
+    y = conv.conv2d_mod_t(x, K, p.pad, T_PLAIN)
+    _check_decrypt(p, params, sk, got, y, range(p.M))
+    # the plain one-launch-per-product path gives the same bits
+    d_plain = torch.empty_like(d_out)
+    L.hc_conv_ct_pt_plain(ctx, w, d_in, d_plain)
+    torch.cuda.synchronize()
+    assert torch.equal(d_plain, d_out)
+    # host-buffer entry point
+    h_out = np.zeros((p.O, 2, len(params.moduli), p.N), dtype=np.uint64)
+    L.hc_conv_ct_pt_host(ctx, w, np.ascontiguousarray(ct), h_out)
+    assert np.array_equal(h_out, got)
+
+
+def test_preprocessed_weights_are_ntt_of_packing(L):
+    C_, H, W, M = 6, 10, 10, 4
+    s = Stream(44, 0)
+    K = s.int8(M * C_ * 9).astype(np.int64).reshape(M, C_, 3, 3)
+    N, moduli = 8192, CANONICAL_PRIMES[:3]
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    w = L.hc_weights_preprocess(ctx, L.make_desc(C_, H, W, M, 3, 3, pad=1), K.astype(np.int8))
+    p = conv.canonical_partition(C_, H, W, M, 3, 3, 1, N)
+    _, n_pt = L.hc_weights_data(w)
+    assert n_pt == p.P
+    buf = torch.empty(p.P * 3 * N, dtype=torch.int64, device="cuda")
+    L.hc_weights_export(w, buf)
+    torch.cuda.synchronize()
+    got = to_host(buf).reshape(p.P, 3, N)
+    Kp = conv.pack_weights(K, p)
+    ks = sample_indices(N, 48, 3)
+    for pi in range(p.P):
+        for li, q in enumerate(moduli):
+            want = core.ntt(core.lift_small(Kp[pi], q), q, core.min_psi(q, N), ks)
+            assert np.array_equal(got[pi, li][ks], want), (pi, li)
+
+
+@pytest.fixture(scope="module")
+def layer_56x56x64():
+    """The 56x56x64 -> 64, 3x3 layer at N = 8192 with three primes, encrypted."""
+    sh = CONV_56x56x64
+    x, K = conv_tensors(sh, seed=2)
+    return _encrypted_layer(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, sh.pad, 8192, 3, seed=2, x=x, K=K)
+
+
+def test_layer_56x56x64_parity(L, layer_56x56x64):
+    x, K, p, params, sk, ct = layer_56x56x64
+    assert (p.I, p.P, p.O, p.products) == (32, 512, 256, 2048)
+    ctx, w = _gpu_layer(L, p, params, K)
+    d_in = to_dev(ct)
+    d_out = torch.empty(p.O * 2 * 3 * p.N, dtype=torch.int64, device="cuda")
+    L.hc_conv_ct_pt(ctx, w, d_in, d_out)
+    torch.cuda.synchronize()
+    got = to_host(d_out).reshape(p.O, 2, 3, p.N)
+    # sampled coefficients of every output polynomial vs the schoolbook conv
+    ks = sample_indices(p.N, 40, 11)
+    want = conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, params.moduli, ks)
+    assert np.array_equal(got[..., ks], want)
+    # decrypt every output slot of a spread of output channels
+    y = conv.conv2d_mod_t(x, K, p.pad, T_PLAIN)
+    _check_decrypt(p, params, sk, got, y, [0, 1, 31, 63])
+    # repeat run is deterministic; plain path agrees bit for bit
+    d_out2 = torch.empty_like(d_out)
+    L.hc_conv_ct_pt(ctx, w, d_in, d_out2)
+    torch.cuda.synchronize()
+    assert torch.equal(d_out2, d_out)
+    d_plain = torch.empty_like(d_out)
+    L.hc_conv_ct_pt_plain(ctx, w, d_in, d_plain)
+    torch.cuda.synchronize()
+    assert torch.equal(d_plain, d_out)
+
+
+def test_conv_argument_errors(L):
+    N, moduli = 4096, CANONICAL_PRIMES[:2]
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    other = L.hc_ctx_create(N, moduli, T_PLAIN)
+    K = np.zeros((2, 3, 3, 3), dtype=np.int8)
+    w = L.hc_weights_preprocess(ctx, L.make_desc(3, 5, 5, 2, 3, 3, pad=1), K)
+    buf = torch.zeros(w.I * 2 * 2 * N, dtype=torch.int64, device="cuda")
+    out = torch.zeros(w.O * 2 * 2 * N, dtype=torch.int64, device="cuda")
+    with pytest.raises(L.HcError) as e:
+        L.hc_conv_ct_pt(other, w, buf, out)           # weights of another context
+    assert e.value.status == L.HC_ERR_INVALID_ARG
+    with pytest.raises(L.HcError) as e:
+        L.hc_weights_preprocess(ctx, L.make_desc(3, 5, 5, 2, 3, 3, pad=1, stride=2), K)
+    assert e.value.status == L.HC_ERR_UNSUPPORTED
+    L.hc_conv_ct_pt(ctx, w, buf, out)                 # all-zero input -> all-zero output
+    torch.cuda.synchronize()
+    assert int(out.abs().sum()) == 0
