@@ -181,6 +181,24 @@ hc_status hc_conv_ct_pt_plain(const hc_ctx *ctx, const hc_weights *w, const uint
 hc_status hc_conv_ct_pt_host(const hc_ctx *ctx, const hc_weights *w, const uint64_t *h_ct_in,
                              uint64_t *h_ct_out, void *cuda_stream);
 
+/* hc_conv_ct_pt without any device allocation.  The paper has no counterpart:
+ * this is a deployment variant for callers that must not allocate device
+ * memory -- e.g. a service whose device memory is reserved up front by
+ * another framework's caching allocator, or a latency-critical loop where
+ * cudaMalloc / cudaFree would synchronise the device.  Same arguments, same
+ * result, bit for bit, as hc_conv_ct_pt.  Its scratch (the NTT'd inputs,
+ * I*2*L*N*8 bytes) lives in one static device array of 16 MiB that every GPU
+ * loading the library keeps until the process exits; a larger layer is
+ * rejected with HC_ERR_BUDGET.  The first call on a device looks up that
+ * array's device address (once per device, with the context's device
+ * current); make that first call before any stream capture.  All calls share
+ * the one array: calls whose GPU work overlaps (other streams, other threads)
+ * race on it and must be serialised by the caller.  Every scratch word read
+ * is first written by the same call, so leftovers from earlier calls are
+ * harmless.  Errors: as hc_conv_ct_pt, plus HC_ERR_BUDGET. */
+hc_status hc_conv_ct_pt_noalloc(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in,
+                                uint64_t *d_ct_out, void *cuda_stream);
+
 /* --------------------------------------------------- generic ct x pt MAC --
  * The NTT-domain multiply-accumulate of Sec. 6.2 for arbitrary products:
  *   d_out[s] = sum_{j : h_slot[j] == s} INTT( NTT(d_ct[j]) . d_pt_ntt[j] )

@@ -67,6 +67,7 @@ _SIGS = {
     "hc_conv_ct_pt": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_conv_ct_pt_plain": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_conv_ct_pt_host": (C.c_int, [_P, _P, _P, _P, _P]),
+    "hc_conv_ct_pt_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_ctpt_mac": (C.c_int, [_P, _P, _P, _P, C.c_size_t, _P, C.c_size_t, _P]),
     "hc_set_allocator": (None, [_P, _P, _P]),
     "hc_profile_enable": (None, [C.c_int]),
@@ -257,6 +258,11 @@ def hc_conv_ct_pt(ctx, w, ct_in, ct_out, stream=None):
 
 def hc_conv_ct_pt_plain(ctx, w, ct_in, ct_out, stream=None):
     _check(lib().hc_conv_ct_pt_plain(ctx.ptr, w.ptr, _dptr(ct_in), _dptr(ct_out), _stream(stream)))
+
+
+def hc_conv_ct_pt_noalloc(ctx, w, ct_in, ct_out, stream=None):
+    """hc_conv_ct_pt with its scratch in the library's static device array (no allocation)."""
+    _check(lib().hc_conv_ct_pt_noalloc(ctx.ptr, w.ptr, _dptr(ct_in), _dptr(ct_out), _stream(stream)))
 
 
 def hc_conv_ct_pt_host(ctx, w, h_in, h_out, stream=None):

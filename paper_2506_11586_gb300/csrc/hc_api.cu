@@ -126,6 +126,17 @@ void pack_weights(const hc_conv_desc &d, const Geom &g, uint32_t N, const int8_t
         }
 }
 
+struct ScratchGuard {
+    void *p = nullptr;
+    cudaStream_t s;
+    explicit ScratchGuard(cudaStream_t st) : s(st) {}
+    ~ScratchGuard() { dev_free(p, s); }
+};
+
+}  // namespace
+
+namespace hc {
+// checked mode: HC_ERR_RANGE if any residue of [n][L][N] is >= its q_i (synchronises s)
 hc_status check_inputs(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cudaStream_t s)
 {
     if (!(ctx->flags & HC_CTX_CHECKED) || n_polys == 0) return HC_OK;
@@ -138,15 +149,7 @@ hc_status check_inputs(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cud
     if (h) return set_error(HC_ERR_RANGE, "input residue out of range [0, q_i)");
     return HC_OK;
 }
-
-struct ScratchGuard {
-    void *p = nullptr;
-    cudaStream_t s;
-    explicit ScratchGuard(cudaStream_t st) : s(st) {}
-    ~ScratchGuard() { dev_free(p, s); }
-};
-
-}  // namespace
+}  // namespace hc
 
 // =============================================================================
 extern "C" {

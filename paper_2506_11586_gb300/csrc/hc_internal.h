@@ -137,6 +137,7 @@ hc_status launch_lift_int8(const hc_ctx *ctx, const int8_t *packed, uint64_t *ou
 hc_status launch_range_check(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, int *flag,
                              cudaStream_t s);
 
-hc_status check_range_now(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cudaStream_t s);
+// checked mode only: HC_ERR_RANGE if a residue is >= its q_i (synchronises s); HC_OK otherwise
+hc_status check_inputs(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cudaStream_t s);
 
 }  // namespace hc
