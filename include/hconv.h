@@ -25,7 +25,7 @@
  *     GPU finishes; launch errors are reported by the call, execution errors
  *     by a later call or by stream synchronisation.
  *   - Supported parameters: N in {4096, 8192, 16384}; 1 <= L <= 8 distinct
- *     primes q_i < 2^50 with q_i = 1 (mod 2N).
+ *     primes 2^32 < q_i < 2^50 with q_i = 1 (mod 2N).
  *   - A context is immutable after creation and may be used from several
  *     streams and host threads at once; weights likewise.  A plan is not
  *     thread-safe: run one plan on one stream at a time.
@@ -47,7 +47,7 @@ typedef struct hc_plan hc_plan;
 typedef enum {
     HC_OK = 0,
     HC_ERR_INVALID_ARG = 1,  /* null pointer, zero/oversized count, bad shape */
-    HC_ERR_BAD_MODULUS = 2,  /* not prime, >= 2^50, != 1 mod 2N, duplicate */
+    HC_ERR_BAD_MODULUS = 2,  /* not prime, outside (2^32, 2^50), != 1 mod 2N, duplicate */
     HC_ERR_RANGE = 3,        /* checked mode: an input residue >= q_i */
     HC_ERR_OOM = 4,          /* device or host allocation failed */
     HC_ERR_BUDGET = 5,       /* admission: request exceeds the memory budget */
@@ -82,6 +82,17 @@ hc_status hc_ctx_validate(uint32_t N, const uint64_t *moduli, uint32_t L, uint64
  * and psi_out (host arrays of L entries) receive q_i and the psi_i used. */
 hc_status hc_ctx_info(const hc_ctx *ctx, uint32_t *N, uint32_t *L, uint64_t *t,
                       uint64_t *moduli_out, uint64_t *psi_out);
+
+/* Launch-shape tuning (no counterpart in the paper: a GPU scheduling knob).
+ * Kernel families (kind): 0 forward NTT, 1 inverse NTT, 2 fused NTT-domain
+ * MAC + inverse NTT, 3 fused standalone product, 4 forward NTT of whole
+ * ciphertexts.  variant (0..2) selects the radix per register round, the
+ * polynomials per CTA and the CTAs per SM for the context's N; every variant
+ * computes the same bits, only speed differs.  hc_ctx_create picks defaults.
+ * Changing a variant while other threads use the context is a data race.
+ * Errors: HC_ERR_INVALID_ARG (bad handle, kind or variant). */
+hc_status hc_ctx_set_variant(hc_ctx *ctx, uint32_t kind, uint32_t variant);
+hc_status hc_ctx_get_variant(const hc_ctx *ctx, uint32_t kind, uint32_t *variant);
 
 /* -------------------------------------------------------------- transforms --
  * Negacyclic NTT over each RNS limb (App. C.1): the point-value form in which

@@ -55,6 +55,8 @@ _SIGS = {
     "hc_ctx_create": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64, C.POINTER(_P)]),
     "hc_ctx_create_ex": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(_P)]),
     "hc_ctx_validate": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64]),
+    "hc_ctx_set_variant": (C.c_int, [_P, C.c_uint32, C.c_uint32]),
+    "hc_ctx_get_variant": (C.c_int, [_P, C.c_uint32, C.POINTER(C.c_uint32)]),
     "hc_ctx_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), _P, _P]),
     "hc_ntt_fwd": (C.c_int, [_P, _P, C.c_size_t, _P]),
     "hc_ntt_inv": (C.c_int, [_P, _P, C.c_size_t, _P]),
@@ -174,6 +176,20 @@ def hc_ctx_create(N, moduli, t, flags=0):
     out = C.c_void_p()
     _check(lib().hc_ctx_create_ex(N, C.c_void_p(m.ctypes.data), m.size, t, flags, C.byref(out)))
     return Ctx(out, N, [int(x) for x in m], t)
+
+
+KIND_NTT_FWD, KIND_NTT_INV, KIND_MAC_INTT, KIND_PRODUCT, KIND_NTT_FWD_CT = range(5)
+N_VARIANTS = 3
+
+
+def hc_ctx_set_variant(ctx, kind, variant):
+    _check(lib().hc_ctx_set_variant(ctx.ptr, kind, variant))
+
+
+def hc_ctx_get_variant(ctx, kind):
+    v = C.c_uint32()
+    _check(lib().hc_ctx_get_variant(ctx.ptr, kind, C.byref(v)))
+    return v.value
 
 
 def hc_ctx_info(ctx):

@@ -185,6 +185,7 @@ hc_status hc_ctx_validate(uint32_t N, const uint64_t *moduli, uint32_t L, uint64
     for (uint32_t i = 0; i < L; ++i) {
         const uint64_t q = moduli[i];
         if (q >= (1ull << 50)) return set_error(HC_ERR_BAD_MODULUS, "q[%u] = %llu >= 2^50", i, (unsigned long long)q);
+        if (q <= (1ull << 32)) return set_error(HC_ERR_BAD_MODULUS, "q[%u] = %llu <= 2^32", i, (unsigned long long)q);
         if (q % (2ull * N) != 1)
             return set_error(HC_ERR_BAD_MODULUS, "q[%u] = %llu is not 1 mod 2N", i, (unsigned long long)q);
         if (!is_prime_u64(q)) return set_error(HC_ERR_BAD_MODULUS, "q[%u] = %llu is not prime", i, (unsigned long long)q);
@@ -210,6 +211,7 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
     c->L = L;
     c->t = t;
     c->flags = flags;
+    for (int k = 0; k < KK_COUNT; ++k) c->variant[k] = (uint8_t)default_variant(k, c->logN);
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         delete c;
         cudaGetLastError();
@@ -287,6 +289,23 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
 hc_status hc_ctx_create(uint32_t N, const uint64_t *moduli, uint32_t L, uint64_t t, hc_ctx **out)
 {
     return hc_ctx_create_ex(N, moduli, L, t, 0, out);
+}
+
+hc_status hc_ctx_set_variant(hc_ctx *ctx, uint32_t kind, uint32_t variant)
+{
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (kind >= (uint32_t)KK_COUNT) return set_error(HC_ERR_INVALID_ARG, "kernel kind %u out of range", kind);
+    if (variant >= (uint32_t)kNumVariants) return set_error(HC_ERR_INVALID_ARG, "variant %u out of range", variant);
+    ctx->variant[kind] = (uint8_t)variant;
+    return HC_OK;
+}
+
+hc_status hc_ctx_get_variant(const hc_ctx *ctx, uint32_t kind, uint32_t *variant)
+{
+    if (!ctx_ok(ctx) || !variant) return set_error(HC_ERR_INVALID_ARG, "invalid context or output");
+    if (kind >= (uint32_t)KK_COUNT) return set_error(HC_ERR_INVALID_ARG, "kernel kind %u out of range", kind);
+    *variant = ctx->variant[kind];
+    return HC_OK;
 }
 
 hc_status hc_ctx_info(const hc_ctx *ctx, uint32_t *N, uint32_t *L, uint64_t *t, uint64_t *moduli_out,

@@ -32,6 +32,10 @@ struct LimbConst {
 };
 static_assert(sizeof(LimbConst) == 128, "LimbConst is 128 bytes");
 
+// Kernel families whose launch shape is selectable per context.
+enum KernelKind { KK_FWD = 0, KK_INV = 1, KK_MAC = 2, KK_PROD = 3, KK_FWDCT = 4, KK_COUNT = 5 };
+constexpr int kNumVariants = 3;
+
 }  // namespace hc
 
 struct hc_ctx {
@@ -46,6 +50,7 @@ struct hc_ctx {
     void *d_tables;           // twiddle storage (owned)
     size_t table_bytes;
     int *d_flag;              // device error flag for checked mode (owned)
+    uint8_t variant[hc::KK_COUNT];  // launch-shape variant per kernel family
 };
 
 struct hc_weights {
@@ -114,6 +119,22 @@ struct MacTerms {
     const uint32_t *term_ptr;  // [n_out + 1] CSR offsets into terms
     const uint32_t *terms;     // pairs (ct index, pt index), 2 per term
 };
+
+// arguments of one launch of a kernel family (unused fields ignored)
+struct LaunchArgs {
+    const uint64_t *in;
+    uint64_t *out;
+    const uint64_t *pt;
+    MacTerms terms;
+    const uint32_t *out_index;
+    size_t n;
+    bool accumulate;
+};
+template <int LOGN>
+hc_status launch_n(const hc_ctx *ctx, int kind, int variant, const LaunchArgs &a, cudaStream_t s);
+
+// default launch variant of a kernel family at ring degree 2^logn
+int default_variant(int kind, uint32_t logn);
 
 // in-place / out-of-place forward NTT of n_polys polys [n][L][N] (canonical in, canonical out)
 hc_status launch_ntt_fwd(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_polys,

@@ -1,4 +1,6 @@
-// hc_kernels.cu -- sm_103a kernels of the HE-convolution hot path and their launchers.
+// hc_kernels.cuh -- sm_103a kernels of the HE-convolution hot path, their
+// launch shapes and launchers.  Instantiated once per ring degree in
+// hc_kernels_n12.cu / _n13.cu / _n14.cu (compiled in parallel).
 //
 //   k_ntt_fwd   forward NTT of NP polynomials per CTA (in place or out of place)
 //   k_ntt_inv   inverse NTT, NP polynomials per CTA
@@ -6,28 +8,36 @@
 //               out[o] = INTT(sum_t ct_ntt[ct_t] . pt_ntt[pt_t])         (Sec. 6.2)
 //   k_product   one standalone ct x pt product fused end to end:
 //               out[j] (+)= INTT(NTT(ct[j]) . pt_ntt[j])                  (App. C.1)
-//   k_lift_int8 signed 8-bit weight coefficients -> residues mod every q_i
-//   k_range_check  checked mode: flag any residue >= q_i
 //
 // All kernels are plain integer code (no tensor cores: this is exact modular
 // arithmetic, not a floating-point contraction).  One CTA owns NP whole
 // polynomial limbs, so every transform reads and writes HBM exactly once.
+#pragma once
+
 #include <atomic>
 
 #include "hc_ntt.cuh"
 
 namespace hc {
 
-// Launch shapes: 512 threads per CTA for every N; both ciphertext components
-// share a CTA (and its twiddle loads) up to N = 8192.
-template <int LOGN> struct FusedCfgSel;
-template <> struct FusedCfgSel<12> { using type = NttCfg<12, 3, 2>; };
-template <> struct FusedCfgSel<13> { using type = NttCfg<13, 4, 2>; };
-template <> struct FusedCfgSel<14> { using type = NttCfg<14, 5, 1>; };
-template <int LOGN> struct SingleCfgSel;
-template <> struct SingleCfgSel<12> { using type = NttCfg<12, 3, 1>; };
-template <> struct SingleCfgSel<13> { using type = NttCfg<13, 4, 1>; };
-template <> struct SingleCfgSel<14> { using type = NttCfg<14, 5, 1>; };
+// ---------------------------------------------------------------------------
+// Launch-shape variants per ring degree: (log2 C, NP, CTAs per SM).  C residues
+// of each of NP polynomials per thread, T = N / C threads per CTA, registers
+// sized for MINB resident CTAs.  Single-polynomial kernels (KK_FWD, KK_INV)
+// use NP = 1 with the same C and MINB.
+template <int LOGN, int V> struct Variant;
+template <> struct Variant<12, 0> { static constexpr int LOGC = 3, NP = 2, MINB = 1; };   // T 512, 128 regs
+template <> struct Variant<12, 1> { static constexpr int LOGC = 4, NP = 2, MINB = 2; };   // T 256, 128 regs
+template <> struct Variant<12, 2> { static constexpr int LOGC = 4, NP = 1, MINB = 2; };   // T 256, 128 regs
+template <> struct Variant<13, 0> { static constexpr int LOGC = 4, NP = 2, MINB = 1; };   // T 512, 128 regs
+template <> struct Variant<13, 1> { static constexpr int LOGC = 5, NP = 1, MINB = 2; };   // T 256, 128 regs
+template <> struct Variant<13, 2> { static constexpr int LOGC = 4, NP = 1, MINB = 2; };   // T 512, 64 regs
+template <> struct Variant<14, 0> { static constexpr int LOGC = 5, NP = 1, MINB = 1; };   // T 512, 128 regs
+template <> struct Variant<14, 1> { static constexpr int LOGC = 4, NP = 1, MINB = 1; };   // T 1024, 64 regs
+template <> struct Variant<14, 2> { static constexpr int LOGC = 5, NP = 1, MINB = 1; };   // (same as 0)
+
+template <int LOGN, int V, bool SINGLE>
+using VCfg = NttCfg<LOGN, Variant<LOGN, V>::LOGC, SINGLE ? 1 : Variant<LOGN, V>::NP, Variant<LOGN, V>::MINB>;
 
 // ---------------------------------------------------------------------------
 // store the last inverse-round layout: slot r = v*KK + j holds element
@@ -40,9 +50,21 @@ __device__ __forceinline__ int inv_out_elem(int tid, int r)
     return tid + Cfg::T * (v + j * RS::SUBS);
 }
 
+// after the block has filled shared memory: x[p][r] = element tid*C + r
+// (the inverse transform's round-0 layout)
+template <class Cfg>
+__device__ __forceinline__ void load_round0(uint64_t (&x)[Cfg::NP][Cfg::C], const uint64_t *sm, int tid)
+{
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < Cfg::C; ++r)
+#pragma unroll
+        for (int p = 0; p < Cfg::NP; ++p) x[p][r] = sm[p * Cfg::N + spos<Cfg>(tid * Cfg::C + r)];
+}
+
 // ---------------------------------------------------------------------------
 template <class Cfg>
-__global__ void __launch_bounds__(Cfg::T, 1)
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_ntt_fwd(const uint64_t *in, uint64_t *out, const LimbConst *__restrict__ limbs, uint32_t L,
           uint32_t n_groups)
 {
@@ -63,12 +85,13 @@ k_ntt_fwd(const uint64_t *in, uint64_t *out, const LimbConst *__restrict__ limbs
     fwd_transform<Cfg>(x, sm, lc.tw_f, q, tid);
 
     // canonical residues, stored through shared memory as coalesced 16-byte pairs
-    const uint64_t one_s = lc.one_s;
+    const uint32_t ones = (uint32_t)lc.one_s;
+    const uint64_t nq = 0ull - q;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < C; ++r) {
 #pragma unroll
-        for (int p = 0; p < NP; ++p) sm[p * N + spos<Cfg>(tid * C + r)] = reduce64(x[p][r], q, one_s);
+        for (int p = 0; p < NP; ++p) sm[p * N + spos<Cfg>(tid * C + r)] = canon3(reduce_lazy(x[p][r], ones, nq), q);
     }
     __syncthreads();
 #pragma unroll
@@ -86,7 +109,7 @@ k_ntt_fwd(const uint64_t *in, uint64_t *out, const LimbConst *__restrict__ limbs
 }
 
 template <class Cfg>
-__global__ void __launch_bounds__(Cfg::T, 1)
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_ntt_inv(const uint64_t *in, uint64_t *out, const LimbConst *__restrict__ limbs, uint32_t L,
           uint32_t n_groups)
 {
@@ -96,18 +119,21 @@ k_ntt_inv(const uint64_t *in, uint64_t *out, const LimbConst *__restrict__ limbs
     const uint32_t limb = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
     const LimbConst &lc = limbs[limb];
 
-    uint64_t x[NP][C];
+    // coalesced 16-byte loads into shared memory, then the round-0 layout
+    // (element tid*C + r) out of it
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const ulonglong2 *src =
-            reinterpret_cast<const ulonglong2 *>(in + ((size_t)(grp * NP + p) * L + limb) * N + tid * C);
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(in + ((size_t)(grp * NP + p) * L + limb) * N);
 #pragma unroll
         for (int r = 0; r < C / 2; ++r) {
-            const ulonglong2 v = __ldg(src + r);
-            x[p][2 * r] = v.x;
-            x[p][2 * r + 1] = v.y;
+            const int e = 2 * (tid + r * Cfg::T);
+            const ulonglong2 v = __ldg(src + tid + r * Cfg::T);
+            sm[p * N + spos<Cfg>(e)] = v.x;
+            sm[p * N + spos<Cfg>(e + 1)] = v.y;
         }
     }
+    uint64_t x[NP][C];
+    load_round0<Cfg>(x, sm, tid);
     inv_transform<Cfg>(x, sm, lc, lc.tw_i, tid);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -121,7 +147,7 @@ k_ntt_inv(const uint64_t *in, uint64_t *out, const LimbConst *__restrict__ limbs
 // group = one output and NP of its components; limb-major item order so that
 // consecutive CTAs (consecutive outputs) share weight polynomials in L2.
 template <class Cfg>
-__global__ void __launch_bounds__(Cfg::T, 1)
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_mac_intt(const uint64_t *__restrict__ ct_ntt, const uint64_t *__restrict__ pt_ntt,
            const uint32_t *__restrict__ term_ptr, const uint32_t *__restrict__ terms,
            uint64_t *__restrict__ out, const LimbConst *__restrict__ limbs, uint32_t L,
@@ -135,38 +161,43 @@ k_mac_intt(const uint64_t *__restrict__ ct_ntt, const uint64_t *__restrict__ pt_
     const uint32_t o = grp / CPG;
     const uint32_t comp0 = (grp % CPG) * NP;
     const LimbConst &lc = limbs[limb];
-    const uint64_t q = lc.q, r64 = lc.r64, r64_s = lc.r64_s, one_s = lc.one_s;
+    const uint64_t q = lc.q, nq = 0ull - q, r64 = lc.r64, r64_s = lc.r64_s;
+    const uint32_t ones = (uint32_t)lc.one_s;
     const uint32_t t0 = __ldg(term_ptr + o), t1 = __ldg(term_ptr + o + 1);
 
-    uint64_t x[NP][C];
+    // MAC in the coalesced pair layout: thread tid owns residue pairs
+    // e = 2*(tid + r*T), so each warp-wide 16-byte load covers 512 contiguous
+    // bytes.  Sums go to shared memory in canonical form.
+    const size_t limb_off = (size_t)limb * N;
+#pragma unroll 1
+    for (int r = 0; r < C / 2; ++r) {
+        const int e = 2 * (tid + r * Cfg::T);
+        MacAcc acc[NP][2];
 #pragma unroll
-    for (int cb = 0; cb < C; cb += 4) {
-        uint64_t lo[NP][4], hi[NP][4];
-#pragma unroll
-        for (int p = 0; p < NP; ++p)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) lo[p][i] = hi[p][i] = 0;
+        for (int p = 0; p < NP; ++p) {
+            mac_zero(acc[p][0]);
+            mac_zero(acc[p][1]);
+        }
+#pragma unroll 4
         for (uint32_t t = t0; t < t1; ++t) {
             const uint32_t ci = __ldg(terms + 2 * t), pi = __ldg(terms + 2 * t + 1);
-            const ulonglong2 *wp =
-                reinterpret_cast<const ulonglong2 *>(pt_ntt + ((size_t)pi * L + limb) * N + tid * C + cb);
-            const ulonglong2 w01 = __ldg(wp), w23 = __ldg(wp + 1);
+            const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(pt_ntt + (size_t)pi * L * N + limb_off + e));
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                const ulonglong2 *xp = reinterpret_cast<const ulonglong2 *>(
-                    ct_ntt + (((size_t)ci * 2 + comp0 + p) * L + limb) * N + tid * C + cb);
-                const ulonglong2 x01 = __ldg(xp), x23 = __ldg(xp + 1);
-                mac128(lo[p][0], hi[p][0], x01.x, w01.x);
-                mac128(lo[p][1], hi[p][1], x01.y, w01.y);
-                mac128(lo[p][2], hi[p][2], x23.x, w23.x);
-                mac128(lo[p][3], hi[p][3], x23.y, w23.y);
+                const ulonglong2 xv = __ldg(reinterpret_cast<const ulonglong2 *>(
+                    ct_ntt + ((size_t)ci * 2 + comp0 + p) * L * N + limb_off + e));
+                mac_add(acc[p][0], xv.x, w.x);
+                mac_add(acc[p][1], xv.y, w.y);
             }
         }
 #pragma unroll
-        for (int p = 0; p < NP; ++p)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) x[p][cb + i] = reduce128(lo[p][i], hi[p][i], q, r64, r64_s, one_s);
+        for (int p = 0; p < NP; ++p) {
+            sm[p * N + spos<Cfg>(e)] = mac_reduce(acc[p][0], q, nq, r64, r64_s, ones);
+            sm[p * N + spos<Cfg>(e + 1)] = mac_reduce(acc[p][1], q, nq, r64, r64_s, ones);
+        }
     }
+    uint64_t x[NP][C];
+    load_round0<Cfg>(x, sm, tid);
     inv_transform<Cfg>(x, sm, lc, lc.tw_i, tid);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -178,7 +209,7 @@ k_mac_intt(const uint64_t *__restrict__ ct_ntt, const uint64_t *__restrict__ pt_
 
 // ---------------------------------------------------------------------------
 template <class Cfg>
-__global__ void __launch_bounds__(Cfg::T, 1)
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_product(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ pt_ntt,
           const uint32_t *__restrict__ out_index, uint64_t *out, const LimbConst *__restrict__ limbs,
           uint32_t L, uint32_t n_groups, int accumulate)
@@ -200,20 +231,23 @@ k_product(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ pt_ntt,
 #pragma unroll
         for (int r = 0; r < C; ++r) x[p][r] = __ldg(src + tid + r * T);
     }
-    fwd_transform<Cfg>(x, sm, lc.tw_f, q, tid);  // lazy values < 29 q, contiguous layout
+    fwd_transform<Cfg>(x, sm, lc.tw_f, q, tid);  // lazy values < 57 q, contiguous layout
 
-    const uint64_t r64 = lc.r64, r64_s = lc.r64_s, one_s = lc.one_s;
+    const uint64_t nq = 0ull - q, r64 = lc.r64, r64_s = lc.r64_s;
+    const uint32_t ones = (uint32_t)lc.one_s;
     const ulonglong2 *wp = reinterpret_cast<const ulonglong2 *>(pt_ntt + ((size_t)j * L + limb) * N + tid * C);
 #pragma unroll
     for (int r = 0; r < C / 2; ++r) {
         const ulonglong2 w = __ldg(wp + r);
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-            uint64_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-            mac128(lo0, hi0, x[p][2 * r], w.x);
-            mac128(lo1, hi1, x[p][2 * r + 1], w.y);
-            x[p][2 * r] = reduce128(lo0, hi0, q, r64, r64_s, one_s);
-            x[p][2 * r + 1] = reduce128(lo1, hi1, q, r64, r64_s, one_s);
+            MacAcc a0, a1;
+            mac_zero(a0);
+            mac_zero(a1);
+            mac_add(a0, x[p][2 * r], w.x);       // x < 2^56 (lazy forward output)
+            mac_add(a1, x[p][2 * r + 1], w.y);
+            x[p][2 * r] = mac_reduce(a0, q, nq, r64, r64_s, ones);
+            x[p][2 * r + 1] = mac_reduce(a1, q, nq, r64, r64_s, ones);
         }
     }
     inv_transform<Cfg>(x, sm, lc, lc.tw_i, tid);
@@ -235,40 +269,11 @@ k_product(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ pt_ntt,
     }
 }
 
-// ---------------------------------------------------------------------------
-__global__ void k_lift_int8(const int8_t *__restrict__ packed, uint64_t *__restrict__ out,
-                            const LimbConst *__restrict__ limbs, uint32_t L, uint32_t N, size_t n_polys)
-{
-    const size_t total = n_polys * L * N;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const size_t k = i % N;
-        const size_t l = (i / N) % L;
-        const size_t p = i / ((size_t)N * L);
-        const int v = packed[p * N + k];
-        const uint64_t q = limbs[l].q;
-        out[i] = v >= 0 ? (uint64_t)v : q - (uint64_t)(-v);
-    }
-}
-
-__global__ void k_range_check(const uint64_t *__restrict__ p, const LimbConst *__restrict__ limbs,
-                              uint32_t L, uint32_t N, size_t n_polys, int *flag)
-{
-    const size_t total = n_polys * L * N;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const size_t l = (i / N) % L;
-        if (p[i] >= limbs[l].q) {
-            *flag = 1;
-            return;
-        }
-    }
-}
 
 // ===========================================================================
 // launchers
 // ===========================================================================
-namespace {
+namespace detail {
 
 // one cache bit per (kernel family, launch shape, device)
 template <class Cfg, int KIND, class K>
@@ -287,20 +292,24 @@ hc_status prepare(K kernel, size_t smem)
 }
 
 // kernel names reported by the tracing facility: [kind][log2 N - 12]
-const char *const kKernelNames[4][3] = {
-    {"k_ntt_fwd/N4096", "k_ntt_fwd/N8192", "k_ntt_fwd/N16384"},
-    {"k_ntt_inv/N4096", "k_ntt_inv/N8192", "k_ntt_inv/N16384"},
-    {"k_mac_intt/N4096", "k_mac_intt/N8192", "k_mac_intt/N16384"},
-    {"k_product/N4096", "k_product/N8192", "k_product/N16384"},
-};
+inline const char *kname_of(int kind, int logn)
+{
+    static const char *const names[4][3] = {
+        {"k_ntt_fwd/N4096", "k_ntt_fwd/N8192", "k_ntt_fwd/N16384"},
+        {"k_ntt_inv/N4096", "k_ntt_inv/N8192", "k_ntt_inv/N16384"},
+        {"k_mac_intt/N4096", "k_mac_intt/N8192", "k_mac_intt/N16384"},
+        {"k_product/N4096", "k_product/N8192", "k_product/N16384"},
+    };
+    return names[kind][logn - 12];
+}
 
 template <class Cfg>
 const char *kname(int kind)
 {
-    return kKernelNames[kind][Cfg::LOGN - 12];
+    return kname_of(kind, Cfg::LOGN);
 }
 
-hc_status after_launch(const char *what)
+inline hc_status after_launch(const char *what)
 {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HC_OK : cuda_error(e, what);
@@ -311,7 +320,7 @@ hc_status run_ntt_fwd(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size
 {
     if (n_groups == 0) return HC_OK;
     auto kern = k_ntt_fwd<Cfg>;
-    hc_status st = prepare<Cfg, 0>(kern, Cfg::SMEM_BYTES);
+    hc_status st = prepare<Cfg, KK_FWD>(kern, Cfg::SMEM_BYTES);
     if (st != HC_OK) return st;
     const size_t items = n_groups * ctx->L;
     if (items > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
@@ -325,7 +334,7 @@ hc_status run_ntt_inv(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size
 {
     if (n_groups == 0) return HC_OK;
     auto kern = k_ntt_inv<Cfg>;
-    hc_status st = prepare<Cfg, 1>(kern, Cfg::SMEM_BYTES);
+    hc_status st = prepare<Cfg, KK_INV>(kern, Cfg::SMEM_BYTES);
     if (st != HC_OK) return st;
     const size_t items = n_groups * ctx->L;
     if (items > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
@@ -340,7 +349,7 @@ hc_status run_mac_intt(const hc_ctx *ctx, const uint64_t *ct_ntt, const uint64_t
 {
     if (n_out == 0) return HC_OK;
     auto kern = k_mac_intt<Cfg>;
-    hc_status st = prepare<Cfg, 2>(kern, Cfg::SMEM_BYTES);
+    hc_status st = prepare<Cfg, KK_MAC>(kern, Cfg::SMEM_BYTES);
     if (st != HC_OK) return st;
     const size_t n_groups = n_out * (2 / Cfg::NP);
     const size_t items = n_groups * ctx->L;
@@ -357,7 +366,7 @@ hc_status run_product(const hc_ctx *ctx, const uint64_t *ct, const uint64_t *pt_
 {
     if (n == 0) return HC_OK;
     auto kern = k_product<Cfg>;
-    hc_status st = prepare<Cfg, 3>(kern, Cfg::SMEM_BYTES);
+    hc_status st = prepare<Cfg, KK_PROD>(kern, Cfg::SMEM_BYTES);
     if (st != HC_OK) return st;
     const size_t n_groups = n * (2 / Cfg::NP);
     const size_t items = n_groups * ctx->L;
@@ -368,70 +377,32 @@ hc_status run_product(const hc_ctx *ctx, const uint64_t *ct, const uint64_t *pt_
     return after_launch("k_product");
 }
 
-}  // namespace
+}  // namespace detail
 
-#define HC_DISPATCH_LOGN(ctx, SEL, FN, ...)                                              \
-    switch ((ctx)->logN) {                                                                \
-    case 12: return FN<typename SEL<12>::type>(__VA_ARGS__);                              \
-    case 13: return FN<typename SEL<13>::type>(__VA_ARGS__);                              \
-    case 14: return FN<typename SEL<14>::type>(__VA_ARGS__);                              \
-    default: return set_error(HC_ERR_UNSUPPORTED, "unsupported N = %u", (ctx)->N);       \
+template <int LOGN, int V>
+hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaStream_t s)
+{
+    using Fused = VCfg<LOGN, V, false>;
+    using Single = VCfg<LOGN, V, true>;
+    switch (kind) {
+    case KK_FWD: return detail::run_ntt_fwd<Single>(ctx, a.in, a.out, a.n, s);
+    case KK_INV: return detail::run_ntt_inv<Single>(ctx, a.in, a.out, a.n, s);
+    case KK_FWDCT: return detail::run_ntt_fwd<Fused>(ctx, a.in, a.out, a.n * (2 / Fused::NP), s);
+    case KK_MAC: return detail::run_mac_intt<Fused>(ctx, a.in, a.pt, a.terms, a.out, a.n, s);
+    case KK_PROD: return detail::run_product<Fused>(ctx, a.in, a.pt, a.out_index, a.out, a.n, a.accumulate, s);
+    default: return set_error(HC_ERR_INVALID_ARG, "unknown kernel kind %d", kind);
     }
-
-hc_status launch_ntt_fwd(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_polys, cudaStream_t s)
-{
-    HC_DISPATCH_LOGN(ctx, SingleCfgSel, run_ntt_fwd, ctx, in, out, n_polys, s)
 }
 
-hc_status launch_ntt_inv(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_polys, cudaStream_t s)
+template <int LOGN>
+hc_status launch_n(const hc_ctx *ctx, int kind, int variant, const LaunchArgs &a, cudaStream_t s)
 {
-    HC_DISPATCH_LOGN(ctx, SingleCfgSel, run_ntt_inv, ctx, in, out, n_polys, s)
-}
-
-namespace {
-template <class Cfg>
-hc_status run_ntt_fwd_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_ct, cudaStream_t s)
-{
-    // NP = 2: one CTA per (ciphertext, limb); NP = 1: one per (component, limb)
-    return run_ntt_fwd<Cfg>(ctx, in, out, n_ct * (2 / Cfg::NP), s);
-}
-}  // namespace
-
-hc_status launch_ntt_fwd_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_ct, cudaStream_t s)
-{
-    HC_DISPATCH_LOGN(ctx, FusedCfgSel, run_ntt_fwd_ct, ctx, in, out, n_ct, s)
-}
-
-hc_status launch_mac_intt(const hc_ctx *ctx, const uint64_t *ct_ntt, const uint64_t *pt_ntt, MacTerms terms,
-                          uint64_t *out, size_t n_out, cudaStream_t s)
-{
-    HC_DISPATCH_LOGN(ctx, FusedCfgSel, run_mac_intt, ctx, ct_ntt, pt_ntt, terms, out, n_out, s)
-}
-
-hc_status launch_product(const hc_ctx *ctx, const uint64_t *ct, const uint64_t *pt_ntt, const uint32_t *out_index,
-                         uint64_t *out, size_t n, bool accumulate, cudaStream_t s)
-{
-    HC_DISPATCH_LOGN(ctx, FusedCfgSel, run_product, ctx, ct, pt_ntt, out_index, out, n, accumulate, s)
-}
-
-hc_status launch_lift_int8(const hc_ctx *ctx, const int8_t *packed, uint64_t *out, size_t n_polys, cudaStream_t s)
-{
-    if (n_polys == 0) return HC_OK;
-    const size_t total = n_polys * ctx->L * ctx->N;
-    const unsigned blocks = (unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
-    ProfileScope ps("k_lift_int8", s);
-    k_lift_int8<<<blocks, 256, 0, s>>>(packed, out, ctx->d_limbs, ctx->L, ctx->N, n_polys);
-    return after_launch("k_lift_int8");
-}
-
-hc_status launch_range_check(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, int *flag, cudaStream_t s)
-{
-    if (n_polys == 0) return HC_OK;
-    const size_t total = n_polys * ctx->L * ctx->N;
-    const unsigned blocks = (unsigned)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
-    ProfileScope ps("k_range_check", s);
-    k_range_check<<<blocks, 256, 0, s>>>(p, ctx->d_limbs, ctx->L, ctx->N, n_polys, flag);
-    return after_launch("k_range_check");
+    switch (variant) {
+    case 0: return launch_variant<LOGN, 0>(ctx, kind, a, s);
+    case 1: return launch_variant<LOGN, 1>(ctx, kind, a, s);
+    case 2: return launch_variant<LOGN, 2>(ctx, kind, a, s);
+    default: return set_error(HC_ERR_INVALID_ARG, "unknown launch variant %d", variant);
+    }
 }
 
 }  // namespace hc

@@ -14,11 +14,12 @@
 // N / 2^(s+1) groups, group i uses psi^-rev(N/2^(s+1) + i); N^-1 is merged
 // into the last stage.
 //
-// Lazy bounds (q < 2^50, N <= 2^14):
-//   forward: inputs < q; each stage adds 2q  -> outputs < (2 log2 N + 1) q < 2^55
-//   inverse: inputs < q; stage s inputs < 2^s q, X - Y + 2^s q < 2^(s+1) q <= 2^64;
-//            the last stage's Shoup steps and one correction give canonical output.
-//
+// Lazy bounds (q < 2^50, N <= 2^14; shoup_lazy returns values < 4q):
+//   forward: inputs < q; each stage adds 4q -> outputs < (4 log2 N + 1) q < 2^56
+//   inverse: inputs < q; stage 0 corrects its products to < 2q, so stage-s
+//            inputs are < 2^s q and X - Y + 2^s q < 2^(s+1) q <= 2^64; the last
+//            stage's Shoup steps (N^-1 merged) and two corrections give
+//            canonical output.
 // Shared-memory layout: element e of polynomial p lives at word
 // p * N + (e ^ ((e >> LOGC) & 15)); the XOR swizzle makes every 8-byte
 // access pattern below conflict-free (the 16 threads of each half-warp touch
@@ -32,11 +33,12 @@
 
 namespace hc {
 
-template <int LOGN_, int LOGC_, int NP_>
+template <int LOGN_, int LOGC_, int NP_, int MINB_ = 1>
 struct NttCfg {
     static constexpr int LOGN = LOGN_;
     static constexpr int LOGC = LOGC_;
     static constexpr int NP = NP_;
+    static constexpr int MINB = MINB_;  // CTAs per SM the register budget is sized for
     static constexpr int N = 1 << LOGN;
     static constexpr int C = 1 << LOGC;
     static constexpr int T = N / C;
@@ -102,7 +104,7 @@ __device__ __forceinline__ void fwd_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
 {
     using RS = RoundShape<Cfg, R>;
     constexpr int half = RS::KK >> (SIG + 1);
-    const uint64_t q2 = 2 * q;
+    const uint64_t nq = 0ull - q, q4 = 4 * q;
 #pragma unroll
     for (int lam = 0; lam < (1 << SIG); ++lam) {
         const ulonglong2 w = __ldg(tw + (1 << (RS::S0 + SIG)) + (g0 << SIG) + lam);
@@ -112,9 +114,9 @@ __device__ __forceinline__ void fwd_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
 #pragma unroll
             for (int p = 0; p < Cfg::NP; ++p) {
                 const uint64_t X = x[p][j];
-                const uint64_t t = shoup_mul(x[p][j + half], w.x, w.y, q);
+                const uint64_t t = shoup_lazy(x[p][j + half], w.x, w.y, nq);  // < 4q
                 x[p][j] = X + t;
-                x[p][j + half] = X - t + q2;
+                x[p][j + half] = X - t + q4;
             }
         }
     }
@@ -142,8 +144,8 @@ __device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
     constexpr int s = RS::S0 + SIG;  // global stage
     constexpr int dist = 1 << SIG;
     constexpr int ngrp = RS::KK >> (SIG + 1);
-    const uint64_t q = lc.q;
-    const uint64_t qs = q << s;
+    const uint64_t q = lc.q, nq = 0ull - q;
+    const uint64_t qs = q << s;       // bound of the stage's inputs
     if constexpr (s == Cfg::LOGN - 1) {
         // last stage: N^-1 merged into both outputs, canonical result
 #pragma unroll
@@ -154,10 +156,8 @@ __device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
 #pragma unroll
                 for (int p = 0; p < Cfg::NP; ++p) {
                     const uint64_t X = x[p][j], Y = x[p][j + dist];
-                    const uint64_t a = shoup_mul(X + Y, lc.ninv, lc.ninv_s, q);
-                    const uint64_t b = shoup_mul(X - Y + qs, lc.ninvw, lc.ninvw_s, q);
-                    x[p][j] = csub(a, q);
-                    x[p][j + dist] = csub(b, q);
+                    x[p][j] = canon4(shoup_lazy(X + Y, lc.ninv, lc.ninv_s, nq), q);
+                    x[p][j + dist] = canon4(shoup_lazy(X - Y + qs, lc.ninvw, lc.ninvw_s, nq), q);
                 }
             }
         }
@@ -172,7 +172,8 @@ __device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
                 for (int p = 0; p < Cfg::NP; ++p) {
                     const uint64_t X = x[p][j], Y = x[p][j + dist];
                     x[p][j] = X + Y;
-                    x[p][j + dist] = shoup_mul(X - Y + qs, w.x, w.y, q);
+                    const uint64_t t = shoup_lazy(X - Y + qs, w.x, w.y, nq);  // < 4q
+                    x[p][j + dist] = (s == 0) ? csub(t, 2 * q) : t;
                 }
             }
         }

@@ -62,6 +62,7 @@ def test_ctx_validate():
     import sympy
     assert (L.hc_ctx_validate(8192, [comp], T_PLAIN) == L.HC_OK) == sympy.isprime(comp)
     assert L.hc_ctx_validate(8192, [97], T_PLAIN) == L.HC_ERR_BAD_MODULUS       # not 1 mod 2N
+    assert L.hc_ctx_validate(4096, [40961], T_PLAIN) == L.HC_ERR_BAD_MODULUS    # prime, = 1 mod 2N, < 2^32
     assert L.hc_ctx_validate(8192, [1 + 16384 * 5], T_PLAIN) == L.HC_ERR_BAD_MODULUS  # 81921 = 3 * 27307
 
 
@@ -73,7 +74,7 @@ def test_ctx_validate_matches_sympy_on_candidates():
         cand = int(k) * 2 * N + 1
         if cand >= (1 << 50):
             continue
-        want = L.HC_OK if sympy.isprime(cand) else L.HC_ERR_BAD_MODULUS
+        want = L.HC_OK if (sympy.isprime(cand) and cand > (1 << 32)) else L.HC_ERR_BAD_MODULUS
         assert L.hc_ctx_validate(N, [cand], T_PLAIN) == want, cand
 
 

@@ -1,0 +1,99 @@
+"""Every launch-shape variant of every kernel family computes the same bits as
+the oracle: forward / inverse NTT (App. C.1), the fused NTT-domain MAC +
+inverse NTT of a convolution (Sec. 6.2), and the fused standalone product."""
+import numpy as np
+import pytest
+
+from gpu_util import sample_indices, to_dev, to_host
+from oracle import conv, core
+from paper_2506_11586_gb300.inputs import CANONICAL_PRIMES, T_PLAIN, Stream, uniform_residues
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SIZES = [(4096, 2), (8192, 3), (16384, 4)]
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_11586_gb300 import _lib
+    from paper_2506_11586_gb300.build import build
+    build()
+    return _lib
+
+
+@pytest.mark.parametrize("N,nl", SIZES)
+def test_transform_variants(L, N, nl):
+    moduli = CANONICAL_PRIMES[:nl]
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    a = uniform_residues(Stream(7, N), moduli, (3,), N)
+    ks = sample_indices(N, 24, N + 1)
+    psis = [core.min_psi(q, N) for q in moduli]
+    want = [[core.ntt(a[p, li], q, psis[li], ks) for li, q in enumerate(moduli)] for p in range(3)]
+    for v in range(L.N_VARIANTS):
+        L.hc_ctx_set_variant(ctx, L.KIND_NTT_FWD, v)
+        L.hc_ctx_set_variant(ctx, L.KIND_NTT_INV, v)
+        assert L.hc_ctx_get_variant(ctx, L.KIND_NTT_FWD) == v
+        d = to_dev(a)
+        L.hc_ntt_fwd(ctx, d)
+        torch.cuda.synchronize()
+        A = to_host(d).reshape(a.shape)
+        for p in range(3):
+            for li in range(nl):
+                assert np.array_equal(A[p, li][ks], want[p][li]), (v, p, li)
+        L.hc_ntt_inv(ctx, d)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(d).reshape(a.shape), a), v
+
+
+@pytest.mark.parametrize("N,nl", SIZES)
+def test_conv_and_product_variants(L, N, nl):
+    moduli = CANONICAL_PRIMES[:nl]
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    C_, H, W, M = 7, 9, 9, 3
+    s = Stream(8, N)
+    K = s.int8(M * C_ * 9).astype(np.int64).reshape(M, C_, 3, 3)
+    p = conv.canonical_partition(C_, H, W, M, 3, 3, 1, N)
+    ct = uniform_residues(s, moduli, (p.I, 2), N)
+    w = L.hc_weights_preprocess(ctx, L.make_desc(C_, H, W, M, 3, 3, pad=1), K.astype(np.int8))
+    ks = sample_indices(N, 24, 3)
+    want = conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, moduli, ks)
+    d_in = to_dev(ct)
+    out = torch.empty(p.O * 2 * nl * N, dtype=torch.int64, device="cuda")
+    for vm in range(L.N_VARIANTS):
+        for vf in range(L.N_VARIANTS):
+            L.hc_ctx_set_variant(ctx, L.KIND_MAC_INTT, vm)
+            L.hc_ctx_set_variant(ctx, L.KIND_NTT_FWD_CT, vf)
+            out.fill_(-1)
+            L.hc_conv_ct_pt(ctx, w, d_in, out)
+            torch.cuda.synchronize()
+            got = to_host(out).reshape(p.O, 2, nl, N)
+            assert np.array_equal(got[..., ks], want), (vm, vf)
+    # standalone fused products: out[j] = ct[j] * pt[j]
+    n = 5
+    pc = uniform_residues(Stream(9, N), moduli, (n, 2), N)
+    pt = uniform_residues(Stream(10, N), moduli, (n,), N)
+    want_p = np.zeros((n, 2, nl, len(ks)), dtype=np.uint64)
+    for j in range(n):
+        for c in range(2):
+            for li, q in enumerate(moduli):
+                want_p[j, c, li] = core.negacyclic(pc[j, c, li], pt[j, li], q, ks)
+    ptn = to_dev(pt)
+    L.hc_ntt_fwd(ctx, ptn)
+    po = torch.empty(n * 2 * nl * N, dtype=torch.int64, device="cuda")
+    for v in range(L.N_VARIANTS):
+        L.hc_ctx_set_variant(ctx, L.KIND_PRODUCT, v)
+        po.fill_(-1)
+        L.hc_ctpt_mac(ctx, to_dev(pc), ptn, np.arange(n), po)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(po).reshape(n, 2, nl, N)[..., ks], want_p), v
+
+
+def test_variant_argument_errors(L):
+    ctx = L.hc_ctx_create(4096, CANONICAL_PRIMES[:1], T_PLAIN)
+    with pytest.raises(L.HcError):
+        L.hc_ctx_set_variant(ctx, 99, 0)
+    with pytest.raises(L.HcError):
+        L.hc_ctx_set_variant(ctx, L.KIND_MAC_INTT, L.N_VARIANTS)
