@@ -65,6 +65,41 @@ def alg_bytes(geo, N, L):
     return 8 * N * L * (2 * geo["I"] + geo["P"] + 2 * geo["O"])
 
 
+# Integer-pipe cost model (measured on GB300 with ncu counters): the fmaheavy
+# pipe runs 64 32-bit multiply-adds per clock per SM; a 32x32->64 multiply
+# (mad.wide.u32) occupies it twice as long.  In these units a lazy Shoup
+# multiplication (5 wide + 4 narrow) costs 14, a MAC term (4 wide) 8 and the
+# final reduction of a MAC sum (one Shoup + one w=1 reduction) 19.
+IMAD_EQ_BUTTERFLY, IMAD_EQ_MAC_TERM, IMAD_EQ_REDUCE = 14, 8, 19
+
+
+def alu_peak_imad_eq():
+    """T IMAD-equivalents/s: 64 per clock per SM at the maximum SM clock."""
+    mhz, sms = 2070.0, 152
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return 64 * sms * mhz * 1e6 / 1e12
+
+
+def kernel_work(name, geo, N, L):
+    """Algorithmic bytes and IMAD-equivalents of one launch of a kernel of the layer."""
+    logn = N.bit_length() - 1
+    bfly = (N // 2) * logn
+    poly = 8 * N * L
+    I, P, O, prods = geo["I"], geo["P"], geo["O"], geo["products"]
+    mac = prods * 2 * L * N * IMAD_EQ_MAC_TERM + O * 2 * L * N * IMAD_EQ_REDUCE
+    if name.startswith("k_ntt_fwd"):
+        return {"bytes": 2 * poly * 2 * I, "imad_eq": 2 * I * L * bfly * IMAD_EQ_BUTTERFLY}
+    if name.startswith("k_ntt_inv"):
+        return {"bytes": 2 * poly * 2 * O, "imad_eq": 2 * O * L * bfly * IMAD_EQ_BUTTERFLY}
+    if name.startswith("k_mac_conv"):
+        return {"bytes": poly * (2 * I + P + 2 * O), "imad_eq": mac}
+    # fused MAC + inverse NTT
+    return {"bytes": poly * (2 * I + P + 2 * O), "imad_eq": mac + 2 * O * L * bfly * IMAD_EQ_BUTTERFLY}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -268,19 +303,28 @@ def run_gb300(args):
     max_total_ms = replicas.reduce_max(total_ms)
     value = replicas.whole_job_throughput(geo["products"] * args.steps, world, max_total_ms / 1000.0)
 
-    # dominant kernel: the fused MAC + inverse NTT
-    kname = "k_mac_intt/N%d" % N
+    # roofline of the dominant kernel (largest share of device time in the trace)
     launches = sum(v[0] for v in prof.values())
-    kl, kms = prof.get(kname, (0, 0.0))
-    k_avg_ms = kms / kl if kl else float("nan")
+    kname = max(prof, key=lambda k: prof[k][1])
+    kl, kms = prof[kname]
+    k_avg_ms = kms / kl
+    work = kernel_work(kname, geo, N, nl)
     bytes_layer = alg_bytes(geo, N, nl)
     hbm_peak, peak_kind = measured_peaks()
-    achieved = bytes_layer / (k_avg_ms / 1000.0) / 1e9 if kl else None
+    alu_peak = alu_peak_imad_eq()
+    hbm_achieved = work["bytes"] / (k_avg_ms / 1000.0) / 1e9
+    alu_achieved = work["imad_eq"] / (k_avg_ms / 1000.0) / 1e12
+    hbm_frac, alu_frac = hbm_achieved / hbm_peak, alu_achieved / alu_peak
     traffic = committed_traffic(kname)
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
-                "peak_source": peak_kind, "alg_bytes_per_launch": bytes_layer,
-                "kernel_ms": k_avg_ms, "kernel_share": kms / total_ms if total_ms else None}
+    if alu_frac >= hbm_frac:
+        roofline = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "T IMAD-eq/s",
+                    "frac": alu_frac}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac}
+    roofline.update({"kernel": kname, "traffic": traffic, "hbm_gbs": hbm_achieved, "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": hbm_frac, "hbm_peak_source": peak_kind, "alu_frac": alu_frac,
+                     "alg_bytes_per_launch": work["bytes"], "alg_imad_eq_per_launch": work["imad_eq"],
+                     "kernel_ms": k_avg_ms, "kernel_share": kms / total_ms if total_ms else None})
     layer_gbs = bytes_layer * args.steps / (total_ms / 1000.0) / 1e9
 
     # plain one-launch-per-product path on the same inputs (comparison)

@@ -86,13 +86,21 @@ hc_status hc_ctx_info(const hc_ctx *ctx, uint32_t *N, uint32_t *L, uint64_t *t,
 /* Launch-shape tuning (no counterpart in the paper: a GPU scheduling knob).
  * Kernel families (kind): 0 forward NTT, 1 inverse NTT, 2 fused NTT-domain
  * MAC + inverse NTT, 3 fused standalone product, 4 forward NTT of whole
- * ciphertexts.  variant (0..2) selects the radix per register round, the
+ * ciphertexts, 5 inverse NTT of whole ciphertexts.  variant (0..2) selects the radix per register round, the
  * polynomials per CTA and the CTAs per SM for the context's N; every variant
  * computes the same bits, only speed differs.  hc_ctx_create picks defaults.
  * Changing a variant while other threads use the context is a data race.
  * Errors: HC_ERR_INVALID_ARG (bad handle, kind or variant). */
 hc_status hc_ctx_set_variant(hc_ctx *ctx, uint32_t kind, uint32_t variant);
 hc_status hc_ctx_get_variant(const hc_ctx *ctx, uint32_t kind, uint32_t *variant);
+
+/* Device-side status of a context's kernels (no counterpart in the paper).
+ * Kernels that wait on asynchronous copies bound every wait; a wait that runs
+ * out records a flag in the context instead of hanging the GPU, and that
+ * kernel's output is then unspecified.  hc_ctx_device_status synchronises
+ * cuda_stream, reads and clears the flag, and returns HC_ERR_TIMEOUT if it was
+ * set (HC_OK otherwise).  hc_conv_ct_pt_host performs this check itself. */
+hc_status hc_ctx_device_status(const hc_ctx *ctx, void *cuda_stream);
 
 /* -------------------------------------------------------------- transforms --
  * Negacyclic NTT over each RNS limb (App. C.1): the point-value form in which

@@ -55,6 +55,7 @@ _SIGS = {
     "hc_ctx_create": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64, C.POINTER(_P)]),
     "hc_ctx_create_ex": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(_P)]),
     "hc_ctx_validate": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64]),
+    "hc_ctx_device_status": (C.c_int, [_P, _P]),
     "hc_ctx_set_variant": (C.c_int, [_P, C.c_uint32, C.c_uint32]),
     "hc_ctx_get_variant": (C.c_int, [_P, C.c_uint32, C.POINTER(C.c_uint32)]),
     "hc_ctx_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), _P, _P]),
@@ -178,8 +179,13 @@ def hc_ctx_create(N, moduli, t, flags=0):
     return Ctx(out, N, [int(x) for x in m], t)
 
 
-KIND_NTT_FWD, KIND_NTT_INV, KIND_MAC_INTT, KIND_PRODUCT, KIND_NTT_FWD_CT = range(5)
+KIND_NTT_FWD, KIND_NTT_INV, KIND_MAC_INTT, KIND_PRODUCT, KIND_NTT_FWD_CT, KIND_NTT_INV_CT = range(6)
 N_VARIANTS = 3
+
+
+def hc_ctx_device_status(ctx, stream=None):
+    """Synchronise the stream; raise HcError(HC_ERR_TIMEOUT) if a bounded device wait ran out."""
+    _check(lib().hc_ctx_device_status(ctx.ptr, _stream(stream)))
 
 
 def hc_ctx_set_variant(ctx, kind, variant):

@@ -136,6 +136,17 @@ struct ScratchGuard {
 }  // namespace
 
 namespace hc {
+hc_status conv_layer(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out,
+                     uint64_t *scratch, cudaStream_t s)
+{
+    hc_status st = launch_ntt_fwd_ct(ctx, d_in, scratch, w->I, s);
+    if (st != HC_OK) return st;
+    st = launch_mac_conv(ctx, scratch, w->d_pt, d_out, w->G, w->B, w->desc.M, s);
+    if (st == HC_OK) return launch_ntt_inv_ct(ctx, d_out, d_out, w->O, s);
+    if (st != HC_ERR_UNSUPPORTED) return st;
+    return launch_mac_intt(ctx, scratch, w->d_pt, MacTerms{w->d_term_ptr, w->d_terms}, d_out, w->O, s);
+}
+
 // checked mode: HC_ERR_RANGE if any residue of [n][L][N] is >= its q_i (synchronises s)
 hc_status check_inputs(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cudaStream_t s)
 {
@@ -289,6 +300,22 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
 hc_status hc_ctx_create(uint32_t N, const uint64_t *moduli, uint32_t L, uint64_t t, hc_ctx **out)
 {
     return hc_ctx_create_ex(N, moduli, L, t, 0, out);
+}
+
+hc_status hc_ctx_device_status(const hc_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    int h = 0;
+    HC_CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+        HC_CUDA_TRY(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
+        HC_CUDA_TRY(cudaStreamSynchronize(s));
+        return set_error(HC_ERR_TIMEOUT, "a bounded device-side wait expired (code %d)", h);
+    }
+    return HC_OK;
 }
 
 hc_status hc_ctx_set_variant(hc_ctx *ctx, uint32_t kind, uint32_t variant)
@@ -471,9 +498,7 @@ hc_status hc_conv_ct_pt(const hc_ctx *ctx, const hc_weights *w, const uint64_t *
     scratch.p = dev_alloc((size_t)w->I * 2 * ctx->L * ctx->N * sizeof(uint64_t), s);
     if (!scratch.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
     uint64_t *ct_ntt = (uint64_t *)scratch.p;
-    st = launch_ntt_fwd_ct(ctx, d_ct_in, ct_ntt, w->I, s);
-    if (st != HC_OK) return st;
-    return launch_mac_intt(ctx, ct_ntt, w->d_pt, MacTerms{w->d_term_ptr, w->d_terms}, d_ct_out, w->O, s);
+    return conv_layer(ctx, w, d_ct_in, d_ct_out, ct_ntt, s);
 }
 
 hc_status hc_conv_ct_pt_plain(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in, uint64_t *d_ct_out,
@@ -516,8 +541,7 @@ hc_status hc_conv_ct_pt_host(const hc_ctx *ctx, const hc_weights *w, const uint6
     hc_status st = hc_conv_ct_pt(ctx, w, (const uint64_t *)din.p, (uint64_t *)dout.p, cuda_stream);
     if (st != HC_OK) return st;
     HC_CUDA_TRY(cudaMemcpyAsync(h_ct_out, dout.p, w->O * ct_bytes, cudaMemcpyDeviceToHost, s));
-    HC_CUDA_TRY(cudaStreamSynchronize(s));
-    return HC_OK;
+    return hc_ctx_device_status(ctx, cuda_stream);
 }
 
 hc_status hc_ctpt_mac(const hc_ctx *ctx, const uint64_t *d_ct, const uint64_t *d_pt_ntt, const uint32_t *h_slot,

@@ -135,6 +135,19 @@ __device__ __forceinline__ void mac_add(MacAcc &a, uint64_t x, uint64_t w)
         : "l"(x), "l"(w));
 }
 
+// a += b (same representation; the s0 carry is counted in c0)
+__device__ __forceinline__ void mac_merge(MacAcc &a, const MacAcc &b)
+{
+    asm("{\n\t"
+        "add.cc.u64 %0, %0, %4;\n\t"
+        "addc.u32 %3, %3, %7;\n\t"
+        "add.u64 %1, %1, %5;\n\t"
+        "add.u64 %2, %2, %6;\n\t"
+        "}"
+        : "+l"(a.s0), "+l"(a.s1), "+l"(a.s2), "+r"(a.c0)
+        : "l"(b.s0), "l"(b.s1), "l"(b.s2), "r"(b.c0));
+}
+
 // canonical V mod q.  r64 = 2^64 mod q with companion r64_s.
 __device__ __forceinline__ uint64_t mac_reduce(const MacAcc &a, uint64_t q, uint64_t nq, uint64_t r64,
                                                uint64_t r64_s, uint32_t ones)

@@ -33,7 +33,7 @@ struct LimbConst {
 static_assert(sizeof(LimbConst) == 128, "LimbConst is 128 bytes");
 
 // Kernel families whose launch shape is selectable per context.
-enum KernelKind { KK_FWD = 0, KK_INV = 1, KK_MAC = 2, KK_PROD = 3, KK_FWDCT = 4, KK_COUNT = 5 };
+enum KernelKind { KK_FWD = 0, KK_INV = 1, KK_MAC = 2, KK_PROD = 3, KK_FWDCT = 4, KK_INVCT = 5, KK_COUNT = 6 };
 constexpr int kNumVariants = 3;
 
 }  // namespace hc
@@ -141,6 +141,11 @@ hc_status launch_ntt_fwd(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, s
                          cudaStream_t s);
 hc_status launch_ntt_inv(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_polys,
                          cudaStream_t s);
+// inverse NTT of n_ct ciphertexts [n][2][L][N] (canonical NTT domain in, coefficients out)
+hc_status launch_ntt_inv_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_ct, cudaStream_t s);
+// conv MAC blocked over coefficient chunks: Y[m*B+b] = sum_g W[m*G+g] . X[g*B+b] (NTT domain)
+hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64_t *w_ntt, uint64_t *y,
+                          uint32_t G, uint32_t B, uint32_t M, cudaStream_t s);
 // forward NTT of n_ct ciphertexts [n][2][L][N] into out (both components per CTA)
 hc_status launch_ntt_fwd_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_ct,
                             cudaStream_t s);
@@ -157,6 +162,13 @@ hc_status launch_lift_int8(const hc_ctx *ctx, const int8_t *packed, uint64_t *ou
 // checked mode: set *flag if any of count residues of [n][L][N] is >= its q
 hc_status launch_range_check(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, int *flag,
                              cudaStream_t s);
+
+// one convolution layer on the device (Sec. 6.2): NTT of the inputs into
+// scratch ([I][2][L][N]), NTT-domain MAC into d_out, inverse NTT of d_out in
+// place; falls back to the fused MAC + inverse NTT kernel for layers whose
+// input chunk does not fit the blocked MAC's shared memory
+hc_status conv_layer(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out,
+                     uint64_t *scratch, cudaStream_t s);
 
 // checked mode only: HC_ERR_RANGE if a residue is >= its q_i (synchronises s); HC_OK otherwise
 hc_status check_inputs(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cudaStream_t s);

@@ -388,6 +388,7 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
     case KK_FWD: return detail::run_ntt_fwd<Single>(ctx, a.in, a.out, a.n, s);
     case KK_INV: return detail::run_ntt_inv<Single>(ctx, a.in, a.out, a.n, s);
     case KK_FWDCT: return detail::run_ntt_fwd<Fused>(ctx, a.in, a.out, a.n * (2 / Fused::NP), s);
+    case KK_INVCT: return detail::run_ntt_inv<Fused>(ctx, a.in, a.out, a.n * (2 / Fused::NP), s);
     case KK_MAC: return detail::run_mac_intt<Fused>(ctx, a.in, a.pt, a.terms, a.out, a.n, s);
     case KK_PROD: return detail::run_product<Fused>(ctx, a.in, a.pt, a.out_index, a.out, a.n, a.accumulate, s);
     default: return set_error(HC_ERR_INVALID_ARG, "unknown kernel kind %d", kind);

@@ -1,9 +1,20 @@
 // hc_launch.cu -- dispatch of the public launchers to the per-N kernel
 // instantiations and the launch variant recorded in the context, plus the
-// small elementwise kernels (weight lifting, range checks).
+// small elementwise kernels (weight lifting, range checks) and the blocked
+// convolution MAC.
+#include <atomic>
+
+#include "hc_arith.cuh"
+#include "hc_async.cuh"
 #include "hc_internal.h"
 
 namespace hc {
+
+static hc_status after_launch_status(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HC_OK : cuda_error(e, what);
+}
 
 // ---------------------------------------------------------------------------
 __global__ void k_lift_int8(const int8_t *__restrict__ packed, uint64_t *__restrict__ out,
@@ -41,6 +52,137 @@ int default_variant(int kind, uint32_t logn)
     (void)kind;
     (void)logn;
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Convolution MAC in the NTT domain, blocked over coefficient chunks (Sec. 6.2):
+//   Y[m*B+b][c] = sum_g W[m*G+g] . X[g*B+b][c]      (slot-wise, mod q_limb)
+// A CTA owns one chunk of KC slots of one limb for every input ciphertext and
+// a group of MB output channels.  The input chunk (G*2B rows of KC slots) is
+// fetched once into shared memory by TMA bulk copies; the weight slices
+// (G rows of KC slots per channel) stream through a ring of kMacStages
+// shared-memory stages, fetched two channels ahead of the compute.  Each
+// weight slot is therefore read from memory once and each input slot once
+// per channel group.  Thread (k, h) owns slot k0 + k and the component pairs
+// p = 2b + c with p = h (mod H).  Waits are bounded: a wait that runs out sets
+// err = 2, drains this CTA's copies in flight (bounded) and ends the CTA.
+constexpr int kMacThreads = 256;
+constexpr int kMacStages = 3;
+
+template <int KC>
+__global__ void __launch_bounds__(kMacThreads)
+k_mac_conv(const uint64_t *__restrict__ X, const uint64_t *__restrict__ W, uint64_t *__restrict__ Y,
+           const LimbConst *__restrict__ limbs, uint32_t N, uint32_t L, uint32_t G, uint32_t B, uint32_t M,
+           uint32_t MB, int *err)
+{
+    constexpr int H = kMacThreads / KC;
+    constexpr uint32_t ROW_BYTES = KC * sizeof(uint64_t);
+    __shared__ __align__(8) uint64_t bars[1 + kMacStages];
+    extern __shared__ __align__(16) uint64_t dsm[];
+    const uint32_t P = 2 * B, rows = G * P;
+    uint64_t *xs = dsm;                          // [rows][KC]
+    uint64_t *ws = dsm + (size_t)rows * KC;      // [kMacStages][G][KC]
+    const uint32_t k0 = blockIdx.x * KC, limb = blockIdx.y;
+    const uint32_t m0 = blockIdx.z * MB, m1 = min(M, m0 + MB);
+    const uint32_t nm = m1 > m0 ? m1 - m0 : 0;
+    const size_t LN = (size_t)L * N;
+    const uint64_t *xsrc = X + (size_t)limb * N + k0;   // input row r at xsrc + r*LN
+    const uint64_t *wsrc = W + (size_t)limb * N + k0;   // weight poly j at wsrc + j*LN
+    const int tid = threadIdx.x;
+
+    auto issue_w = [&](uint32_t i) {  // weight slice of channel m0 + i into stage i % kMacStages
+        const uint32_t st = i % kMacStages;
+        mbar_arrive_expect_tx(&bars[1 + st], G * ROW_BYTES);
+        const uint64_t *src = wsrc + (size_t)(m0 + i) * G * LN;
+        for (uint32_t g = 0; g < G; ++g) bulk_g2s(ws + ((size_t)st * G + g) * KC, src + g * LN, ROW_BYTES, &bars[1 + st]);
+    };
+    if (tid == 0) {
+        for (int i = 0; i < 1 + kMacStages; ++i) mbar_init(&bars[i], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bars[0], rows * ROW_BYTES);
+        for (uint32_t r = 0; r < rows; ++r) bulk_g2s(xs + (size_t)r * KC, xsrc + r * LN, ROW_BYTES, &bars[0]);
+        for (uint32_t i = 0; i < (uint32_t)kMacStages && i < nm; ++i) issue_w(i);
+    }
+
+    const LimbConst &lc = limbs[limb];
+    const uint64_t q = lc.q, nq = 0ull - q, r64 = lc.r64, r64_s = lc.r64_s;
+    const uint32_t ones = (uint32_t)lc.one_s;
+    const uint32_t k = tid % KC, h = tid / KC;  // h is warp-uniform
+    bool ok = mbar_wait(&bars[0], 0);
+    uint32_t i = 0;
+    for (; i < nm; ++i) {
+        const uint32_t st = i % kMacStages;
+        ok = mbar_wait(&bars[1 + st], (i / kMacStages) & 1) && ok;
+        ok = __syncthreads_and(ok);  // also: every thread has finished channel i - 1
+        if (!ok) break;
+        if (tid == 0 && i >= 1 && i - 1 + kMacStages < nm) {
+            fence_proxy_async();
+            issue_w(i - 1 + kMacStages);  // into the stage channel i - 1 used
+        }
+        const uint64_t *wk = ws + (size_t)st * G * KC + k;
+        uint64_t *yk = Y + (size_t)limb * N + k0 + k + (size_t)(m0 + i) * P * LN;
+        for (uint32_t p = h; p < P; p += H) {
+            MacAcc acc0, acc1;  // two chains over alternating terms for latency hiding
+            mac_zero(acc0);
+            mac_zero(acc1);
+            const uint64_t *xp = xs + (size_t)p * KC + k;
+            const uint32_t xstep = P * KC;
+            uint32_t g = 0;
+            for (; g + 1 < G; g += 2) {
+                mac_add(acc0, xp[0], wk[g * KC]);
+                mac_add(acc1, xp[xstep], wk[(g + 1) * KC]);
+                xp += 2 * xstep;
+            }
+            if (g < G) mac_add(acc0, xp[0], wk[g * KC]);
+            mac_merge(acc0, acc1);
+            yk[(size_t)p * LN] = mac_reduce(acc0, q, nq, r64, r64_s, ones);
+        }
+    }
+    if (!ok && tid == 0) {
+        atomicExch(err, 2);
+        // drain this CTA's bulk copies still in flight before its shared memory is released
+        mbar_wait(&bars[0], 0);
+        const uint32_t last = i == 0 ? min(nm, (uint32_t)kMacStages) : min(nm, i - 1 + kMacStages);
+        for (uint32_t j = i; j < last; ++j) mbar_wait(&bars[1 + j % kMacStages], (j / kMacStages) & 1);
+    }
+}
+
+template <int KC>
+static hc_status run_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64_t *w_ntt, uint64_t *y,
+                              uint32_t G, uint32_t B, uint32_t M, cudaStream_t s)
+{
+    const size_t smem = ((size_t)G * 2 * B + (size_t)kMacStages * G) * KC * sizeof(uint64_t);
+    static std::atomic<uint32_t> attr_done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(attr_done.load() & (1u << (dev & 31)))) {
+        cudaError_t e = cudaFuncSetAttribute(k_mac_conv<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_mac_conv)");
+        attr_done.fetch_or(1u << (dev & 31));
+    }
+    // enough CTAs for about four waves: split the output channels into groups of MB
+    const uint32_t per_sm = (uint32_t)((200 * 1024) / smem) < 4 ? (uint32_t)((200 * 1024) / smem) : 4;
+    const uint32_t chunks = ctx->N / KC;
+    const uint32_t target = 152 * (per_sm ? per_sm : 1) * 4;
+    const uint32_t want = (target + chunks * ctx->L - 1) / (chunks * ctx->L);
+    const uint32_t groups = want < 1 ? 1 : (want > M ? M : want);
+    const uint32_t MB = (M + groups - 1) / groups;
+    const dim3 grid(chunks, ctx->L, (M + MB - 1) / MB);
+    ProfileScope ps("k_mac_conv", s);
+    k_mac_conv<KC><<<grid, kMacThreads, smem, s>>>(x_ntt, w_ntt, y, ctx->d_limbs, ctx->N, ctx->L, G, B, M, MB,
+                                                   ctx->d_flag + 1);
+    return after_launch_status("k_mac_conv");
+}
+
+hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64_t *w_ntt, uint64_t *y, uint32_t G,
+                          uint32_t B, uint32_t M, cudaStream_t s)
+{
+    const size_t rows = (size_t)G * 2 * B + (size_t)kMacStages * G;
+    if (rows * 64 * sizeof(uint64_t) > 200 * 1024) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
+    return run_mac_conv<64>(ctx, x_ntt, w_ntt, y, G, B, M, s);
 }
 
 namespace {
@@ -89,6 +231,15 @@ hc_status launch_ntt_fwd_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out
     a.out = out;
     a.n = n_ct;
     return dispatch(ctx, KK_FWDCT, a, s);
+}
+
+hc_status launch_ntt_inv_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_ct, cudaStream_t s)
+{
+    LaunchArgs a{};
+    a.in = in;
+    a.out = out;
+    a.n = n_ct;
+    return dispatch(ctx, KK_INVCT, a, s);
 }
 
 hc_status launch_mac_intt(const hc_ctx *ctx, const uint64_t *ct_ntt, const uint64_t *pt_ntt, MacTerms terms,

@@ -63,9 +63,7 @@ extern "C" hc_status hc_conv_ct_pt_noalloc(const hc_ctx *ctx, const hc_weights *
     if (st != HC_OK) return st;
     st = check_inputs(ctx, d_ct_in, (size_t)2 * w->I, s);
     if (st != HC_OK) return st;
-    // the forward NTT overwrites every scratch word the MAC reads, so nothing
-    // left over from an earlier call is ever used
-    st = launch_ntt_fwd_ct(ctx, d_ct_in, scratch, w->I, s);
-    if (st != HC_OK) return st;
-    return launch_mac_intt(ctx, scratch, w->d_pt, MacTerms{w->d_term_ptr, w->d_terms}, d_ct_out, w->O, s);
+    // the forward NTT overwrites every scratch word the later phases read, so
+    // nothing left over from an earlier call is ever used
+    return conv_layer(ctx, w, d_ct_in, d_ct_out, scratch, s);
 }

@@ -124,6 +124,7 @@ def test_layer_56x56x64_parity(L, layer_56x56x64):
     d_in = to_dev(ct)
     d_out = torch.empty(p.O * 2 * 3 * p.N, dtype=torch.int64, device="cuda")
     L.hc_conv_ct_pt(ctx, w, d_in, d_out)
+    L.hc_ctx_device_status(ctx)          # no bounded device wait ran out
     torch.cuda.synchronize()
     got = to_host(d_out).reshape(p.O, 2, 3, p.N)
     # sampled coefficients of every output polynomial vs the schoolbook conv
