@@ -233,6 +233,76 @@ hc_status hc_ctpt_mac(const hc_ctx *ctx, const uint64_t *d_ct, const uint64_t *d
                       const uint32_t *h_slot, size_t n, uint64_t *d_out, size_t n_out,
                       void *cuda_stream);
 
+/* ------------------------------------------------------------------ plans --
+ * Batching across layers, products and ring degrees (Sec. 6.2; the paper's
+ * closing remarks on accelerating composite HE operations).  A plan binds a
+ * list of independent work items to their buffers once, then runs them all
+ * with as few launches as the work allows:
+ *   - the forward NTTs of every conv item of one ring degree in one launch,
+ *   - the NTT-domain MACs of every conv item in one launch (all degrees),
+ *   - the inverse NTTs of every conv item of one ring degree in one launch,
+ *   - every standalone product of every degree in one persistent launch
+ *     whose CTAs pull (product, limb) units from a global counter.
+ * (At most 48 conv items share one launch; more items take more launches.)
+ * hc_plan_run captures that launch sequence into a CUDA graph the first time
+ * and replays the graph afterwards.  Results are identical, bit for bit, to
+ * running every item alone with hc_conv_ct_pt / hc_ctpt_mac.
+ *
+ * Items are independent: no item's output may overlap another item's input
+ * or output.  An item's output may coincide exactly with its own input
+ * (in place).  The plan keeps the pointers; buffers, contexts and weights
+ * must outlive it.  A plan owns device scratch for the conv items' NTT'd
+ * inputs (sum of I*2*L*N*8 bytes) and its work tables, allocated when it is
+ * created. */
+typedef enum {
+    HC_WORK_CONV = 0,     /* one conv layer: weights, d_ct_in [I][2][L][N], d_ct_out [O][2][L][N] */
+    HC_WORK_PRODUCTS = 1  /* n standalone products: d_ct_out[j] = INTT(NTT(d_ct_in[j]) . d_pt_ntt[j]) */
+} hc_work_kind;
+
+typedef struct {
+    uint32_t kind;              /* hc_work_kind */
+    const hc_ctx *ctx;
+    const hc_weights *weights;  /* HC_WORK_CONV: preprocessed for ctx */
+    const uint64_t *d_ct_in;    /* coefficient domain */
+    const uint64_t *d_pt_ntt;   /* HC_WORK_PRODUCTS: [n][L][N] NTT domain */
+    uint64_t *d_ct_out;         /* coefficient domain, fully overwritten */
+    size_t n;                   /* HC_WORK_PRODUCTS: number of products */
+} hc_work_item;
+
+/* Build a plan over n items (copied).  All contexts must live on the device
+ * that is current at the call.  Errors: HC_ERR_INVALID_ARG (null/invalid
+ * handle or buffer, weights of another context, overlapping items, more than
+ * 2^28 products), HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_plan_create(const hc_work_item *items, size_t n, hc_plan **out);
+
+/* Run the plan on cuda_stream (graph replay after the first run; while
+ * hc_profile_enable is on, the launches are issued directly instead so that
+ * they can be timed).  Checked contexts range-check every input first.
+ * Errors: HC_ERR_RANGE (checked mode), HC_ERR_CUDA, HC_ERR_TIMEOUT (a
+ * bounded device wait expired in an earlier launch). */
+hc_status hc_plan_run(hc_plan *plan, void *cuda_stream);
+
+/* The same results the plain way: one kernel launch per ct x pt product
+ * (forward NTT, slot-wise product, inverse NTT, accumulate), no batching and
+ * no graph.  Comparison path for the batched form. */
+hc_status hc_plan_run_plain(hc_plan *plan, void *cuda_stream);
+
+/* Pick the fastest launch variant of each kernel family the plan uses, per
+ * context, by timing the plan itself (CUDA events on cuda_stream, median of
+ * several runs), and set it in the contexts (hc_ctx_set_variant).  Variants
+ * change speed only, never results.  cache_path (NULL = no cache) names a
+ * text file of earlier choices keyed by GPU, N, L and moduli; cached choices
+ * are applied without timing and new ones are appended.  The plan's outputs
+ * hold unspecified values afterwards.  Errors: as hc_plan_run, plus
+ * HC_ERR_INVALID_ARG (unreadable cache lines are ignored, not errors). */
+hc_status hc_plan_autotune(hc_plan *plan, const char *cache_path, void *cuda_stream);
+
+/* Work in a plan: total ct x pt products, algorithmic HBM bytes of one run
+ * (8*N*L*(2I + P + 2O) per conv item, 8*N*L*5 per product: read the inputs
+ * and weights once, write the outputs once) and the kernel launches of one
+ * batched run.  Any out pointer may be NULL. */
+hc_status hc_plan_info(const hc_plan *plan, uint64_t *n_products, uint64_t *alg_bytes, uint32_t *n_launches);
+
 /* ------------------------------------------------------------- allocation --
  * Device memory used by the library: handles' resident tables and weights,
  * and per-call scratch.  alloc(bytes, stream, user) must return device memory

@@ -609,6 +609,8 @@ void hc_free(void *handle)
         dev_free_persistent(c->d_flag);
         c->magic = kMagicDead;
         delete c;
+    } else if (magic == kMagicPlan) {
+        plan_destroy((hc_plan *)handle);
     } else if (magic == kMagicWeights) {
         hc_weights *w = (hc_weights *)handle;
         DeviceGuard g(w->device);

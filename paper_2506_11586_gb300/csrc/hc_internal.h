@@ -120,8 +120,66 @@ struct MacTerms {
     const uint32_t *terms;     // pairs (ct index, pt index), 2 per term
 };
 
+// one batch of a multi-segment transform launch: n_groups CTAs per limb (in
+// ciphertexts for the *_SEGS kinds), CTAs [cta_begin, cta_begin + n_groups * L)
+struct NttSeg {
+    const uint64_t *in;
+    uint64_t *out;
+    const LimbConst *limbs;
+    uint32_t L, n_groups, cta_begin;
+};
+constexpr int kMaxSegs = 48;
+struct NttSegs {
+    uint32_t n;
+    NttSeg s[kMaxSegs];
+};
+// one layer of a multi-layer blocked-MAC launch (see k_mac_conv)
+struct MacSeg {
+    const uint64_t *X;
+    const uint64_t *W;
+    uint64_t *Y;
+    const LimbConst *limbs;
+    uint32_t N, L, G, B, M, MB, chunks, groups, cta_begin;
+};
+struct MacSegs {
+    uint32_t n;
+    MacSeg s[kMaxSegs];
+};
+struct MacLayer {
+    const uint64_t *x;
+    const uint64_t *w;
+    uint64_t *y;
+    uint32_t G, B, M;
+};
+bool mac_conv_fits(uint32_t G, uint32_t B);
+// blocked MACs of n layers (layer i on ctxs[i]) in ceil(n / kMaxSegs) launches
+hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s);
+
+void plan_destroy(hc_plan *p);
+
+// one standalone product of a mixed-degree batch (see k_product_mixed)
+struct MixItem {
+    const uint64_t *ct;       // [2][L][N] coefficient domain
+    const uint64_t *pt;       // [L][N] NTT domain
+    uint64_t *out;            // [2][L][N] coefficient domain
+    const LimbConst *limbs;
+    uint32_t L, logN;
+};
+// work unit code: item << 4 | limb << 1 | component
+constexpr uint32_t mix_unit(uint32_t item, uint32_t limb, uint32_t comp) { return item << 4 | limb << 1 | comp; }
+// components per unit at ring degree 2^logN (2: both in one unit, 1: one unit per component)
+constexpr uint32_t mix_comps_per_unit(uint32_t logN) { return logN >= 14 ? 1 : 2; }
+// persistent launch over n_units units (sorted by cost, most expensive first);
+// *next must be 0 when the launch starts
+hc_status launch_product_mixed(const MixItem *items, const uint32_t *units, uint32_t n_units, uint32_t *next,
+                               cudaStream_t s);
+
+// transform kinds that take a segment table (pseudo-kinds, variant of FWDCT / INVCT)
+constexpr int KK_FWDCT_SEGS = 100, KK_INVCT_SEGS = 101;
+
 // arguments of one launch of a kernel family (unused fields ignored)
 struct LaunchArgs {
+    const NttSegs *segs;
     const uint64_t *in;
     uint64_t *out;
     const uint64_t *pt;
@@ -143,6 +201,9 @@ hc_status launch_ntt_inv(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, s
                          cudaStream_t s);
 // inverse NTT of n_ct ciphertexts [n][2][L][N] (canonical NTT domain in, coefficients out)
 hc_status launch_ntt_inv_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_ct, cudaStream_t s);
+// multi-segment forward / inverse transforms of ciphertexts (all segments share
+// ctx's N and launch variant; n_groups counts ciphertexts)
+hc_status launch_ntt_ct_segs(const hc_ctx *ctx, const NttSegs &segs, bool inverse, cudaStream_t s);
 // conv MAC blocked over coefficient chunks: Y[m*B+b] = sum_g W[m*G+g] . X[g*B+b] (NTT domain)
 hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64_t *w_ntt, uint64_t *y,
                           uint32_t G, uint32_t B, uint32_t M, cudaStream_t s);

@@ -39,6 +39,14 @@ template <> struct Variant<14, 2> { static constexpr int LOGC = 5, NP = 1, MINB 
 template <int LOGN, int V, bool SINGLE>
 using VCfg = NttCfg<LOGN, Variant<LOGN, V>::LOGC, SINGLE ? 1 : Variant<LOGN, V>::NP, Variant<LOGN, V>::MINB>;
 
+// segment of a multi-segment launch that owns this CTA (segments in CTA order)
+__device__ __forceinline__ const NttSeg &find_seg(const NttSegs &segs)
+{
+    uint32_t i = 0;
+    while (i + 1 < segs.n && blockIdx.x >= segs.s[i + 1].cta_begin) ++i;
+    return segs.s[i];
+}
+
 // ---------------------------------------------------------------------------
 // store the last inverse-round layout: slot r = v*KK + j holds element
 // tid + T*(v + j*SUBS)  (coalesced across the warp)
@@ -65,14 +73,18 @@ __device__ __forceinline__ void load_round0(uint64_t (&x)[Cfg::NP][Cfg::C], cons
 // ---------------------------------------------------------------------------
 template <class Cfg>
 __global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
-k_ntt_fwd(const uint64_t *in, uint64_t *out, const LimbConst *__restrict__ limbs, uint32_t L,
-          uint32_t n_groups)
+k_ntt_fwd(const __grid_constant__ NttSegs segs)
 {
     extern __shared__ uint64_t sm[];
     constexpr int NP = Cfg::NP, C = Cfg::C, T = Cfg::T, N = Cfg::N;
     const int tid = threadIdx.x;
-    const uint32_t limb = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
-    const LimbConst &lc = limbs[limb];
+    const NttSeg &sg = find_seg(segs);
+    const uint64_t *in = sg.in;
+    uint64_t *out = sg.out;
+    const uint32_t L = sg.L, n_groups = sg.n_groups;
+    const uint32_t local = blockIdx.x - sg.cta_begin;
+    const uint32_t limb = local / n_groups, grp = local % n_groups;
+    const LimbConst &lc = sg.limbs[limb];
     const uint64_t q = lc.q;
 
     uint64_t x[NP][C];
@@ -110,14 +122,18 @@ k_ntt_fwd(const uint64_t *in, uint64_t *out, const LimbConst *__restrict__ limbs
 
 template <class Cfg>
 __global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
-k_ntt_inv(const uint64_t *in, uint64_t *out, const LimbConst *__restrict__ limbs, uint32_t L,
-          uint32_t n_groups)
+k_ntt_inv(const __grid_constant__ NttSegs segs)
 {
     extern __shared__ uint64_t sm[];
     constexpr int NP = Cfg::NP, C = Cfg::C, N = Cfg::N;
     const int tid = threadIdx.x;
-    const uint32_t limb = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
-    const LimbConst &lc = limbs[limb];
+    const NttSeg &sg = find_seg(segs);
+    const uint64_t *in = sg.in;
+    uint64_t *out = sg.out;
+    const uint32_t L = sg.L, n_groups = sg.n_groups;
+    const uint32_t local = blockIdx.x - sg.cta_begin;
+    const uint32_t limb = local / n_groups, grp = local % n_groups;
+    const LimbConst &lc = sg.limbs[limb];
 
     // coalesced 16-byte loads into shared memory, then the round-0 layout
     // (element tid*C + r) out of it
@@ -208,26 +224,23 @@ k_mac_intt(const uint64_t *__restrict__ ct_ntt, const uint64_t *__restrict__ pt_
 }
 
 // ---------------------------------------------------------------------------
+// One task of a standalone product: NP components (comp0, comp0 + 1, ...) of
+// one limb.  ct is the product's ciphertext [2][L][N], pt its NTT-domain
+// plaintext [L][N], out its output ciphertext [2][L][N]:
+//   out[c][limb] (+)= INTT(NTT(ct[c][limb]) . pt[limb])                  (App. C.1)
 template <class Cfg>
-__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
-k_product(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ pt_ntt,
-          const uint32_t *__restrict__ out_index, uint64_t *out, const LimbConst *__restrict__ limbs,
-          uint32_t L, uint32_t n_groups, int accumulate)
+__device__ __forceinline__ void product_task(uint64_t *sm, const uint64_t *__restrict__ ct,
+                                             const uint64_t *__restrict__ pt, uint64_t *out, const LimbConst &lc,
+                                             uint32_t L, uint32_t limb, uint32_t comp0, bool accumulate)
 {
-    extern __shared__ uint64_t sm[];
     constexpr int NP = Cfg::NP, C = Cfg::C, T = Cfg::T, N = Cfg::N;
-    constexpr int CPG = 2 / NP;
     const int tid = threadIdx.x;
-    const uint32_t limb = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
-    const uint32_t j = grp / CPG;
-    const uint32_t comp0 = (grp % CPG) * NP;
-    const LimbConst &lc = limbs[limb];
     const uint64_t q = lc.q;
 
     uint64_t x[NP][C];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const uint64_t *src = ct + (((size_t)j * 2 + comp0 + p) * L + limb) * N;
+        const uint64_t *src = ct + ((size_t)(comp0 + p) * L + limb) * N;
 #pragma unroll
         for (int r = 0; r < C; ++r) x[p][r] = __ldg(src + tid + r * T);
     }
@@ -235,7 +248,7 @@ k_product(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ pt_ntt,
 
     const uint64_t nq = 0ull - q, r64 = lc.r64, r64_s = lc.r64_s;
     const uint32_t ones = (uint32_t)lc.one_s;
-    const ulonglong2 *wp = reinterpret_cast<const ulonglong2 *>(pt_ntt + ((size_t)j * L + limb) * N + tid * C);
+    const ulonglong2 *wp = reinterpret_cast<const ulonglong2 *>(pt + (size_t)limb * N + tid * C);
 #pragma unroll
     for (int r = 0; r < C / 2; ++r) {
         const ulonglong2 w = __ldg(wp + r);
@@ -252,10 +265,9 @@ k_product(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ pt_ntt,
     }
     inv_transform<Cfg>(x, sm, lc, lc.tw_i, tid);
 
-    const uint32_t oj = out_index ? __ldg(out_index + j) : j;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        uint64_t *dst = out + (((size_t)oj * 2 + comp0 + p) * L + limb) * N;
+        uint64_t *dst = out + ((size_t)(comp0 + p) * L + limb) * N;
         if (accumulate) {
 #pragma unroll
             for (int r = 0; r < C; ++r) {
@@ -267,6 +279,23 @@ k_product(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ pt_ntt,
             for (int r = 0; r < C; ++r) dst[inv_out_elem<Cfg>(tid, r)] = x[p][r];
         }
     }
+}
+
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
+k_product(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ pt_ntt,
+          const uint32_t *__restrict__ out_index, uint64_t *out, const LimbConst *__restrict__ limbs,
+          uint32_t L, uint32_t n_groups, int accumulate)
+{
+    extern __shared__ uint64_t sm[];
+    constexpr int CPG = 2 / Cfg::NP;
+    constexpr size_t N = Cfg::N;
+    const uint32_t limb = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
+    const uint32_t j = grp / CPG;
+    const uint32_t comp0 = (grp % CPG) * Cfg::NP;
+    const uint32_t oj = out_index ? __ldg(out_index + j) : j;
+    product_task<Cfg>(sm, ct + (size_t)j * 2 * L * N, pt_ntt + (size_t)j * L * N, out + (size_t)oj * 2 * L * N,
+                      limbs[limb], L, limb, comp0, accumulate != 0);
 }
 
 
@@ -315,32 +344,51 @@ inline hc_status after_launch(const char *what)
     return e == cudaSuccess ? HC_OK : cuda_error(e, what);
 }
 
+template <class Cfg, int KIND>
+hc_status run_ntt_segs(const NttSegs &segs, cudaStream_t s, bool inverse)
+{
+    uint32_t items = 0;
+    for (uint32_t i = 0; i < segs.n; ++i) items = segs.s[i].cta_begin + segs.s[i].n_groups * segs.s[i].L;
+    if (items == 0) return HC_OK;
+    if (inverse) {
+        auto kern = k_ntt_inv<Cfg>;
+        hc_status st = prepare<Cfg, KIND>(kern, Cfg::SMEM_BYTES);
+        if (st != HC_OK) return st;
+        ProfileScope ps(kname<Cfg>(KK_INV), s);
+        kern<<<items, Cfg::T, Cfg::SMEM_BYTES, s>>>(segs);
+        return after_launch("k_ntt_inv");
+    }
+    auto kern = k_ntt_fwd<Cfg>;
+    hc_status st = prepare<Cfg, KIND>(kern, Cfg::SMEM_BYTES);
+    if (st != HC_OK) return st;
+    ProfileScope ps(kname<Cfg>(KK_FWD), s);
+    kern<<<items, Cfg::T, Cfg::SMEM_BYTES, s>>>(segs);
+    return after_launch("k_ntt_fwd");
+}
+
+// one-segment launch: n_groups CTAs per limb
+inline NttSegs one_seg(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_groups)
+{
+    NttSegs segs{};
+    segs.n = 1;
+    segs.s[0] = NttSeg{in, out, ctx->d_limbs, ctx->L, (uint32_t)n_groups, 0};
+    return segs;
+}
+
 template <class Cfg>
 hc_status run_ntt_fwd(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_groups, cudaStream_t s)
 {
     if (n_groups == 0) return HC_OK;
-    auto kern = k_ntt_fwd<Cfg>;
-    hc_status st = prepare<Cfg, KK_FWD>(kern, Cfg::SMEM_BYTES);
-    if (st != HC_OK) return st;
-    const size_t items = n_groups * ctx->L;
-    if (items > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
-    ProfileScope ps(kname<Cfg>(0), s);
-    kern<<<(unsigned)items, Cfg::T, Cfg::SMEM_BYTES, s>>>(in, out, ctx->d_limbs, ctx->L, (uint32_t)n_groups);
-    return after_launch("k_ntt_fwd");
+    if (n_groups * ctx->L > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
+    return run_ntt_segs<Cfg, KK_FWD>(one_seg(ctx, in, out, n_groups), s, false);
 }
 
 template <class Cfg>
 hc_status run_ntt_inv(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_groups, cudaStream_t s)
 {
     if (n_groups == 0) return HC_OK;
-    auto kern = k_ntt_inv<Cfg>;
-    hc_status st = prepare<Cfg, KK_INV>(kern, Cfg::SMEM_BYTES);
-    if (st != HC_OK) return st;
-    const size_t items = n_groups * ctx->L;
-    if (items > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
-    ProfileScope ps(kname<Cfg>(1), s);
-    kern<<<(unsigned)items, Cfg::T, Cfg::SMEM_BYTES, s>>>(in, out, ctx->d_limbs, ctx->L, (uint32_t)n_groups);
-    return after_launch("k_ntt_inv");
+    if (n_groups * ctx->L > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
+    return run_ntt_segs<Cfg, KK_INV>(one_seg(ctx, in, out, n_groups), s, true);
 }
 
 template <class Cfg>
@@ -389,6 +437,19 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
     case KK_INV: return detail::run_ntt_inv<Single>(ctx, a.in, a.out, a.n, s);
     case KK_FWDCT: return detail::run_ntt_fwd<Fused>(ctx, a.in, a.out, a.n * (2 / Fused::NP), s);
     case KK_INVCT: return detail::run_ntt_inv<Fused>(ctx, a.in, a.out, a.n * (2 / Fused::NP), s);
+    case KK_FWDCT_SEGS:
+    case KK_INVCT_SEGS: {
+        // segment n_groups are given in ciphertexts; scale to CTAs of this shape
+        NttSegs segs = *a.segs;
+        uint32_t begin = 0;
+        for (uint32_t i = 0; i < segs.n; ++i) {
+            segs.s[i].n_groups *= 2 / Fused::NP;
+            segs.s[i].cta_begin = begin;
+            begin += segs.s[i].n_groups * segs.s[i].L;
+        }
+        return kind == KK_FWDCT_SEGS ? detail::run_ntt_segs<Fused, KK_FWDCT>(segs, s, false)
+                                     : detail::run_ntt_segs<Fused, KK_INVCT>(segs, s, true);
+    }
     case KK_MAC: return detail::run_mac_intt<Fused>(ctx, a.in, a.pt, a.terms, a.out, a.n, s);
     case KK_PROD: return detail::run_product<Fused>(ctx, a.in, a.pt, a.out_index, a.out, a.n, a.accumulate, s);
     default: return set_error(HC_ERR_INVALID_ARG, "unknown kernel kind %d", kind);

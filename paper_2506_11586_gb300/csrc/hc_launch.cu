@@ -71,19 +71,27 @@ constexpr int kMacStages = 3;
 
 template <int KC>
 __global__ void __launch_bounds__(kMacThreads)
-k_mac_conv(const uint64_t *__restrict__ X, const uint64_t *__restrict__ W, uint64_t *__restrict__ Y,
-           const LimbConst *__restrict__ limbs, uint32_t N, uint32_t L, uint32_t G, uint32_t B, uint32_t M,
-           uint32_t MB, int *err)
+k_mac_conv(const __grid_constant__ MacSegs segs, int *err)
 {
     constexpr int H = kMacThreads / KC;
     constexpr uint32_t ROW_BYTES = KC * sizeof(uint64_t);
     __shared__ __align__(8) uint64_t bars[1 + kMacStages];
     extern __shared__ __align__(16) uint64_t dsm[];
+    uint32_t si = 0;
+    while (si + 1 < segs.n && blockIdx.x >= segs.s[si + 1].cta_begin) ++si;
+    const MacSeg &sg = segs.s[si];
+    const uint64_t *__restrict__ X = sg.X;
+    const uint64_t *__restrict__ W = sg.W;
+    uint64_t *__restrict__ Y = sg.Y;
+    const LimbConst *__restrict__ limbs = sg.limbs;
+    const uint32_t N = sg.N, L = sg.L, G = sg.G, B = sg.B, M = sg.M, MB = sg.MB;
+    const uint32_t local = blockIdx.x - sg.cta_begin;
+    const uint32_t chunk = local % sg.chunks, rest = local / sg.chunks;
     const uint32_t P = 2 * B, rows = G * P;
     uint64_t *xs = dsm;                          // [rows][KC]
     uint64_t *ws = dsm + (size_t)rows * KC;      // [kMacStages][G][KC]
-    const uint32_t k0 = blockIdx.x * KC, limb = blockIdx.y;
-    const uint32_t m0 = blockIdx.z * MB, m1 = min(M, m0 + MB);
+    const uint32_t k0 = chunk * KC, limb = rest % L;
+    const uint32_t m0 = (rest / L) * MB, m1 = min(M, m0 + MB);
     const uint32_t nm = m1 > m0 ? m1 - m0 : 0;
     const size_t LN = (size_t)L * N;
     const uint64_t *xsrc = X + (size_t)limb * N + k0;   // input row r at xsrc + r*LN
@@ -150,39 +158,92 @@ k_mac_conv(const uint64_t *__restrict__ X, const uint64_t *__restrict__ W, uint6
     }
 }
 
-template <int KC>
-static hc_status run_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64_t *w_ntt, uint64_t *y,
-                              uint32_t G, uint32_t B, uint32_t M, cudaStream_t s)
+constexpr int kMacKC = 64;
+
+static size_t mac_smem(uint32_t G, uint32_t B)
 {
-    const size_t smem = ((size_t)G * 2 * B + (size_t)kMacStages * G) * KC * sizeof(uint64_t);
+    return ((size_t)G * 2 * B + (size_t)kMacStages * G) * kMacKC * sizeof(uint64_t);
+}
+
+// fill the launch geometry of one segment: enough CTAs for about four waves
+static MacSeg mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
+                      uint32_t M)
+{
+    MacSeg sg{};
+    sg.X = x;
+    sg.W = w;
+    sg.Y = y;
+    sg.limbs = ctx->d_limbs;
+    sg.N = ctx->N;
+    sg.L = ctx->L;
+    sg.G = G;
+    sg.B = B;
+    sg.M = M;
+    const size_t smem = mac_smem(G, B);
+    const uint32_t per_sm = (uint32_t)((200 * 1024) / smem) < 4 ? (uint32_t)((200 * 1024) / smem) : 4;
+    sg.chunks = ctx->N / kMacKC;
+    const uint32_t target = 152 * (per_sm ? per_sm : 1) * 4;
+    const uint32_t want = (target + sg.chunks * ctx->L - 1) / (sg.chunks * ctx->L);
+    const uint32_t groups = want < 1 ? 1 : (want > M ? M : want);
+    sg.MB = (M + groups - 1) / groups;
+    sg.groups = (M + sg.MB - 1) / sg.MB;
+    return sg;
+}
+
+static hc_status run_mac_segs(MacSegs &segs, size_t smem, int *err, cudaStream_t s)
+{
     static std::atomic<uint32_t> attr_done{0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!(attr_done.load() & (1u << (dev & 31)))) {
-        cudaError_t e = cudaFuncSetAttribute(k_mac_conv<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_mac_conv<kMacKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_mac_conv)");
         attr_done.fetch_or(1u << (dev & 31));
     }
-    // enough CTAs for about four waves: split the output channels into groups of MB
-    const uint32_t per_sm = (uint32_t)((200 * 1024) / smem) < 4 ? (uint32_t)((200 * 1024) / smem) : 4;
-    const uint32_t chunks = ctx->N / KC;
-    const uint32_t target = 152 * (per_sm ? per_sm : 1) * 4;
-    const uint32_t want = (target + chunks * ctx->L - 1) / (chunks * ctx->L);
-    const uint32_t groups = want < 1 ? 1 : (want > M ? M : want);
-    const uint32_t MB = (M + groups - 1) / groups;
-    const dim3 grid(chunks, ctx->L, (M + MB - 1) / MB);
+    uint32_t begin = 0;
+    for (uint32_t i = 0; i < segs.n; ++i) {
+        segs.s[i].cta_begin = begin;
+        begin += segs.s[i].chunks * segs.s[i].L * segs.s[i].groups;
+    }
+    if (begin == 0) return HC_OK;
     ProfileScope ps("k_mac_conv", s);
-    k_mac_conv<KC><<<grid, kMacThreads, smem, s>>>(x_ntt, w_ntt, y, ctx->d_limbs, ctx->N, ctx->L, G, B, M, MB,
-                                                   ctx->d_flag + 1);
+    k_mac_conv<kMacKC><<<begin, kMacThreads, smem, s>>>(segs, err);
     return after_launch_status("k_mac_conv");
+}
+
+bool mac_conv_fits(uint32_t G, uint32_t B)
+{
+    return mac_smem(G, B) <= 200 * 1024;
 }
 
 hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64_t *w_ntt, uint64_t *y, uint32_t G,
                           uint32_t B, uint32_t M, cudaStream_t s)
 {
-    const size_t rows = (size_t)G * 2 * B + (size_t)kMacStages * G;
-    if (rows * 64 * sizeof(uint64_t) > 200 * 1024) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
-    return run_mac_conv<64>(ctx, x_ntt, w_ntt, y, G, B, M, s);
+    if (!mac_conv_fits(G, B) || ctx->N % kMacKC) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
+    MacSegs segs{};
+    segs.n = 1;
+    segs.s[0] = mac_seg(ctx, x_ntt, w_ntt, y, G, B, M);
+    return run_mac_segs(segs, mac_smem(G, B), ctx->d_flag + 1, s);
+}
+
+hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s)
+{
+    for (size_t i0 = 0; i0 < n; i0 += kMaxSegs) {
+        MacSegs segs{};
+        size_t smem = 0;
+        const size_t i1 = i0 + kMaxSegs < n ? i0 + kMaxSegs : n;
+        for (size_t i = i0; i < i1; ++i) {
+            const MacLayer &ly = layers[i];
+            if (!mac_conv_fits(ly.G, ly.B)) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
+            segs.s[segs.n++] = mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M);
+            const size_t sm = mac_smem(ly.G, ly.B);
+            if (sm > smem) smem = sm;
+        }
+        hc_status st = run_mac_segs(segs, smem, ctxs[i0]->d_flag + 1, s);
+        if (st != HC_OK) return st;
+    }
+    return HC_OK;
 }
 
 namespace {
@@ -195,7 +256,8 @@ hc_status after(const char *what)
 
 hc_status dispatch(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaStream_t s)
 {
-    const int v = ctx->variant[kind];
+    const int v = kind == KK_FWDCT_SEGS ? ctx->variant[KK_FWDCT]
+                  : kind == KK_INVCT_SEGS ? ctx->variant[KK_INVCT] : ctx->variant[kind];
     switch (ctx->logN) {
     case 12: return launch_n<12>(ctx, kind, v, a, s);
     case 13: return launch_n<13>(ctx, kind, v, a, s);
@@ -240,6 +302,13 @@ hc_status launch_ntt_inv_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out
     a.out = out;
     a.n = n_ct;
     return dispatch(ctx, KK_INVCT, a, s);
+}
+
+hc_status launch_ntt_ct_segs(const hc_ctx *ctx, const NttSegs &segs, bool inverse, cudaStream_t s)
+{
+    LaunchArgs a{};
+    a.segs = &segs;
+    return dispatch(ctx, inverse ? KK_INVCT_SEGS : KK_FWDCT_SEGS, a, s);
 }
 
 hc_status launch_mac_intt(const hc_ctx *ctx, const uint64_t *ct_ntt, const uint64_t *pt_ntt, MacTerms terms,

@@ -1,0 +1,548 @@
+// hc_plan.cu -- plans: one batched launch sequence over many conv layers and
+// standalone products of any supported ring degree, captured into a CUDA
+// graph and replayed; the plain one-launch-per-product form of the same work;
+// and the plan autotuner (launch-shape variants timed on the plan itself).
+//
+// The arithmetic is the one of Sec. 6.2 / App. C.1 (NTT -> NTT-domain MAC ->
+// INTT); batching only changes how many launches carry it.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hc_internal.h"
+
+using namespace hc;
+
+namespace {
+
+struct PlanConv {
+    const hc_ctx *ctx;
+    const hc_weights *w;
+    const uint64_t *in;
+    uint64_t *out;
+    uint64_t *ntt;    // plan scratch: NTT-domain inputs [I][2][L][N]
+    bool blocked;     // blocked MAC fits in shared memory (else fused MAC + INTT)
+};
+
+struct PlanProd {
+    const hc_ctx *ctx;
+    const uint64_t *ct;
+    const uint64_t *pt;
+    uint64_t *out;
+    size_t n;
+};
+
+}  // namespace
+
+struct hc_plan {
+    uint32_t magic;
+    int device;
+    std::vector<PlanConv> convs;
+    std::vector<PlanProd> prods;
+    std::vector<const hc_ctx *> ctxs;   // distinct contexts, first-use order
+    void *d_scratch = nullptr;          // conv NTT'd inputs
+    void *d_mix = nullptr;              // MixItem[] | units[] | counter
+    MixItem *d_items = nullptr;
+    uint32_t *d_units = nullptr;
+    uint32_t *d_next = nullptr;
+    uint32_t n_units = 0;
+    uint64_t n_products = 0, alg_bytes = 0;
+    uint32_t n_launches = 0;
+    uint32_t runs = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+inline bool ctx_ok(const hc_ctx *c) { return c && c->magic == kMagicCtx; }
+inline bool weights_ok(const hc_weights *w) { return w && w->magic == kMagicWeights; }
+inline bool plan_ok(const hc_plan *p) { return p && p->magic == kMagicPlan; }
+
+size_t ct_words(const hc_ctx *c) { return (size_t)2 * c->L * c->N; }
+
+// ---- overlap check ----------------------------------------------------------
+struct Span {
+    uintptr_t b, e;
+    size_t item;
+    int role;  // 0 input ct, 1 input pt, 2 output
+};
+
+hc_status check_overlaps(const std::vector<hc_work_item> &items)
+{
+    std::vector<Span> sp;
+    for (size_t i = 0; i < items.size(); ++i) {
+        const hc_work_item &it = items[i];
+        const size_t cw = ct_words(it.ctx) * 8;
+        size_t nin, nout;
+        if (it.kind == HC_WORK_CONV) {
+            nin = it.weights->I;
+            nout = it.weights->O;
+        } else {
+            nin = nout = it.n;
+            const uintptr_t pb = (uintptr_t)it.d_pt_ntt;
+            sp.push_back(Span{pb, pb + it.n * (size_t)it.ctx->L * it.ctx->N * 8, i, 1});
+        }
+        const uintptr_t ib = (uintptr_t)it.d_ct_in, ob = (uintptr_t)it.d_ct_out;
+        sp.push_back(Span{ib, ib + nin * cw, i, 0});
+        sp.push_back(Span{ob, ob + nout * cw, i, 2});
+    }
+    std::sort(sp.begin(), sp.end(), [](const Span &a, const Span &b) { return a.b < b.b; });
+    std::vector<Span> active;
+    for (const Span &cur : sp) {
+        active.erase(std::remove_if(active.begin(), active.end(), [&](const Span &a) { return a.e <= cur.b; }),
+                     active.end());
+        for (const Span &a : active) {
+            if (a.role != 2 && cur.role != 2) continue;  // inputs may be shared
+            if (a.item != cur.item)
+                return set_error(HC_ERR_INVALID_ARG, "items %zu and %zu overlap (an output is involved)", a.item,
+                                 cur.item);
+            const hc_work_item &it = items[a.item];
+            const bool in_out = (a.role == 0 && cur.role == 2) || (a.role == 2 && cur.role == 0);
+            if (it.kind == HC_WORK_CONV && in_out) continue;  // all inputs are read before any output is written
+            if (it.kind == HC_WORK_PRODUCTS && in_out && a.b == cur.b) continue;  // exactly in place
+            return set_error(HC_ERR_INVALID_ARG, "item %zu: output partially overlaps its inputs", a.item);
+        }
+        active.push_back(cur);
+    }
+    return HC_OK;
+}
+
+// ---- the batched launch sequence ---------------------------------------------
+hc_status run_batched(hc_plan *p, cudaStream_t s)
+{
+    // forward NTT of every conv input, one launch per ring degree (per 48 items)
+    for (uint32_t logN = 12; logN <= 14; ++logN) {
+        NttSegs segs{};
+        const hc_ctx *first = nullptr;
+        auto flush = [&]() -> hc_status {
+            if (!segs.n) return HC_OK;
+            hc_status st = launch_ntt_ct_segs(first, segs, false, s);
+            segs.n = 0;
+            first = nullptr;
+            return st;
+        };
+        for (const PlanConv &c : p->convs) {
+            if (c.ctx->logN != logN) continue;
+            if (!first) first = c.ctx;
+            segs.s[segs.n++] = NttSeg{c.in, c.ntt, c.ctx->d_limbs, c.ctx->L, c.w->I, 0};
+            if (segs.n == kMaxSegs) {
+                hc_status st = flush();
+                if (st != HC_OK) return st;
+            }
+        }
+        hc_status st = flush();
+        if (st != HC_OK) return st;
+    }
+    // NTT-domain MAC of every conv item that has a blocked MAC, one launch
+    std::vector<const hc_ctx *> mctx;
+    std::vector<MacLayer> layers;
+    for (const PlanConv &c : p->convs) {
+        if (c.blocked) {
+            mctx.push_back(c.ctx);
+            layers.push_back(MacLayer{c.ntt, c.w->d_pt, c.out, c.w->G, c.w->B, c.w->desc.M});
+        } else {
+            hc_status st = launch_mac_intt(c.ctx, c.ntt, c.w->d_pt, MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out,
+                                           c.w->O, s);
+            if (st != HC_OK) return st;
+        }
+    }
+    if (!layers.empty()) {
+        hc_status st = launch_mac_conv_layers(mctx.data(), layers.data(), layers.size(), s);
+        if (st != HC_OK) return st;
+    }
+    // inverse NTT of every blocked-MAC output, in place, one launch per ring degree
+    for (uint32_t logN = 12; logN <= 14; ++logN) {
+        NttSegs segs{};
+        const hc_ctx *first = nullptr;
+        for (const PlanConv &c : p->convs) {
+            if (c.ctx->logN != logN || !c.blocked) continue;
+            if (!first) first = c.ctx;
+            segs.s[segs.n++] = NttSeg{c.out, c.out, c.ctx->d_limbs, c.ctx->L, c.w->O, 0};
+            if (segs.n == kMaxSegs) {
+                hc_status st = launch_ntt_ct_segs(first, segs, true, s);
+                if (st != HC_OK) return st;
+                segs.n = 0;
+                first = nullptr;
+            }
+        }
+        if (segs.n) {
+            hc_status st = launch_ntt_ct_segs(first, segs, true, s);
+            if (st != HC_OK) return st;
+        }
+    }
+    // every standalone product, one persistent launch
+    if (p->n_units) {
+        HC_CUDA_TRY(cudaMemsetAsync(p->d_next, 0, sizeof(uint32_t), s));
+        hc_status st = launch_product_mixed(p->d_items, p->d_units, p->n_units, p->d_next, s);
+        if (st != HC_OK) return st;
+    }
+    return HC_OK;
+}
+
+uint32_t count_launches(const hc_plan *p)
+{
+    uint32_t n = 0, fit = 0;
+    uint32_t per_n[3] = {0, 0, 0}, per_n_fit[3] = {0, 0, 0};
+    for (const PlanConv &c : p->convs) {
+        ++per_n[c.ctx->logN - 12];
+        if (c.blocked) {
+            ++per_n_fit[c.ctx->logN - 12];
+            ++fit;
+        } else {
+            ++n;  // fused MAC + INTT
+        }
+    }
+    for (int i = 0; i < 3; ++i) n += (per_n[i] + kMaxSegs - 1) / kMaxSegs + (per_n_fit[i] + kMaxSegs - 1) / kMaxSegs;
+    n += (fit + kMaxSegs - 1) / kMaxSegs;
+    if (p->n_units) ++n;
+    return n;
+}
+
+hc_status check_plan_inputs(hc_plan *p, cudaStream_t s)
+{
+    for (const PlanConv &c : p->convs) {
+        hc_status st = check_inputs(c.ctx, c.in, (size_t)2 * c.w->I, s);
+        if (st != HC_OK) return st;
+    }
+    for (const PlanProd &q : p->prods) {
+        hc_status st = check_inputs(q.ctx, q.ct, 2 * q.n, s);
+        if (st == HC_OK) st = check_inputs(q.ctx, q.pt, q.n, s);
+        if (st != HC_OK) return st;
+    }
+    return HC_OK;
+}
+
+void drop_graph(hc_plan *p)
+{
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+}
+
+hc_status capture(hc_plan *p)
+{
+    if (!p->cap_stream) HC_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    HC_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    hc_status st = run_batched(p, p->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (st != HC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        p->exec = nullptr;
+        return cuda_error(e, "cudaGraphInstantiate");
+    }
+    p->graph = g;
+    return HC_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------------
+std::string tune_key(const hc_ctx *c, int kind, const char *gpu, int sms)
+{
+    std::string k = gpu;
+    for (char &ch : k)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    char buf[64];
+    snprintf(buf, sizeof buf, "|sm%d|N%u|L%u", sms, c->N, c->L);
+    k += buf;
+    for (uint32_t i = 0; i < c->L; ++i) {
+        snprintf(buf, sizeof buf, "|%llx", (unsigned long long)c->q[i]);
+        k += buf;
+    }
+    snprintf(buf, sizeof buf, "|kind%d", kind);
+    return k + buf;
+}
+
+// median device time (ms) of `reps` batched runs on s
+hc_status time_batched(hc_plan *p, cudaStream_t s, int reps, float *ms)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    HC_CUDA_TRY(cudaEventCreate(&a));
+    cudaError_t e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return cuda_error(e, "cudaEventCreate");
+    }
+    std::vector<float> t;
+    hc_status st = run_batched(p, s);  // warm-up with this variant
+    for (int r = 0; st == HC_OK && r < reps; ++r) {
+        cudaEventRecord(a, s);
+        st = run_batched(p, s);
+        cudaEventRecord(b, s);
+        if (st != HC_OK) break;
+        e = cudaEventSynchronize(b);
+        float x = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&x, a, b);
+        if (e != cudaSuccess) st = cuda_error(e, "autotune timing");
+        t.push_back(x);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != HC_OK) return st;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return HC_OK;
+}
+
+}  // namespace
+
+namespace hc {
+void plan_destroy(hc_plan *p)
+{
+    DeviceGuard g(p->device);
+    drop_graph(p);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    dev_free_persistent(p->d_scratch);
+    dev_free_persistent(p->d_mix);
+    p->magic = kMagicDead;
+    delete p;
+}
+}  // namespace hc
+
+// =============================================================================
+extern "C" {
+
+hc_status hc_plan_create(const hc_work_item *items, size_t n, hc_plan **out)
+{
+    if (!out) return set_error(HC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n > 0 && !items) return set_error(HC_ERR_INVALID_ARG, "items is NULL");
+    int dev = 0;
+    HC_CUDA_TRY(cudaGetDevice(&dev));
+    std::vector<hc_work_item> its(items, items + n);
+    for (size_t i = 0; i < n; ++i) {
+        const hc_work_item &it = its[i];
+        if (!ctx_ok(it.ctx)) return set_error(HC_ERR_INVALID_ARG, "item %zu: invalid context", i);
+        if (it.ctx->device != dev) return set_error(HC_ERR_INVALID_ARG, "item %zu: context on another device", i);
+        if (!it.d_ct_in || !it.d_ct_out) return set_error(HC_ERR_INVALID_ARG, "item %zu: null buffer", i);
+        if (it.kind == HC_WORK_CONV) {
+            if (!weights_ok(it.weights) || it.weights->ctx != it.ctx)
+                return set_error(HC_ERR_INVALID_ARG, "item %zu: weights invalid or of another context", i);
+        } else if (it.kind == HC_WORK_PRODUCTS) {
+            if (it.n == 0 || !it.d_pt_ntt) return set_error(HC_ERR_INVALID_ARG, "item %zu: empty product list", i);
+        } else {
+            return set_error(HC_ERR_INVALID_ARG, "item %zu: unknown kind %u", i, it.kind);
+        }
+    }
+    hc_status st = check_overlaps(its);
+    if (st != HC_OK) return st;
+
+    hc_plan *p = new (std::nothrow) hc_plan();
+    if (!p) return set_error(HC_ERR_OOM, "host allocation failed");
+    p->magic = kMagicPlan;
+    p->device = dev;
+    size_t scratch_words = 0;
+    std::vector<MixItem> mix;
+    for (const hc_work_item &it : its) {
+        const hc_ctx *c = it.ctx;
+        if (std::find(p->ctxs.begin(), p->ctxs.end(), c) == p->ctxs.end()) p->ctxs.push_back(c);
+        const uint64_t nl = (uint64_t)c->N * c->L * 8;
+        if (it.kind == HC_WORK_CONV) {
+            const hc_weights *w = it.weights;
+            p->convs.push_back(PlanConv{c, w, it.d_ct_in, it.d_ct_out, nullptr, mac_conv_fits(w->G, w->B) && c->N % 64 == 0});
+            scratch_words += (size_t)w->I * ct_words(c);
+            p->n_products += (uint64_t)w->desc.M * w->G * w->B;
+            p->alg_bytes += nl * (2ull * w->I + w->P + 2ull * w->O);
+        } else {
+            p->prods.push_back(PlanProd{c, it.d_ct_in, it.d_pt_ntt, it.d_ct_out, it.n});
+            for (size_t j = 0; j < it.n; ++j)
+                mix.push_back(MixItem{it.d_ct_in + j * ct_words(c), it.d_pt_ntt + j * (size_t)c->L * c->N,
+                                      it.d_ct_out + j * ct_words(c), c->d_limbs, c->L, c->logN});
+            p->n_products += it.n;
+            p->alg_bytes += nl * 5ull * it.n;
+        }
+    }
+    if (mix.size() >= (1u << 28)) {
+        hc_free(p);
+        return set_error(HC_ERR_INVALID_ARG, "more than 2^28 standalone products");
+    }
+    // units in cost order: larger ring degree first (stable: item order within a degree)
+    std::vector<uint32_t> units;
+    for (uint32_t logN = 14; logN >= 12; --logN)
+        for (uint32_t j = 0; j < mix.size(); ++j) {
+            if (mix[j].logN != logN) continue;
+            const uint32_t step = mix_comps_per_unit(logN);
+            for (uint32_t limb = 0; limb < mix[j].L; ++limb)
+                for (uint32_t comp = 0; comp < 2; comp += step) units.push_back(mix_unit(j, limb, comp));
+        }
+    p->n_units = (uint32_t)units.size();
+
+    if (scratch_words) {
+        p->d_scratch = dev_alloc_persistent(scratch_words * sizeof(uint64_t));
+        if (!p->d_scratch) {
+            hc_free(p);
+            return set_error(HC_ERR_OOM, "plan scratch allocation failed (%zu bytes)", scratch_words * 8);
+        }
+        uint64_t *q = (uint64_t *)p->d_scratch;
+        for (PlanConv &c : p->convs) {
+            c.ntt = q;
+            q += (size_t)c.w->I * ct_words(c.ctx);
+        }
+    }
+    if (!mix.empty()) {
+        const size_t items_b = (mix.size() * sizeof(MixItem) + 255) & ~(size_t)255;
+        const size_t units_b = (units.size() * sizeof(uint32_t) + 255) & ~(size_t)255;
+        p->d_mix = dev_alloc_persistent(items_b + units_b + 256);
+        if (!p->d_mix) {
+            hc_free(p);
+            return set_error(HC_ERR_OOM, "plan work-table allocation failed");
+        }
+        p->d_items = (MixItem *)p->d_mix;
+        p->d_units = (uint32_t *)((char *)p->d_mix + items_b);
+        p->d_next = (uint32_t *)((char *)p->d_mix + items_b + units_b);
+        cudaError_t e = cudaMemcpy(p->d_items, mix.data(), mix.size() * sizeof(MixItem), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_units, units.data(), units.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            hc_free(p);
+            return cuda_error(e, "plan work-table upload");
+        }
+    }
+    p->n_launches = count_launches(p);
+    *out = p;
+    return HC_OK;
+}
+
+hc_status hc_plan_run(hc_plan *p, void *cuda_stream)
+{
+    if (!plan_ok(p)) return set_error(HC_ERR_INVALID_ARG, "invalid plan");
+    DeviceGuard g(p->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    hc_status st = check_plan_inputs(p, s);
+    if (st != HC_OK) return st;
+    // the first run (and any run while tracing) issues the launches directly;
+    // the launch sequence is then captured once and replayed
+    if (profile_enabled() || (!p->exec && p->runs == 0)) {
+        st = run_batched(p, s);
+        if (st == HC_OK) ++p->runs;
+        return st;
+    }
+    if (!p->exec) {
+        st = capture(p);
+        if (st != HC_OK) return st;
+    }
+    HC_CUDA_TRY(cudaGraphLaunch(p->exec, s));
+    ++p->runs;
+    return HC_OK;
+}
+
+hc_status hc_plan_run_plain(hc_plan *p, void *cuda_stream)
+{
+    if (!plan_ok(p)) return set_error(HC_ERR_INVALID_ARG, "invalid plan");
+    DeviceGuard g(p->device);
+    for (const PlanConv &c : p->convs) {
+        hc_status st = hc_conv_ct_pt_plain(c.ctx, c.w, c.in, c.out, cuda_stream);
+        if (st != HC_OK) return st;
+    }
+    cudaStream_t s = as_stream(cuda_stream);
+    for (const PlanProd &q : p->prods) {
+        hc_status st = check_inputs(q.ctx, q.ct, 2 * q.n, s);
+        if (st == HC_OK) st = check_inputs(q.ctx, q.pt, q.n, s);
+        if (st != HC_OK) return st;
+        const size_t cw = ct_words(q.ctx), pw = (size_t)q.ctx->L * q.ctx->N;
+        for (size_t j = 0; j < q.n; ++j) {
+            st = launch_product(q.ctx, q.ct + j * cw, q.pt + j * pw, nullptr, q.out + j * cw, 1, false, s);
+            if (st != HC_OK) return st;
+        }
+    }
+    return HC_OK;
+}
+
+hc_status hc_plan_autotune(hc_plan *p, const char *cache_path, void *cuda_stream)
+{
+    if (!plan_ok(p)) return set_error(HC_ERR_INVALID_ARG, "invalid plan");
+    DeviceGuard g(p->device);
+    cudaStream_t s = as_stream(cuda_stream);
+    cudaDeviceProp prop;
+    HC_CUDA_TRY(cudaGetDeviceProperties(&prop, p->device));
+
+    // knobs: the kernel families this plan launches, per context
+    struct Knob {
+        hc_ctx *ctx;
+        int kind;
+    };
+    std::vector<Knob> knobs;
+    for (const hc_ctx *c : p->ctxs) {
+        bool any = false, blocked = false, fused = false;
+        for (const PlanConv &cv : p->convs)
+            if (cv.ctx == c) {
+                any = true;
+                (cv.blocked ? blocked : fused) = true;
+            }
+        hc_ctx *mc = const_cast<hc_ctx *>(c);  // variants are a documented mutable hint
+        if (any) knobs.push_back(Knob{mc, KK_FWDCT});
+        if (blocked) knobs.push_back(Knob{mc, KK_INVCT});
+        if (fused) knobs.push_back(Knob{mc, KK_MAC});
+    }
+
+    std::vector<std::pair<std::string, int>> cache;
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "r")) {
+            char line[1024];
+            while (fgets(line, sizeof line, f)) {
+                char key[960];
+                int v = -1;
+                if (sscanf(line, "%959s %d", key, &v) == 2 && v >= 0 && v < kNumVariants) cache.emplace_back(key, v);
+            }
+            fclose(f);
+        }
+    }
+    std::vector<size_t> pending;
+    for (size_t i = 0; i < knobs.size(); ++i) {
+        const std::string k = tune_key(knobs[i].ctx, knobs[i].kind, prop.name, prop.multiProcessorCount);
+        int v = -1;
+        for (const auto &e : cache)
+            if (e.first == k) v = e.second;  // last entry wins
+        if (v >= 0)
+            knobs[i].ctx->variant[knobs[i].kind] = (uint8_t)v;
+        else
+            pending.push_back(i);
+    }
+    drop_graph(p);  // captured launches carry the old variants
+    if (pending.empty()) return HC_OK;
+
+    FILE *out = cache_path ? fopen(cache_path, "a") : nullptr;
+    hc_status st = HC_OK;
+    for (size_t i : pending) {
+        Knob &kb = knobs[i];
+        int best = kb.ctx->variant[kb.kind];
+        float best_ms = -1.f;
+        for (int v = 0; v < kNumVariants && st == HC_OK; ++v) {
+            kb.ctx->variant[kb.kind] = (uint8_t)v;
+            float ms = 0.f;
+            st = time_batched(p, s, 5, &ms);
+            if (st == HC_OK && (best_ms < 0.f || ms < best_ms)) {
+                best_ms = ms;
+                best = v;
+            }
+        }
+        kb.ctx->variant[kb.kind] = (uint8_t)best;
+        if (st != HC_OK) break;
+        if (out)
+            fprintf(out, "%s %d\n", tune_key(kb.ctx, kb.kind, prop.name, prop.multiProcessorCount).c_str(), best);
+    }
+    if (out) fclose(out);
+    return st;
+}
+
+hc_status hc_plan_info(const hc_plan *p, uint64_t *n_products, uint64_t *alg_bytes, uint32_t *n_launches)
+{
+    if (!plan_ok(p)) return set_error(HC_ERR_INVALID_ARG, "invalid plan");
+    if (n_products) *n_products = p->n_products;
+    if (alg_bytes) *alg_bytes = p->alg_bytes;
+    if (n_launches) *n_launches = p->n_launches;
+    return HC_OK;
+}
+
+}  // extern "C"

@@ -44,6 +44,8 @@ bool profile_enabled() { return g_enabled.load(std::memory_order_relaxed) != 0; 
 ProfileScope::ProfileScope(const char *name, cudaStream_t s) : name_(name), s_(s)
 {
     if (!profile_enabled()) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s_, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;  // no timing in graphs
     std::lock_guard<std::mutex> lk(g_mu);
     start_ = take_event();
     stop_ = take_event();
