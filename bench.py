@@ -10,6 +10,20 @@ P = 512 weight plaintexts, O = 256 output ciphertexts, 2048 ct x pt products).
 Inputs are seeded synthetic residues uniform in [0, q_i) (the cost does not
 depend on the values); weights are seeded uniform int8.
 
+The same line also carries, measured in the same run:
+  batched  -- every stride-1 SqueezeNet-1.1 convolution (25 layers, 23,568
+              products, N = 8192, L = 3) as one plan replayed from a CUDA
+              graph, against the 25 single-layer calls and the plain
+              one-launch-per-product form; and 2000 standalone products of
+              uneven ring degree (40/40/20 over N = 4096/8192/16384 with
+              2/3/4 limbs) in one persistent launch, against one launch per
+              degree and one launch per product;
+  serving  -- Poisson arrivals (200 requests/s, seed 5) of single-layer
+              requests drawn half from the SqueezeNet-1.1 layers and half
+              from the 46 stride-1 ResNet-50 convolution instances
+              (N = 16384, L = 4), weights resident, continuous batching under
+              a 32 GiB device budget: p50/p99 latency and products/s.
+
 Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle (plain
 schoolbook convolution) on a bounded sample of the same workload instead.
 """
@@ -31,6 +45,10 @@ METRIC = "HE conv ct x pt products/s (bit-exact)"
 UNIT = "products/s"
 WORKLOAD = "conv3x3_56x56x64_to64_N8192_L3"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+TUNE_CACHE = os.path.join(ROOT, "paper_2506_11586_gb300", "_build", "autotune.txt")
+
+
+KIND_NAMES = {"ntt_fwd_ct": 4, "mac_conv": 6, "ntt_inv_ct": 5}
 
 
 def parse():
@@ -44,6 +62,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=6000)
+    ap.add_argument("--serving-rate", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -246,6 +267,120 @@ def run_reference(args):
     return 0
 
 
+def _events_ms(fn, reps, stream, flush=None):
+    """Device time (ms) of each of reps calls of fn, CUDA events on stream."""
+    import torch
+    out = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return out
+
+
+def _kernel_trace(L, fn):
+    import torch
+    L.hc_profile_collect()
+    L.hc_profile_enable(True)
+    fn()
+    torch.cuda.synchronize()
+    L.hc_profile_enable(False)
+    return {k: {"launches": v[0], "ms": v[1]} for k, v in L.hc_profile_collect().items()}
+
+
+def batched_squeezenet(L, stream, reps=20):
+    """All 25 stride-1 SqueezeNet-1.1 layers as one plan (CUDA graph) vs per-layer calls vs plain."""
+    import numpy as np
+    import torch
+    from paper_2506_11586_gb300.inputs import (CANONICAL_PRIMES, SQUEEZENET_1_1, T_PLAIN, Stream, conv_tensors,
+                                               uniform_residues)
+    ctx = L.hc_ctx_create(8192, CANONICAL_PRIMES[:3], T_PLAIN)
+    items = []
+    for i, sh in enumerate(SQUEEZENET_1_1):
+        _, K = conv_tensors(sh, seed=3)
+        w = L.hc_weights_preprocess(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), K)
+        ct = uniform_residues(Stream(3, 100 + i), CANONICAL_PRIMES[:3], (w.I, 2), 8192)
+        items.append((w, torch.from_numpy(ct.view(np.int64)).cuda(),
+                      torch.empty(w.O * 2 * 3 * 8192, dtype=torch.int64, device="cuda")))
+    plan = L.hc_plan_create([L.work_conv(ctx, w, a, b) for w, a, b in items])
+    products, nbytes, launches = L.hc_plan_info(plan)
+    L.hc_plan_autotune(plan, TUNE_CACHE, stream)
+    for _ in range(3):
+        L.hc_plan_run(plan, stream)
+    g = _events_ms(lambda: L.hc_plan_run(plan, stream), reps, stream)
+    batched = [b.clone() for _, _, b in items]
+
+    def per_layer():
+        for w, a, b in items:
+            L.hc_conv_ct_pt(ctx, w, a, b, stream)
+    per_layer()
+    pl = _events_ms(per_layer, max(3, reps // 2), stream)
+    exact_layers = all(bool(torch.equal(x, b)) for x, (_, _, b) in zip(batched, items))
+    pp = _events_ms(lambda: L.hc_plan_run_plain(plan, stream), 1, stream)
+    exact_plain = all(bool(torch.equal(x, b)) for x, (_, _, b) in zip(batched, items))
+    kern = _kernel_trace(L, lambda: L.hc_plan_run(plan, stream))
+    ms = statistics.median(g)
+    out = {"workload": "squeezenet1.1_stride1_25layers_N8192_L3", "products": products, "alg_bytes": nbytes,
+           "launches_per_pass": launches, "batched_ms": ms, "batched_p99_ms": max(g),
+           "value": products / (ms / 1e3), "unit": UNIT, "alg_gbs": nbytes / (ms / 1e3) / 1e9,
+           "per_layer_ms": statistics.median(pl), "per_layer_launches": 3 * len(items),
+           "plain_ms": pp[0], "plain_launches": products,
+           "speedup_vs_per_layer": statistics.median(pl) / ms, "speedup_vs_plain": pp[0] / ms,
+           "bit_exact_vs_per_layer": exact_layers, "bit_exact_vs_plain": exact_plain, "kernels": kern,
+           "variants": {name: L.hc_ctx_get_variant(ctx, k) for name, k in KIND_NAMES.items()}}
+    plan.close()
+    return out
+
+
+def batched_uneven(L, stream, reps=20):
+    """2000 standalone products of mixed degree in one persistent launch vs per-degree vs plain."""
+    import numpy as np
+    import torch
+    from paper_2506_11586_gb300.inputs import (CANONICAL_PRIMES, T_PLAIN, UNEVEN_CLASSES, Stream, uneven_mix,
+                                               uniform_residues)
+    labels = uneven_mix(2000, seed=4)
+    items, ctxs = [], []
+    for cls, (N, nl, _) in enumerate(UNEVEN_CLASSES):
+        n = int((labels == cls).sum())
+        ctx = L.hc_ctx_create(N, CANONICAL_PRIMES[:nl], T_PLAIN)
+        s = Stream(4, 10 + cls)
+        ct = torch.from_numpy(uniform_residues(s, CANONICAL_PRIMES[:nl], (n, 2), N).view(np.int64)).cuda()
+        pt = torch.from_numpy(uniform_residues(s, CANONICAL_PRIMES[:nl], (n,), N).view(np.int64)).cuda()
+        L.hc_ntt_fwd(ctx, pt, stream)
+        items.append((ctx, ct, pt, torch.empty_like(ct), n))
+        ctxs.append(ctx)
+    plan = L.hc_plan_create([L.work_products(c, a, p, o) for c, a, p, o, _ in items])
+    products, nbytes, launches = L.hc_plan_info(plan)
+    for _ in range(3):
+        L.hc_plan_run(plan, stream)
+    g = _events_ms(lambda: L.hc_plan_run(plan, stream), reps, stream)
+    batched = [o.clone() for _, _, _, o, _ in items]
+
+    def per_degree():
+        for c, a, p, o, n in items:
+            L.hc_ctpt_mac(c, a, p, np.arange(n), o, stream)
+    per_degree()
+    pd = _events_ms(per_degree, reps, stream)
+    exact_deg = all(bool(torch.equal(x, it[3])) for x, it in zip(batched, items))
+    pp = _events_ms(lambda: L.hc_plan_run_plain(plan, stream), 2, stream)
+    exact_plain = all(bool(torch.equal(x, it[3])) for x, it in zip(batched, items))
+    kern = _kernel_trace(L, lambda: L.hc_plan_run(plan, stream))
+    ms = statistics.median(g)
+    out = {"workload": "uneven_2000_products_40_40_20_N4096L2_N8192L3_N16384L4", "products": products,
+           "alg_bytes": nbytes, "launches_per_pass": launches, "batched_ms": ms, "batched_p99_ms": max(g),
+           "value": products / (ms / 1e3), "unit": UNIT, "alg_gbs": nbytes / (ms / 1e3) / 1e9,
+           "per_degree_ms": statistics.median(pd), "plain_ms": statistics.median(pp), "plain_launches": products,
+           "speedup_vs_per_degree": statistics.median(pd) / ms, "speedup_vs_plain": statistics.median(pp) / ms,
+           "bit_exact_vs_per_degree": exact_deg, "bit_exact_vs_plain": exact_plain, "kernels": kern}
+    plan.close()
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -263,10 +398,6 @@ def run_gb300(args):
     _, K = conv_tensors(sh, seed=2)
 
     ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
-    tuned = None
-    if not args.no_autotune:
-        from paper_2506_11586_gb300.autotune import autotune
-        tuned = autotune(ctx)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     w = L.hc_weights_preprocess(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), K)
@@ -275,6 +406,12 @@ def run_gb300(args):
     ct_host = uniform_residues(Stream(2, 5 + rank), moduli, (geo["I"], 2), N)
     d_in = torch.from_numpy(ct_host.view(np.int64)).cuda()
     d_out = torch.empty(geo["O"] * 2 * nl * N, dtype=torch.int64, device="cuda")
+    tuned = None
+    if not args.no_autotune:                # the library's autotuner, timed on this layer as a plan
+        plan = L.hc_plan_create([L.work_conv(ctx, w, d_in, d_out)])
+        L.hc_plan_autotune(plan, TUNE_CACHE)
+        plan.close()
+        tuned = {name: L.hc_ctx_get_variant(ctx, k) for name, k in KIND_NAMES.items()}
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -377,6 +514,17 @@ def run_gb300(args):
                "sample": "%d of %d output ciphertexts (%d products) of the same layer, %.1f s"
                          % (outs, geo["O"], prods, el)}
 
+    batched = serving = None
+    if rank == 0 and not args.no_batched:
+        batched = {"squeezenet": batched_squeezenet(L, stream), "uneven": batched_uneven(L, stream)}
+    if rank == 0 and args.serving_requests > 0:
+        from paper_2506_11586_gb300 import serving as srv_mod
+        layers = srv_mod.ServingLayers()
+        serving = srv_mod.run(layers, n_requests=args.serving_requests, rate=args.serving_rate)
+        serving.update({"workload": "poisson_squeezenet1.1_N8192L3_resnet50_N16384L4",
+                        "setup_s": layers.setup_s, "resident_weight_bytes": layers.weight_bytes})
+        del layers
+
     srt = sorted(step_ms)
     p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
     line = {
@@ -388,6 +536,7 @@ def run_gb300(args):
                    "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps"},
         "p50_ms": statistics.median(step_ms), "p99_ms": p99, "layer_gbs": layer_gbs,
         "roofline": roofline, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
+        "batched": batched, "serving": serving,
         "gpu_launches": launches, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
         "offline_weights_s": offline_s, "launch_variants": tuned, "clocks": clocks, "device": torch.cuda.get_device_name(local),
     }

@@ -86,8 +86,10 @@ hc_status hc_ctx_info(const hc_ctx *ctx, uint32_t *N, uint32_t *L, uint64_t *t,
 /* Launch-shape tuning (no counterpart in the paper: a GPU scheduling knob).
  * Kernel families (kind): 0 forward NTT, 1 inverse NTT, 2 fused NTT-domain
  * MAC + inverse NTT, 3 fused standalone product, 4 forward NTT of whole
- * ciphertexts, 5 inverse NTT of whole ciphertexts.  variant (0..2) selects the radix per register round, the
- * polynomials per CTA and the CTAs per SM for the context's N; every variant
+ * ciphertexts, 5 inverse NTT of whole ciphertexts, 6 blocked convolution MAC.
+ * variant (0..2) selects, for kinds 0-5, the radix per register round, the
+ * polynomials per CTA and the CTAs per SM for the context's N; for kind 6 the
+ * weight rows per pipeline stage (about 8, 16 or 32).  Every variant
  * computes the same bits, only speed differs.  hc_ctx_create picks defaults.
  * Changing a variant while other threads use the context is a data race.
  * Errors: HC_ERR_INVALID_ARG (bad handle, kind or variant). */
@@ -303,6 +305,97 @@ hc_status hc_plan_autotune(hc_plan *plan, const char *cache_path, void *cuda_str
  * batched run.  Any out pointer may be NULL. */
 hc_status hc_plan_info(const hc_plan *plan, uint64_t *n_products, uint64_t *alg_bytes, uint32_t *n_launches);
 
+/* ---------------------------------------------------------------- serving --
+ * The server side of the paper's linear layers as a request loop (Sec. 6.2:
+ * the server holds NTT-preprocessed weights and answers each client
+ * ciphertext with NTT -> MAC -> INTT).  Layers (context + resident weights)
+ * are registered once; requests -- one layer applied to one client's input
+ * ciphertexts -- arrive at any time from any host thread.
+ *
+ * Continuous batching: a scheduler thread admits queued requests in arrival
+ * order as soon as their device buffers fit in the memory budget, and each
+ * time one of the max_inflight stream slots is free it launches every
+ * admitted request (up to max_batch) as one batch: host->device copies of the
+ * inputs, then the batched launch sequence of hc_plan_run over all the
+ * batch's layers (any mix of layers and ring degrees), then device->host
+ * copies of the outputs that have a host buffer.  Batches on different
+ * streams overlap on the device.  A completion thread retires batches,
+ * returns their memory to the budget and wakes waiters.  Each request's
+ * result is bit-identical to hc_conv_ct_pt on the same layer and input,
+ * whatever else is in flight.
+ *
+ * Device memory: one pool of budget_bytes is reserved at creation; a request
+ * takes (2*I + O)*2*L*N*8 bytes (input, NTT scratch, output) from it while in
+ * flight.  Requests that can never fit are refused at submission. */
+typedef struct hc_server hc_server;
+
+typedef struct {
+    size_t budget_bytes;      /* device pool for in-flight requests (0 = 32 GiB) */
+    uint32_t max_batch;       /* most requests per batch (0 = 64, at most 4096) */
+    uint32_t max_inflight;    /* batches on the device at once, one stream each (0 = 2, at most 16) */
+} hc_server_config;
+
+typedef struct {
+    hc_status status;         /* HC_OK, or the error that failed the request's batch */
+    uint32_t batch_size;      /* requests in the batch that carried it */
+    double queue_ms;          /* submission -> its batch was enqueued */
+    double latency_ms;        /* submission -> result ready (retired by the completion thread) */
+} hc_request_info;
+
+typedef struct {
+    uint64_t submitted, completed, refused, batches, products;
+    uint64_t pool_bytes, bytes_in_use, peak_bytes_in_use;
+    uint32_t max_batch_seen;
+} hc_server_stats;
+
+/* Reserve the pool (on the current device) and start the scheduler and
+ * completion threads.  cfg may be NULL (defaults).  Errors:
+ * HC_ERR_INVALID_ARG, HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_server_create(const hc_server_config *cfg, hc_server **out);
+
+/* Register a layer: ctx and weights (preprocessed for ctx, on the server's
+ * device) must outlive the server.  *layer_id receives its index.  Errors:
+ * HC_ERR_INVALID_ARG. */
+hc_status hc_server_add_layer(hc_server *srv, const hc_ctx *ctx, const hc_weights *w, uint32_t *layer_id);
+
+/* Queue a request and return at once with its ticket.  h_ct_in: host
+ * [I][2][L][N] (pinned gives asynchronous copies), read during the request
+ * and kept valid by the caller until it completes.  h_ct_out: host
+ * [O][2][L][N] that receives the result, or NULL to keep the result in the
+ * pool (hc_server_result) until hc_server_release.  Errors:
+ * HC_ERR_INVALID_ARG (bad layer or buffer), HC_ERR_BUDGET (the request alone
+ * exceeds the pool), HC_ERR_INVALID_ARG after hc_server_shutdown. */
+hc_status hc_server_submit(hc_server *srv, uint32_t layer_id, const uint64_t *h_ct_in, uint64_t *h_ct_out,
+                           uint64_t *ticket);
+
+/* Block until the request is done (timeout_s < 0: no limit) and fill *info
+ * (may be NULL).  Errors: HC_ERR_INVALID_ARG (unknown or released ticket),
+ * HC_ERR_TIMEOUT (not done within timeout_s). */
+hc_status hc_server_wait(hc_server *srv, uint64_t ticket, double timeout_s, hc_request_info *info);
+
+/* Non-blocking: *done = 1 and *info filled if the request is done. */
+hc_status hc_server_poll(hc_server *srv, uint64_t ticket, int *done, hc_request_info *info);
+
+/* Device pointer of a done request's result [O][2][L][N] kept in the pool
+ * (submitted with h_ct_out == NULL), valid until hc_server_release.  Errors:
+ * HC_ERR_INVALID_ARG (unknown ticket, not done, or copied to the host). */
+hc_status hc_server_result(hc_server *srv, uint64_t ticket, const uint64_t **d_ct_out);
+
+/* Copy a done request's pool-resident result to host memory h_ct_out
+ * ([O][2][L][N]); returns when the copy is complete.  Errors: as
+ * hc_server_result, HC_ERR_CUDA. */
+hc_status hc_server_fetch(hc_server *srv, uint64_t ticket, uint64_t *h_ct_out);
+
+/* Forget a done request and return its result memory to the pool.  Every
+ * ticket is released once.  Errors: HC_ERR_INVALID_ARG (unknown or not done). */
+hc_status hc_server_release(hc_server *srv, uint64_t ticket);
+
+hc_status hc_server_stats_get(hc_server *srv, hc_server_stats *out);
+
+/* Stop accepting requests, finish everything queued, join the threads.
+ * hc_free(server) does this too. */
+hc_status hc_server_shutdown(hc_server *srv);
+
 /* ------------------------------------------------------------- allocation --
  * Device memory used by the library: handles' resident tables and weights,
  * and per-call scratch.  alloc(bytes, stream, user) must return device memory
@@ -331,7 +424,7 @@ typedef struct {
 void hc_profile_enable(int on);
 hc_status hc_profile_collect(hc_kernel_time *entries, size_t cap, size_t *n_out);
 
-/* Release a handle of any kind (context, weights, plan).  NULL is a no-op.
+/* Release a handle of any kind (context, weights, plan, server).  NULL is a no-op.
  * A handle must not be in use by queued GPU work when it is freed. */
 void hc_free(void *handle);
 

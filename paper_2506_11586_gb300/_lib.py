@@ -47,6 +47,29 @@ class hc_conv_desc(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in ("C", "H", "W", "M", "kh", "kw", "stride", "pad", "Cw", "Hw", "Ww")]
 
 
+class hc_work_item(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("ctx", C.c_void_p), ("weights", C.c_void_p), ("d_ct_in", C.c_void_p),
+                ("d_pt_ntt", C.c_void_p), ("d_ct_out", C.c_void_p), ("n", C.c_size_t)]
+
+
+HC_WORK_CONV = 0
+HC_WORK_PRODUCTS = 1
+
+
+class hc_server_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("max_batch", C.c_uint32), ("max_inflight", C.c_uint32)]
+
+
+class hc_request_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("batch_size", C.c_uint32), ("queue_ms", C.c_double),
+                ("latency_ms", C.c_double)]
+
+
+class hc_server_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "refused", "batches", "products",
+                                          "pool_bytes", "bytes_in_use", "peak_bytes_in_use")] + \
+               [("max_batch_seen", C.c_uint32)]
+
 _lib = None
 
 # name -> (restype, argtypes); mirrors include/hconv.h
@@ -72,6 +95,21 @@ _SIGS = {
     "hc_conv_ct_pt_host": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_conv_ct_pt_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_ctpt_mac": (C.c_int, [_P, _P, _P, _P, C.c_size_t, _P, C.c_size_t, _P]),
+    "hc_plan_create": (C.c_int, [_P, C.c_size_t, C.POINTER(_P)]),
+    "hc_plan_run": (C.c_int, [_P, _P]),
+    "hc_plan_run_plain": (C.c_int, [_P, _P]),
+    "hc_plan_autotune": (C.c_int, [_P, C.c_char_p, _P]),
+    "hc_plan_info": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
+    "hc_server_create": (C.c_int, [C.POINTER(hc_server_config), C.POINTER(_P)]),
+    "hc_server_add_layer": (C.c_int, [_P, _P, _P, C.POINTER(C.c_uint32)]),
+    "hc_server_submit": (C.c_int, [_P, C.c_uint32, _P, _P, C.POINTER(C.c_uint64)]),
+    "hc_server_wait": (C.c_int, [_P, C.c_uint64, C.c_double, C.POINTER(hc_request_info)]),
+    "hc_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int), C.POINTER(hc_request_info)]),
+    "hc_server_result": (C.c_int, [_P, C.c_uint64, C.POINTER(_P)]),
+    "hc_server_release": (C.c_int, [_P, C.c_uint64]),
+    "hc_server_fetch": (C.c_int, [_P, C.c_uint64, _P]),
+    "hc_server_stats_get": (C.c_int, [_P, C.POINTER(hc_server_stats)]),
+    "hc_server_shutdown": (C.c_int, [_P]),
     "hc_set_allocator": (None, [_P, _P, _P]),
     "hc_profile_enable": (None, [C.c_int]),
     "hc_profile_collect": (C.c_int, [_P, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -179,7 +217,7 @@ def hc_ctx_create(N, moduli, t, flags=0):
     return Ctx(out, N, [int(x) for x in m], t)
 
 
-KIND_NTT_FWD, KIND_NTT_INV, KIND_MAC_INTT, KIND_PRODUCT, KIND_NTT_FWD_CT, KIND_NTT_INV_CT = range(6)
+KIND_NTT_FWD, KIND_NTT_INV, KIND_MAC_INTT, KIND_PRODUCT, KIND_NTT_FWD_CT, KIND_NTT_INV_CT, KIND_MAC_CONV = range(7)
 N_VARIANTS = 3
 
 
@@ -296,6 +334,125 @@ def hc_ctpt_mac(ctx, ct, pt_ntt, slots, out, stream=None):
     n_out = _npolys(ctx, out) // 2
     _check(lib().hc_ctpt_mac(ctx.ptr, _dptr(ct), _dptr(pt_ntt), C.c_void_p(sl.ctypes.data), sl.size,
                              _dptr(out), n_out, _stream(stream)))
+
+
+class Plan(_Handle):
+    """A plan handle; keeps the contexts, weights and tensors it refers to alive."""
+
+
+def work_conv(ctx, w, ct_in, ct_out):
+    """Plan item: one conv layer (hc_conv_ct_pt's arguments)."""
+    return (HC_WORK_CONV, ctx, w, ct_in, None, ct_out, 0)
+
+
+def work_products(ctx, ct, pt_ntt, out):
+    """Plan item: standalone products out[j] = INTT(NTT(ct[j]) . pt_ntt[j]), j < n."""
+    n = _npolys(ctx, pt_ntt)
+    if _npolys(ctx, ct) != 2 * n or _npolys(ctx, out) != 2 * n:
+        raise ValueError("ct and out must hold 2*n polynomials, pt_ntt n")
+    return (HC_WORK_PRODUCTS, ctx, None, ct, pt_ntt, out, n)
+
+
+def hc_plan_create(items):
+    """items: list of work_conv(...) / work_products(...) tuples."""
+    arr = (hc_work_item * max(1, len(items)))()
+    keep = []
+    for i, (kind, ctx, w, ct_in, pt, ct_out, n) in enumerate(items):
+        arr[i] = hc_work_item(kind, ctx.ptr, w.ptr if w is not None else None, _dptr(ct_in),
+                              _dptr(pt) if pt is not None else None, _dptr(ct_out), n)
+        keep.append((ctx, w, ct_in, pt, ct_out))
+    h = C.c_void_p()
+    _check(lib().hc_plan_create(C.cast(arr, C.c_void_p), len(items), C.byref(h)))
+    return Plan(h, keep=keep)
+
+
+def hc_plan_run(plan, stream=None):
+    _check(lib().hc_plan_run(plan.ptr, _stream(stream)))
+
+
+def hc_plan_run_plain(plan, stream=None):
+    _check(lib().hc_plan_run_plain(plan.ptr, _stream(stream)))
+
+
+def hc_plan_autotune(plan, cache_path=None, stream=None):
+    _check(lib().hc_plan_autotune(plan.ptr, cache_path.encode() if cache_path else None, _stream(stream)))
+
+
+def hc_plan_info(plan):
+    """(products, algorithmic bytes, kernel launches) of one batched run."""
+    a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint32()
+    _check(lib().hc_plan_info(plan.ptr, C.byref(a), C.byref(b), C.byref(c)))
+    return int(a.value), int(b.value), int(c.value)
+
+
+class Server(_Handle):
+    """A server handle; keeps its layers' contexts and weights alive."""
+
+
+def hc_server_create(budget_bytes=0, max_batch=0, max_inflight=0):
+    cfg = hc_server_config(budget_bytes, max_batch, max_inflight)
+    h = C.c_void_p()
+    _check(lib().hc_server_create(C.byref(cfg), C.byref(h)))
+    return Server(h, keep=[])
+
+
+def hc_server_add_layer(srv, ctx, w):
+    lid = C.c_uint32()
+    _check(lib().hc_server_add_layer(srv.ptr, ctx.ptr, w.ptr, C.byref(lid)))
+    srv._keep.append((ctx, w))
+    return int(lid.value)
+
+
+def hc_server_submit(srv, layer_id, h_in, h_out=None):
+    """Queue a request; h_in / h_out: host arrays (pinned CPU tensors or numpy), h_out None = keep on device.
+    The caller keeps both alive until the request is done.  Returns the ticket."""
+    t = C.c_uint64()
+    _check(lib().hc_server_submit(srv.ptr, layer_id, _hptr(h_in), _hptr(h_out) if h_out is not None else None,
+                                  C.byref(t)))
+    return int(t.value)
+
+
+def _info(i):
+    return {"status": int(i.status), "batch_size": int(i.batch_size), "queue_ms": float(i.queue_ms),
+            "latency_ms": float(i.latency_ms)}
+
+
+def hc_server_wait(srv, ticket, timeout_s=-1.0):
+    i = hc_request_info()
+    _check(lib().hc_server_wait(srv.ptr, ticket, timeout_s, C.byref(i)))
+    return _info(i)
+
+
+def hc_server_poll(srv, ticket):
+    """None while running, else the request's info dict."""
+    d, i = C.c_int(), hc_request_info()
+    _check(lib().hc_server_poll(srv.ptr, ticket, C.byref(d), C.byref(i)))
+    return _info(i) if d.value else None
+
+
+def hc_server_result(srv, ticket):
+    """Device address of a done request's pool-resident result."""
+    p = C.c_void_p()
+    _check(lib().hc_server_result(srv.ptr, ticket, C.byref(p)))
+    return int(p.value)
+
+
+def hc_server_fetch(srv, ticket, h_out):
+    _check(lib().hc_server_fetch(srv.ptr, ticket, _hptr(h_out)))
+
+
+def hc_server_release(srv, ticket):
+    _check(lib().hc_server_release(srv.ptr, ticket))
+
+
+def hc_server_stats_get(srv):
+    st = hc_server_stats()
+    _check(lib().hc_server_stats_get(srv.ptr, C.byref(st)))
+    return {n: int(getattr(st, n)) for n, _ in hc_server_stats._fields_}
+
+
+def hc_server_shutdown(srv):
+    _check(lib().hc_server_shutdown(srv.ptr))
 
 
 def hc_profile_enable(on=True):

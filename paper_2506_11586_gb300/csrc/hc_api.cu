@@ -611,6 +611,8 @@ void hc_free(void *handle)
         delete c;
     } else if (magic == kMagicPlan) {
         plan_destroy((hc_plan *)handle);
+    } else if (magic == kMagicServer) {
+        server_destroy((hc_server *)handle);
     } else if (magic == kMagicWeights) {
         hc_weights *w = (hc_weights *)handle;
         DeviceGuard g(w->device);

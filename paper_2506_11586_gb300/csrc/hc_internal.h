@@ -16,6 +16,7 @@ constexpr uint32_t kMaxLimbs = 8;
 constexpr uint32_t kMagicCtx = 0x48435458u;      // 'HCTX'
 constexpr uint32_t kMagicWeights = 0x48435754u;  // 'HCWT'
 constexpr uint32_t kMagicPlan = 0x4843504Cu;     // 'HCPL'
+constexpr uint32_t kMagicServer = 0x48435352u;   // 'HCSR'
 constexpr uint32_t kMagicDead = 0xDEADDEADu;
 
 // Per-limb constants and twiddle tables, device-resident, read through the
@@ -33,7 +34,7 @@ struct LimbConst {
 static_assert(sizeof(LimbConst) == 128, "LimbConst is 128 bytes");
 
 // Kernel families whose launch shape is selectable per context.
-enum KernelKind { KK_FWD = 0, KK_INV = 1, KK_MAC = 2, KK_PROD = 3, KK_FWDCT = 4, KK_INVCT = 5, KK_COUNT = 6 };
+enum KernelKind { KK_FWD = 0, KK_INV = 1, KK_MAC = 2, KK_PROD = 3, KK_FWDCT = 4, KK_INVCT = 5, KK_MACB = 6, KK_COUNT = 7 };
 constexpr int kNumVariants = 3;
 
 }  // namespace hc
@@ -139,7 +140,7 @@ struct MacSeg {
     const uint64_t *W;
     uint64_t *Y;
     const LimbConst *limbs;
-    uint32_t N, L, G, B, M, MB, chunks, groups, cta_begin;
+    uint32_t N, L, G, B, M, MB, MS, chunks, groups, cta_begin;
 };
 struct MacSegs {
     uint32_t n;
@@ -156,6 +157,21 @@ bool mac_conv_fits(uint32_t G, uint32_t B);
 hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s);
 
 void plan_destroy(hc_plan *p);
+void server_destroy(hc_server *s);
+
+// one conv layer of a batched launch sequence
+struct ConvJob {
+    const hc_ctx *ctx;
+    const hc_weights *w;
+    const uint64_t *in;   // [I][2][L][N] coefficient domain
+    uint64_t *out;        // [O][2][L][N] coefficient domain
+    uint64_t *ntt;        // scratch: NTT-domain inputs [I][2][L][N]
+    bool blocked;         // blocked MAC fits (else fused MAC + inverse NTT)
+};
+bool conv_job_blocked(const hc_ctx *c, const hc_weights *w);
+// forward NTTs of all jobs (one launch per degree), their MACs (one launch),
+// their inverse NTTs (one launch per degree); at most kMaxSegs jobs per launch
+hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s);
 
 // one standalone product of a mixed-degree batch (see k_product_mixed)
 struct MixItem {

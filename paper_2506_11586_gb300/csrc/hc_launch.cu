@@ -60,12 +60,14 @@ int default_variant(int kind, uint32_t logn)
 // A CTA owns one chunk of KC slots of one limb for every input ciphertext and
 // a group of MB output channels.  The input chunk (G*2B rows of KC slots) is
 // fetched once into shared memory by TMA bulk copies; the weight slices
-// (G rows of KC slots per channel) stream through a ring of kMacStages
-// shared-memory stages, fetched two channels ahead of the compute.  Each
-// weight slot is therefore read from memory once and each input slot once
-// per channel group.  Thread (k, h) owns slot k0 + k and the component pairs
-// p = 2b + c with p = h (mod H).  Waits are bounded: a wait that runs out sets
-// err = 2, drains this CTA's copies in flight (bounded) and ends the CTA.
+// stream through a ring of kMacStages shared-memory stages of MS channels
+// each (MS*G rows of KC slots), refilled while the other stages are in use.
+// Each weight slot is therefore read from memory once and each input slot
+// once per channel group.  Per stage the CTA computes MS*2B output rows of KC
+// slots: thread (k, h) owns slot k0 + k and the rows j = h (mod H), row
+// j = m*2B + p for channel m of the stage and component pair p = 2b + c.
+// Waits are bounded: a wait that runs out sets err = 2, drains this CTA's
+// copies in flight (bounded) and ends the CTA.
 constexpr int kMacThreads = 256;
 constexpr int kMacStages = 3;
 
@@ -83,26 +85,28 @@ k_mac_conv(const __grid_constant__ MacSegs segs, int *err)
     const uint64_t *__restrict__ X = sg.X;
     const uint64_t *__restrict__ W = sg.W;
     uint64_t *__restrict__ Y = sg.Y;
-    const LimbConst *__restrict__ limbs = sg.limbs;
-    const uint32_t N = sg.N, L = sg.L, G = sg.G, B = sg.B, M = sg.M, MB = sg.MB;
+    const uint32_t N = sg.N, L = sg.L, G = sg.G, B = sg.B, M = sg.M, MB = sg.MB, MS = sg.MS;
     const uint32_t local = blockIdx.x - sg.cta_begin;
     const uint32_t chunk = local % sg.chunks, rest = local / sg.chunks;
-    const uint32_t P = 2 * B, rows = G * P;
+    const uint32_t P = 2 * B, rows = G * P, SR = MS * G;
     uint64_t *xs = dsm;                          // [rows][KC]
-    uint64_t *ws = dsm + (size_t)rows * KC;      // [kMacStages][G][KC]
+    uint64_t *ws = dsm + (size_t)rows * KC;      // [kMacStages][SR][KC]
     const uint32_t k0 = chunk * KC, limb = rest % L;
     const uint32_t m0 = (rest / L) * MB, m1 = min(M, m0 + MB);
     const uint32_t nm = m1 > m0 ? m1 - m0 : 0;
+    const uint32_t nst = (nm + MS - 1) / MS;     // stages of this CTA
     const size_t LN = (size_t)L * N;
     const uint64_t *xsrc = X + (size_t)limb * N + k0;   // input row r at xsrc + r*LN
     const uint64_t *wsrc = W + (size_t)limb * N + k0;   // weight poly j at wsrc + j*LN
     const int tid = threadIdx.x;
 
-    auto issue_w = [&](uint32_t i) {  // weight slice of channel m0 + i into stage i % kMacStages
-        const uint32_t st = i % kMacStages;
-        mbar_arrive_expect_tx(&bars[1 + st], G * ROW_BYTES);
-        const uint64_t *src = wsrc + (size_t)(m0 + i) * G * LN;
-        for (uint32_t g = 0; g < G; ++g) bulk_g2s(ws + ((size_t)st * G + g) * KC, src + g * LN, ROW_BYTES, &bars[1 + st]);
+    auto issue_w = [&](uint32_t i) {  // channels m0 + i*MS ... into stage i % kMacStages
+        const uint32_t st = i % kMacStages, c0 = m0 + i * MS;
+        const uint32_t nr = min(MS, m1 - c0) * G;
+        mbar_arrive_expect_tx(&bars[1 + st], nr * ROW_BYTES);
+        const uint64_t *src = wsrc + (size_t)c0 * G * LN;
+        uint64_t *dst = ws + (size_t)st * SR * KC;
+        for (uint32_t r = 0; r < nr; ++r) bulk_g2s(dst + (size_t)r * KC, src + r * LN, ROW_BYTES, &bars[1 + st]);
     };
     if (tid == 0) {
         for (int i = 0; i < 1 + kMacStages; ++i) mbar_init(&bars[i], 1);
@@ -112,32 +116,35 @@ k_mac_conv(const __grid_constant__ MacSegs segs, int *err)
     if (tid == 0) {
         mbar_arrive_expect_tx(&bars[0], rows * ROW_BYTES);
         for (uint32_t r = 0; r < rows; ++r) bulk_g2s(xs + (size_t)r * KC, xsrc + r * LN, ROW_BYTES, &bars[0]);
-        for (uint32_t i = 0; i < (uint32_t)kMacStages && i < nm; ++i) issue_w(i);
+        for (uint32_t i = 0; i < (uint32_t)kMacStages && i < nst; ++i) issue_w(i);
     }
 
-    const LimbConst &lc = limbs[limb];
+    const LimbConst &lc = sg.limbs[limb];
     const uint64_t q = lc.q, nq = 0ull - q, r64 = lc.r64, r64_s = lc.r64_s;
     const uint32_t ones = (uint32_t)lc.one_s;
     const uint32_t k = tid % KC, h = tid / KC;  // h is warp-uniform
+    const uint32_t xstep = P * KC;
     bool ok = mbar_wait(&bars[0], 0);
     uint32_t i = 0;
-    for (; i < nm; ++i) {
+    for (; i < nst; ++i) {
         const uint32_t st = i % kMacStages;
         ok = mbar_wait(&bars[1 + st], (i / kMacStages) & 1) && ok;
-        ok = __syncthreads_and(ok);  // also: every thread has finished channel i - 1
+        ok = __syncthreads_and(ok);  // also: every thread has finished stage i - 1
         if (!ok) break;
-        if (tid == 0 && i >= 1 && i - 1 + kMacStages < nm) {
+        if (tid == 0 && i >= 1 && i - 1 + kMacStages < nst) {
             fence_proxy_async();
-            issue_w(i - 1 + kMacStages);  // into the stage channel i - 1 used
+            issue_w(i - 1 + kMacStages);  // into the stage that stage i - 1 used
         }
-        const uint64_t *wk = ws + (size_t)st * G * KC + k;
-        uint64_t *yk = Y + (size_t)limb * N + k0 + k + (size_t)(m0 + i) * P * LN;
-        for (uint32_t p = h; p < P; p += H) {
+        const uint32_t c0 = m0 + i * MS, jobs = min(MS, m1 - c0) * P;
+        const uint64_t *wst = ws + (size_t)st * SR * KC + k;
+        uint64_t *yk = Y + (size_t)limb * N + k0 + k + (size_t)c0 * P * LN;
+        uint32_t ml = h / P, p = h % P;  // row j = ml*P + p, stepping by H
+        for (uint32_t j = h; j < jobs; j += H) {
             MacAcc acc0, acc1;  // two chains over alternating terms for latency hiding
             mac_zero(acc0);
             mac_zero(acc1);
             const uint64_t *xp = xs + (size_t)p * KC + k;
-            const uint32_t xstep = P * KC;
+            const uint64_t *wk = wst + (size_t)ml * G * KC;
             uint32_t g = 0;
             for (; g + 1 < G; g += 2) {
                 mac_add(acc0, xp[0], wk[g * KC]);
@@ -146,23 +153,42 @@ k_mac_conv(const __grid_constant__ MacSegs segs, int *err)
             }
             if (g < G) mac_add(acc0, xp[0], wk[g * KC]);
             mac_merge(acc0, acc1);
-            yk[(size_t)p * LN] = mac_reduce(acc0, q, nq, r64, r64_s, ones);
+            yk[(size_t)j * LN] = mac_reduce(acc0, q, nq, r64, r64_s, ones);
+            p += H;
+            while (p >= P) {
+                p -= P;
+                ++ml;
+            }
         }
     }
     if (!ok && tid == 0) {
         atomicExch(err, 2);
         // drain this CTA's bulk copies still in flight before its shared memory is released
         mbar_wait(&bars[0], 0);
-        const uint32_t last = i == 0 ? min(nm, (uint32_t)kMacStages) : min(nm, i - 1 + kMacStages);
+        const uint32_t last = i == 0 ? min(nst, (uint32_t)kMacStages) : min(nst, i - 1 + kMacStages);
         for (uint32_t j = i; j < last; ++j) mbar_wait(&bars[1 + j % kMacStages], (j / kMacStages) & 1);
     }
 }
 
 constexpr int kMacKC = 64;
 
-static size_t mac_smem(uint32_t G, uint32_t B)
+// stage rows targeted by each launch variant of the blocked MAC
+constexpr uint32_t kMacStageRows[kNumVariants] = {8, 16, 32};
+constexpr size_t kMacSmemCap = 200 * 1024;
+
+static size_t mac_smem(uint32_t G, uint32_t B, uint32_t MS)
 {
-    return ((size_t)G * 2 * B + (size_t)kMacStages * G) * kMacKC * sizeof(uint64_t);
+    return ((size_t)G * 2 * B + (size_t)kMacStages * MS * G) * kMacKC * sizeof(uint64_t);
+}
+
+// channels per stage: about the variant's stage rows, within the shared-memory cap
+static uint32_t mac_stage_channels(uint32_t G, uint32_t B, uint32_t M, int variant)
+{
+    uint32_t ms = kMacStageRows[variant] / G;
+    if (ms < 1) ms = 1;
+    if (ms > M) ms = M;
+    while (ms > 1 && mac_smem(G, B, ms) > kMacSmemCap / 2) --ms;  // keep two CTAs per SM where possible
+    return ms;
 }
 
 // fill the launch geometry of one segment: enough CTAs for about four waves
@@ -179,13 +205,15 @@ static MacSeg mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, u
     sg.G = G;
     sg.B = B;
     sg.M = M;
-    const size_t smem = mac_smem(G, B);
-    const uint32_t per_sm = (uint32_t)((200 * 1024) / smem) < 4 ? (uint32_t)((200 * 1024) / smem) : 4;
+    sg.MS = mac_stage_channels(G, B, M, ctx->variant[KK_MACB]);
+    const size_t smem = mac_smem(G, B, sg.MS);
+    const uint32_t per_sm = (uint32_t)(kMacSmemCap / smem) < 4 ? (uint32_t)(kMacSmemCap / smem) : 4;
     sg.chunks = ctx->N / kMacKC;
     const uint32_t target = 152 * (per_sm ? per_sm : 1) * 4;
     const uint32_t want = (target + sg.chunks * ctx->L - 1) / (sg.chunks * ctx->L);
     const uint32_t groups = want < 1 ? 1 : (want > M ? M : want);
     sg.MB = (M + groups - 1) / groups;
+    sg.MB = (sg.MB + sg.MS - 1) / sg.MS * sg.MS;  // whole stages per CTA
     sg.groups = (M + sg.MB - 1) / sg.MB;
     return sg;
 }
@@ -197,7 +225,7 @@ static hc_status run_mac_segs(MacSegs &segs, size_t smem, int *err, cudaStream_t
     cudaGetDevice(&dev);
     if (!(attr_done.load() & (1u << (dev & 31)))) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_mac_conv<kMacKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(k_mac_conv<kMacKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMacSmemCap);
         if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_mac_conv)");
         attr_done.fetch_or(1u << (dev & 31));
     }
@@ -214,7 +242,7 @@ static hc_status run_mac_segs(MacSegs &segs, size_t smem, int *err, cudaStream_t
 
 bool mac_conv_fits(uint32_t G, uint32_t B)
 {
-    return mac_smem(G, B) <= 200 * 1024;
+    return mac_smem(G, B, 1) <= kMacSmemCap;
 }
 
 hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64_t *w_ntt, uint64_t *y, uint32_t G,
@@ -224,7 +252,7 @@ hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64
     MacSegs segs{};
     segs.n = 1;
     segs.s[0] = mac_seg(ctx, x_ntt, w_ntt, y, G, B, M);
-    return run_mac_segs(segs, mac_smem(G, B), ctx->d_flag + 1, s);
+    return run_mac_segs(segs, mac_smem(G, B, segs.s[0].MS), ctx->d_flag + 1, s);
 }
 
 hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s)
@@ -236,8 +264,8 @@ hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *laye
         for (size_t i = i0; i < i1; ++i) {
             const MacLayer &ly = layers[i];
             if (!mac_conv_fits(ly.G, ly.B)) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
-            segs.s[segs.n++] = mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M);
-            const size_t sm = mac_smem(ly.G, ly.B);
+            segs.s[segs.n] = mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M);
+            const size_t sm = mac_smem(ly.G, ly.B, segs.s[segs.n++].MS);
             if (sm > smem) smem = sm;
         }
         hc_status st = run_mac_segs(segs, smem, ctxs[i0]->d_flag + 1, s);

@@ -17,14 +17,7 @@ using namespace hc;
 
 namespace {
 
-struct PlanConv {
-    const hc_ctx *ctx;
-    const hc_weights *w;
-    const uint64_t *in;
-    uint64_t *out;
-    uint64_t *ntt;    // plan scratch: NTT-domain inputs [I][2][L][N]
-    bool blocked;     // blocked MAC fits in shared memory (else fused MAC + INTT)
-};
+using PlanConv = ConvJob;
 
 struct PlanProd {
     const hc_ctx *ctx;
@@ -115,70 +108,12 @@ hc_status check_overlaps(const std::vector<hc_work_item> &items)
 // ---- the batched launch sequence ---------------------------------------------
 hc_status run_batched(hc_plan *p, cudaStream_t s)
 {
-    // forward NTT of every conv input, one launch per ring degree (per 48 items)
-    for (uint32_t logN = 12; logN <= 14; ++logN) {
-        NttSegs segs{};
-        const hc_ctx *first = nullptr;
-        auto flush = [&]() -> hc_status {
-            if (!segs.n) return HC_OK;
-            hc_status st = launch_ntt_ct_segs(first, segs, false, s);
-            segs.n = 0;
-            first = nullptr;
-            return st;
-        };
-        for (const PlanConv &c : p->convs) {
-            if (c.ctx->logN != logN) continue;
-            if (!first) first = c.ctx;
-            segs.s[segs.n++] = NttSeg{c.in, c.ntt, c.ctx->d_limbs, c.ctx->L, c.w->I, 0};
-            if (segs.n == kMaxSegs) {
-                hc_status st = flush();
-                if (st != HC_OK) return st;
-            }
-        }
-        hc_status st = flush();
-        if (st != HC_OK) return st;
-    }
-    // NTT-domain MAC of every conv item that has a blocked MAC, one launch
-    std::vector<const hc_ctx *> mctx;
-    std::vector<MacLayer> layers;
-    for (const PlanConv &c : p->convs) {
-        if (c.blocked) {
-            mctx.push_back(c.ctx);
-            layers.push_back(MacLayer{c.ntt, c.w->d_pt, c.out, c.w->G, c.w->B, c.w->desc.M});
-        } else {
-            hc_status st = launch_mac_intt(c.ctx, c.ntt, c.w->d_pt, MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out,
-                                           c.w->O, s);
-            if (st != HC_OK) return st;
-        }
-    }
-    if (!layers.empty()) {
-        hc_status st = launch_mac_conv_layers(mctx.data(), layers.data(), layers.size(), s);
-        if (st != HC_OK) return st;
-    }
-    // inverse NTT of every blocked-MAC output, in place, one launch per ring degree
-    for (uint32_t logN = 12; logN <= 14; ++logN) {
-        NttSegs segs{};
-        const hc_ctx *first = nullptr;
-        for (const PlanConv &c : p->convs) {
-            if (c.ctx->logN != logN || !c.blocked) continue;
-            if (!first) first = c.ctx;
-            segs.s[segs.n++] = NttSeg{c.out, c.out, c.ctx->d_limbs, c.ctx->L, c.w->O, 0};
-            if (segs.n == kMaxSegs) {
-                hc_status st = launch_ntt_ct_segs(first, segs, true, s);
-                if (st != HC_OK) return st;
-                segs.n = 0;
-                first = nullptr;
-            }
-        }
-        if (segs.n) {
-            hc_status st = launch_ntt_ct_segs(first, segs, true, s);
-            if (st != HC_OK) return st;
-        }
-    }
+    hc_status st = launch_conv_jobs(p->convs.data(), p->convs.size(), s);
+    if (st != HC_OK) return st;
     // every standalone product, one persistent launch
     if (p->n_units) {
         HC_CUDA_TRY(cudaMemsetAsync(p->d_next, 0, sizeof(uint32_t), s));
-        hc_status st = launch_product_mixed(p->d_items, p->d_units, p->n_units, p->d_next, s);
+        st = launch_product_mixed(p->d_items, p->d_units, p->n_units, p->d_next, s);
         if (st != HC_OK) return st;
     }
     return HC_OK;
@@ -298,6 +233,70 @@ hc_status time_batched(hc_plan *p, cudaStream_t s, int reps, float *ms)
 }  // namespace
 
 namespace hc {
+bool conv_job_blocked(const hc_ctx *c, const hc_weights *w) { return mac_conv_fits(w->G, w->B) && c->N % 64 == 0; }
+
+// the batched launch sequence of n conv jobs (all degrees), in stream order on s
+hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s)
+{
+    // forward NTT of every conv input, one launch per ring degree (per kMaxSegs jobs)
+    for (uint32_t logN = 12; logN <= 14; ++logN) {
+        NttSegs segs{};
+        const hc_ctx *first = nullptr;
+        for (size_t i = 0; i <= n; ++i) {
+            if (i < n) {
+                const ConvJob &c = jobs[i];
+                if (c.ctx->logN != logN) continue;
+                if (!first) first = c.ctx;
+                segs.s[segs.n++] = NttSeg{c.in, c.ntt, c.ctx->d_limbs, c.ctx->L, c.w->I, 0};
+            }
+            if (segs.n && (segs.n == kMaxSegs || i == n)) {
+                hc_status st = launch_ntt_ct_segs(first, segs, false, s);
+                if (st != HC_OK) return st;
+                segs.n = 0;
+                first = nullptr;
+            }
+        }
+    }
+    // NTT-domain MAC of every job with a blocked MAC, one launch (per kMaxSegs jobs)
+    std::vector<const hc_ctx *> mctx;
+    std::vector<MacLayer> layers;
+    for (size_t i = 0; i < n; ++i) {
+        const ConvJob &c = jobs[i];
+        if (c.blocked) {
+            mctx.push_back(c.ctx);
+            layers.push_back(MacLayer{c.ntt, c.w->d_pt, c.out, c.w->G, c.w->B, c.w->desc.M});
+        } else {
+            hc_status st = launch_mac_intt(c.ctx, c.ntt, c.w->d_pt, MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out,
+                                           c.w->O, s);
+            if (st != HC_OK) return st;
+        }
+    }
+    if (!layers.empty()) {
+        hc_status st = launch_mac_conv_layers(mctx.data(), layers.data(), layers.size(), s);
+        if (st != HC_OK) return st;
+    }
+    // inverse NTT of every blocked-MAC output, in place, one launch per ring degree
+    for (uint32_t logN = 12; logN <= 14; ++logN) {
+        NttSegs segs{};
+        const hc_ctx *first = nullptr;
+        for (size_t i = 0; i <= n; ++i) {
+            if (i < n) {
+                const ConvJob &c = jobs[i];
+                if (c.ctx->logN != logN || !c.blocked) continue;
+                if (!first) first = c.ctx;
+                segs.s[segs.n++] = NttSeg{c.out, c.out, c.ctx->d_limbs, c.ctx->L, c.w->O, 0};
+            }
+            if (segs.n && (segs.n == kMaxSegs || i == n)) {
+                hc_status st = launch_ntt_ct_segs(first, segs, true, s);
+                if (st != HC_OK) return st;
+                segs.n = 0;
+                first = nullptr;
+            }
+        }
+    }
+    return HC_OK;
+}
+
 void plan_destroy(hc_plan *p)
 {
     DeviceGuard g(p->device);
@@ -350,7 +349,7 @@ hc_status hc_plan_create(const hc_work_item *items, size_t n, hc_plan **out)
         const uint64_t nl = (uint64_t)c->N * c->L * 8;
         if (it.kind == HC_WORK_CONV) {
             const hc_weights *w = it.weights;
-            p->convs.push_back(PlanConv{c, w, it.d_ct_in, it.d_ct_out, nullptr, mac_conv_fits(w->G, w->B) && c->N % 64 == 0});
+            p->convs.push_back(PlanConv{c, w, it.d_ct_in, it.d_ct_out, nullptr, conv_job_blocked(c, w)});
             scratch_words += (size_t)w->I * ct_words(c);
             p->n_products += (uint64_t)w->desc.M * w->G * w->B;
             p->alg_bytes += nl * (2ull * w->I + w->P + 2ull * w->O);
@@ -482,6 +481,7 @@ hc_status hc_plan_autotune(hc_plan *p, const char *cache_path, void *cuda_stream
             }
         hc_ctx *mc = const_cast<hc_ctx *>(c);  // variants are a documented mutable hint
         if (any) knobs.push_back(Knob{mc, KK_FWDCT});
+        if (blocked) knobs.push_back(Knob{mc, KK_MACB});
         if (blocked) knobs.push_back(Knob{mc, KK_INVCT});
         if (fused) knobs.push_back(Knob{mc, KK_MAC});
     }

@@ -189,3 +189,50 @@ def uneven_mix(n_products: int, seed: int):
     labels = np.concatenate([np.full(c, i, dtype=np.int64) for i, c in enumerate(counts)])
     keys = Stream(seed, 7).u64(n_products)
     return labels[np.argsort(keys, kind="stable")]
+
+
+# ---- serving workload ------------------------------------------------------------
+
+# How many times each distinct stride-1 ResNet-50 (v1.5) convolution shape
+# occurs in the network (the 3x3 stride-2 convolutions and stride-2
+# projection shortcuts of the first block of stages 3-5 are not stride-1; the
+# stride-1 projection shortcut 64 -> 256 of stage 2 has res2.conv3's shape).
+# Each occurrence has its own weights: about 47 GB of NTT-domain weights at
+# N = 16384 with four 50-bit primes.
+RESNET50_MULTIPLICITY = {
+    "res2.conv1_in64": 1, "res2.conv2": 3, "res2.conv3": 4, "res2.conv1": 2,
+    "res3.conv1_in256": 1, "res3.conv2": 3, "res3.conv3": 4, "res3.conv1": 3,
+    "res4.conv1_in512": 1, "res4.conv2": 5, "res4.conv3": 6, "res4.conv1": 5,
+    "res5.conv1_in1024": 1, "res5.conv2": 2, "res5.conv3": 3, "res5.conv1": 2,
+}
+
+
+def resnet50_instances():
+    """Every stride-1 convolution instance of ResNet-50: list of (ConvShape, occurrence)."""
+    return [(sh, k) for sh in RESNET50_STRIDE1 for k in range(RESNET50_MULTIPLICITY[sh.name])]
+
+
+@dataclass(frozen=True)
+class ServingTrace:
+    """Request arrivals: times in seconds from the start, and for each request
+    its family (0 = SqueezeNet-1.1 at N = 8192, 1 = ResNet-50 at N = 16384)
+    and its layer index within that family."""
+    t: np.ndarray
+    family: np.ndarray
+    layer: np.ndarray
+
+
+def serving_trace(n_requests: int, rate: float, seed: int, n_layers=None) -> ServingTrace:
+    """Poisson arrivals at `rate` requests/s (exponential gaps by inversion),
+    each request a fair coin between the two families and then a uniform
+    layer of that family."""
+    if n_layers is None:
+        n_layers = (len(SQUEEZENET_1_1), len(resnet50_instances()))
+    s = Stream(seed, 11)
+    u = (s.u64(n_requests) >> np.uint64(11)).astype(np.float64) / 9007199254740992.0
+    t = np.cumsum(-np.log1p(-u) / rate)
+    fam = (s.u64(n_requests) >> np.uint64(63)).astype(np.int64)
+    r = (s.u64(n_requests) >> np.uint64(11)).astype(np.float64) / 9007199254740992.0
+    sizes = np.where(fam == 0, n_layers[0], n_layers[1])
+    layer = np.minimum((r * sizes).astype(np.int64), sizes - 1)
+    return ServingTrace(t, fam, layer)

@@ -64,13 +64,34 @@ def test_conv_and_product_variants(L, N, nl):
     out = torch.empty(p.O * 2 * nl * N, dtype=torch.int64, device="cuda")
     for vm in range(L.N_VARIANTS):
         for vf in range(L.N_VARIANTS):
-            L.hc_ctx_set_variant(ctx, L.KIND_MAC_INTT, vm)
+            L.hc_ctx_set_variant(ctx, L.KIND_MAC_CONV, vm)
             L.hc_ctx_set_variant(ctx, L.KIND_NTT_FWD_CT, vf)
+            L.hc_ctx_set_variant(ctx, L.KIND_NTT_INV_CT, vf)
             out.fill_(-1)
             L.hc_conv_ct_pt(ctx, w, d_in, out)
             torch.cuda.synchronize()
             got = to_host(out).reshape(p.O, 2, nl, N)
             assert np.array_equal(got[..., ks], want), (vm, vf)
+    # fused MAC + inverse NTT (general slot lists): every output slot sums two products
+    slots = np.arange(p.I) // 2
+    n_out = int(slots.max()) + 1
+    pt_c = uniform_residues(Stream(11, N), moduli, (p.I,), N)
+    ptn = to_dev(pt_c)
+    L.hc_ntt_fwd(ctx, ptn)
+    want_m = np.zeros((n_out, 2, nl, len(ks)), dtype=object)
+    for j in range(p.I):
+        for c in range(2):
+            for li, q in enumerate(moduli):
+                want_m[slots[j], c, li] += core.negacyclic(ct[j, c, li], pt_c[j, li], q, ks).astype(object)
+    for li, q in enumerate(moduli):
+        want_m[:, :, li] %= q
+    mo = torch.empty(n_out * 2 * nl * N, dtype=torch.int64, device="cuda")
+    for vm in range(L.N_VARIANTS):
+        L.hc_ctx_set_variant(ctx, L.KIND_MAC_INTT, vm)
+        mo.fill_(-1)
+        L.hc_ctpt_mac(ctx, d_in, ptn, slots, mo)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(mo).reshape(n_out, 2, nl, N)[..., ks], want_m.astype(np.uint64)), vm
     # standalone fused products: out[j] = ct[j] * pt[j]
     n = 5
     pc = uniform_residues(Stream(9, N), moduli, (n, 2), N)
@@ -89,6 +110,37 @@ def test_conv_and_product_variants(L, N, nl):
         L.hc_ctpt_mac(ctx, to_dev(pc), ptn, np.arange(n), po)
         torch.cuda.synchronize()
         assert np.array_equal(to_host(po).reshape(n, 2, nl, N)[..., ks], want_p), v
+
+
+def test_blocked_mac_stage_ring_wraps(L):
+    """A 1x1 layer with many output channels at N = 16384, L = 4: every CTA
+    streams more weight stages than the ring holds, under every stage-size
+    variant; sampled coefficients of a spread of outputs vs the oracle."""
+    N, nl, C_, H, W, M = 16384, 4, 64, 16, 16, 300
+    moduli = CANONICAL_PRIMES[:nl]
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    s = Stream(12, N)
+    K = s.int8(M * C_).astype(np.int64).reshape(M, C_, 1, 1)
+    p = conv.canonical_partition(C_, H, W, M, 1, 1, 0, N)
+    ct = uniform_residues(s, moduli, (p.I, 2), N)
+    w = L.hc_weights_preprocess(ctx, L.make_desc(C_, H, W, M, 1, 1), K.astype(np.int8))
+    ks = sample_indices(N, 8, 4)
+    outs = [0, 1, 37, 150, p.O - 2, p.O - 1]
+    want = conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, moduli, ks, outputs=outs)
+    d_in = to_dev(ct)
+    out = torch.empty(p.O * 2 * nl * N, dtype=torch.int64, device="cuda")
+    ref = None
+    for vm in range(L.N_VARIANTS):
+        L.hc_ctx_set_variant(ctx, L.KIND_MAC_CONV, vm)
+        out.fill_(-1)
+        L.hc_conv_ct_pt(ctx, w, d_in, out)
+        L.hc_ctx_device_status(ctx)
+        torch.cuda.synchronize()
+        got = to_host(out).reshape(p.O, 2, nl, N)
+        assert np.array_equal(got[outs][..., ks], want), vm
+        if ref is None:
+            ref = out.clone()
+        assert torch.equal(out, ref), vm
 
 
 def test_variant_argument_errors(L):
