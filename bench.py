@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-reps", type=int, default=20)
+    ap.add_argument("--no-batched-plain", action="store_true", help="skip the one-launch-per-product comparisons")
     ap.add_argument("--serving-requests", type=int, default=6000)
     ap.add_argument("--serving-rate", type=float, default=200.0)
     return ap.parse_args()
@@ -283,17 +285,20 @@ def _events_ms(fn, reps, stream, flush=None):
     return out
 
 
-def _kernel_trace(L, fn):
+def _kernel_trace(L, fn, nvtx_name):
+    """Per-kernel device times of one call of fn (library trace), inside an NVTX range."""
     import torch
     L.hc_profile_collect()
     L.hc_profile_enable(True)
+    torch.cuda.nvtx.range_push(nvtx_name)
     fn()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     L.hc_profile_enable(False)
     return {k: {"launches": v[0], "ms": v[1]} for k, v in L.hc_profile_collect().items()}
 
 
-def batched_squeezenet(L, stream, reps=20):
+def batched_squeezenet(L, stream, reps=20, with_plain=True):
     """All 25 stride-1 SqueezeNet-1.1 layers as one plan (CUDA graph) vs per-layer calls vs plain."""
     import numpy as np
     import torch
@@ -321,23 +326,26 @@ def batched_squeezenet(L, stream, reps=20):
     per_layer()
     pl = _events_ms(per_layer, max(3, reps // 2), stream)
     exact_layers = all(bool(torch.equal(x, b)) for x, (_, _, b) in zip(batched, items))
-    pp = _events_ms(lambda: L.hc_plan_run_plain(plan, stream), 1, stream)
-    exact_plain = all(bool(torch.equal(x, b)) for x, (_, _, b) in zip(batched, items))
-    kern = _kernel_trace(L, lambda: L.hc_plan_run(plan, stream))
+    pp, exact_plain = [None], None
+    if with_plain:
+        pp = _events_ms(lambda: L.hc_plan_run_plain(plan, stream), 1, stream)
+        exact_plain = all(bool(torch.equal(x, b)) for x, (_, _, b) in zip(batched, items))
+    kern = _kernel_trace(L, lambda: L.hc_plan_run(plan, stream), "squeezenet_plan")
     ms = statistics.median(g)
     out = {"workload": "squeezenet1.1_stride1_25layers_N8192_L3", "products": products, "alg_bytes": nbytes,
            "launches_per_pass": launches, "batched_ms": ms, "batched_p99_ms": max(g),
            "value": products / (ms / 1e3), "unit": UNIT, "alg_gbs": nbytes / (ms / 1e3) / 1e9,
            "per_layer_ms": statistics.median(pl), "per_layer_launches": 3 * len(items),
            "plain_ms": pp[0], "plain_launches": products,
-           "speedup_vs_per_layer": statistics.median(pl) / ms, "speedup_vs_plain": pp[0] / ms,
+           "speedup_vs_per_layer": statistics.median(pl) / ms,
+           "speedup_vs_plain": pp[0] / ms if pp[0] is not None else None,
            "bit_exact_vs_per_layer": exact_layers, "bit_exact_vs_plain": exact_plain, "kernels": kern,
            "variants": {name: L.hc_ctx_get_variant(ctx, k) for name, k in KIND_NAMES.items()}}
     plan.close()
     return out
 
 
-def batched_uneven(L, stream, reps=20):
+def batched_uneven(L, stream, reps=20, with_plain=True):
     """2000 standalone products of mixed degree in one persistent launch vs per-degree vs plain."""
     import numpy as np
     import torch
@@ -367,15 +375,19 @@ def batched_uneven(L, stream, reps=20):
     per_degree()
     pd = _events_ms(per_degree, reps, stream)
     exact_deg = all(bool(torch.equal(x, it[3])) for x, it in zip(batched, items))
-    pp = _events_ms(lambda: L.hc_plan_run_plain(plan, stream), 2, stream)
-    exact_plain = all(bool(torch.equal(x, it[3])) for x, it in zip(batched, items))
-    kern = _kernel_trace(L, lambda: L.hc_plan_run(plan, stream))
+    pp, exact_plain = [None], None
+    if with_plain:
+        pp = _events_ms(lambda: L.hc_plan_run_plain(plan, stream), 2, stream)
+        exact_plain = all(bool(torch.equal(x, it[3])) for x, it in zip(batched, items))
+    kern = _kernel_trace(L, lambda: L.hc_plan_run(plan, stream), "uneven_plan")
     ms = statistics.median(g)
     out = {"workload": "uneven_2000_products_40_40_20_N4096L2_N8192L3_N16384L4", "products": products,
            "alg_bytes": nbytes, "launches_per_pass": launches, "batched_ms": ms, "batched_p99_ms": max(g),
            "value": products / (ms / 1e3), "unit": UNIT, "alg_gbs": nbytes / (ms / 1e3) / 1e9,
-           "per_degree_ms": statistics.median(pd), "plain_ms": statistics.median(pp), "plain_launches": products,
-           "speedup_vs_per_degree": statistics.median(pd) / ms, "speedup_vs_plain": statistics.median(pp) / ms,
+           "per_degree_ms": statistics.median(pd),
+           "plain_ms": statistics.median(pp) if pp[0] is not None else None, "plain_launches": products,
+           "speedup_vs_per_degree": statistics.median(pd) / ms,
+           "speedup_vs_plain": statistics.median(pp) / ms if pp[0] is not None else None,
            "bit_exact_vs_per_degree": exact_deg, "bit_exact_vs_plain": exact_plain, "kernels": kern}
     plan.close()
     return out
@@ -516,7 +528,9 @@ def run_gb300(args):
 
     batched = serving = None
     if rank == 0 and not args.no_batched:
-        batched = {"squeezenet": batched_squeezenet(L, stream), "uneven": batched_uneven(L, stream)}
+        wp = not args.no_batched_plain
+        batched = {"squeezenet": batched_squeezenet(L, stream, args.batched_reps, wp),
+                   "uneven": batched_uneven(L, stream, args.batched_reps, wp)}
     if rank == 0 and args.serving_requests > 0:
         from paper_2506_11586_gb300 import serving as srv_mod
         layers = srv_mod.ServingLayers()

@@ -83,6 +83,15 @@ hc_status hc_ctx_validate(uint32_t N, const uint64_t *moduli, uint32_t L, uint64
 hc_status hc_ctx_info(const hc_ctx *ctx, uint32_t *N, uint32_t *L, uint64_t *t,
                       uint64_t *moduli_out, uint64_t *psi_out);
 
+/* Self-test of device-side failure detection (no counterpart in the paper).
+ * Launches one CTA that waits on an mbarrier nothing arrives at, with the
+ * same bounded wait the pipelined kernels use but at most `limit` (1..2^20)
+ * attempts; the wait runs out, the CTA records a timeout in the context's
+ * device flag and exits, leaving the device usable.  A following
+ * hc_ctx_device_status returns HC_ERR_TIMEOUT (and clears the flag).
+ * Errors: HC_ERR_INVALID_ARG, HC_ERR_CUDA. */
+hc_status hc_selftest_wait_timeout(const hc_ctx *ctx, uint32_t limit, void *cuda_stream);
+
 /* Launch-shape tuning (no counterpart in the paper: a GPU scheduling knob).
  * Kernel families (kind): 0 forward NTT, 1 inverse NTT, 2 fused NTT-domain
  * MAC + inverse NTT, 3 fused standalone product, 4 forward NTT of whole

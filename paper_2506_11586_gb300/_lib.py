@@ -80,6 +80,7 @@ _SIGS = {
     "hc_ctx_validate": (C.c_int, [C.c_uint32, _P, C.c_uint32, C.c_uint64]),
     "hc_ctx_device_status": (C.c_int, [_P, _P]),
     "hc_ctx_set_variant": (C.c_int, [_P, C.c_uint32, C.c_uint32]),
+    "hc_selftest_wait_timeout": (C.c_int, [_P, C.c_uint32, _P]),
     "hc_ctx_get_variant": (C.c_int, [_P, C.c_uint32, C.POINTER(C.c_uint32)]),
     "hc_ctx_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), _P, _P]),
     "hc_ntt_fwd": (C.c_int, [_P, _P, C.c_size_t, _P]),
@@ -224,6 +225,10 @@ N_VARIANTS = 3
 def hc_ctx_device_status(ctx, stream=None):
     """Synchronise the stream; raise HcError(HC_ERR_TIMEOUT) if a bounded device wait ran out."""
     _check(lib().hc_ctx_device_status(ctx.ptr, _stream(stream)))
+
+
+def hc_selftest_wait_timeout(ctx, limit=256, stream=None):
+    _check(lib().hc_selftest_wait_timeout(ctx.ptr, limit, _stream(stream)))
 
 
 def hc_ctx_set_variant(ctx, kind, variant):

@@ -318,6 +318,14 @@ hc_status hc_ctx_device_status(const hc_ctx *ctx, void *cuda_stream)
     return HC_OK;
 }
 
+hc_status hc_selftest_wait_timeout(const hc_ctx *ctx, uint32_t limit, void *cuda_stream)
+{
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (limit == 0 || limit > (1u << 20)) return set_error(HC_ERR_INVALID_ARG, "limit must be in [1, 2^20]");
+    DeviceGuard g(ctx->device);
+    return launch_wait_selftest(ctx, limit, as_stream(cuda_stream));
+}
+
 hc_status hc_ctx_set_variant(hc_ctx *ctx, uint32_t kind, uint32_t variant)
 {
     if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");

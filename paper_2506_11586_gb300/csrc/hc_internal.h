@@ -130,10 +130,13 @@ struct NttSeg {
     uint32_t L, n_groups, cta_begin;
 };
 constexpr int kMaxSegs = 48;
-struct NttSegs {
+template <int NS>
+struct NttSegsT {
     uint32_t n;
-    NttSeg s[kMaxSegs];
+    NttSeg s[NS];
 };
+using NttSegs = NttSegsT<kMaxSegs>;  // multi-layer launches
+using NttSegs1 = NttSegsT<1>;        // one segment: a small kernel-parameter block
 // one layer of a multi-layer blocked-MAC launch (see k_mac_conv)
 struct MacSeg {
     const uint64_t *X;
@@ -142,10 +145,13 @@ struct MacSeg {
     const LimbConst *limbs;
     uint32_t N, L, G, B, M, MB, MS, chunks, groups, cta_begin;
 };
-struct MacSegs {
+template <int NS>
+struct MacSegsT {
     uint32_t n;
-    MacSeg s[kMaxSegs];
+    MacSeg s[NS];
 };
+using MacSegs = MacSegsT<kMaxSegs>;  // multi-layer launches
+using MacSegs1 = MacSegsT<1>;        // one layer: a small kernel-parameter block
 struct MacLayer {
     const uint64_t *x;
     const uint64_t *w;
@@ -157,6 +163,7 @@ bool mac_conv_fits(uint32_t G, uint32_t B);
 hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s);
 
 void plan_destroy(hc_plan *p);
+hc_status launch_wait_selftest(const hc_ctx *ctx, uint32_t limit, cudaStream_t s);
 void server_destroy(hc_server *s);
 
 // one conv layer of a batched launch sequence

@@ -40,7 +40,8 @@ template <int LOGN, int V, bool SINGLE>
 using VCfg = NttCfg<LOGN, Variant<LOGN, V>::LOGC, SINGLE ? 1 : Variant<LOGN, V>::NP, Variant<LOGN, V>::MINB>;
 
 // segment of a multi-segment launch that owns this CTA (segments in CTA order)
-__device__ __forceinline__ const NttSeg &find_seg(const NttSegs &segs)
+template <int NS>
+__device__ __forceinline__ const NttSeg &find_seg(const NttSegsT<NS> &segs)
 {
     uint32_t i = 0;
     while (i + 1 < segs.n && blockIdx.x >= segs.s[i + 1].cta_begin) ++i;
@@ -71,9 +72,9 @@ __device__ __forceinline__ void load_round0(uint64_t (&x)[Cfg::NP][Cfg::C], cons
 }
 
 // ---------------------------------------------------------------------------
-template <class Cfg>
+template <class Cfg, int NS>
 __global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
-k_ntt_fwd(const __grid_constant__ NttSegs segs)
+k_ntt_fwd(const __grid_constant__ NttSegsT<NS> segs)
 {
     extern __shared__ uint64_t sm[];
     constexpr int NP = Cfg::NP, C = Cfg::C, T = Cfg::T, N = Cfg::N;
@@ -120,9 +121,9 @@ k_ntt_fwd(const __grid_constant__ NttSegs segs)
     }
 }
 
-template <class Cfg>
+template <class Cfg, int NS>
 __global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
-k_ntt_inv(const __grid_constant__ NttSegs segs)
+k_ntt_inv(const __grid_constant__ NttSegsT<NS> segs)
 {
     extern __shared__ uint64_t sm[];
     constexpr int NP = Cfg::NP, C = Cfg::C, N = Cfg::N;
@@ -344,22 +345,22 @@ inline hc_status after_launch(const char *what)
     return e == cudaSuccess ? HC_OK : cuda_error(e, what);
 }
 
-template <class Cfg, int KIND>
-hc_status run_ntt_segs(const NttSegs &segs, cudaStream_t s, bool inverse)
+template <class Cfg, int KIND, int NS>
+hc_status run_ntt_segs(const NttSegsT<NS> &segs, cudaStream_t s, bool inverse)
 {
     uint32_t items = 0;
     for (uint32_t i = 0; i < segs.n; ++i) items = segs.s[i].cta_begin + segs.s[i].n_groups * segs.s[i].L;
     if (items == 0) return HC_OK;
     if (inverse) {
-        auto kern = k_ntt_inv<Cfg>;
-        hc_status st = prepare<Cfg, KIND>(kern, Cfg::SMEM_BYTES);
+        auto kern = k_ntt_inv<Cfg, NS>;
+        hc_status st = prepare<Cfg, KIND * 1000 + NS>(kern, Cfg::SMEM_BYTES);
         if (st != HC_OK) return st;
         ProfileScope ps(kname<Cfg>(KK_INV), s);
         kern<<<items, Cfg::T, Cfg::SMEM_BYTES, s>>>(segs);
         return after_launch("k_ntt_inv");
     }
-    auto kern = k_ntt_fwd<Cfg>;
-    hc_status st = prepare<Cfg, KIND>(kern, Cfg::SMEM_BYTES);
+    auto kern = k_ntt_fwd<Cfg, NS>;
+    hc_status st = prepare<Cfg, KIND * 1000 + NS>(kern, Cfg::SMEM_BYTES);
     if (st != HC_OK) return st;
     ProfileScope ps(kname<Cfg>(KK_FWD), s);
     kern<<<items, Cfg::T, Cfg::SMEM_BYTES, s>>>(segs);
@@ -367,9 +368,9 @@ hc_status run_ntt_segs(const NttSegs &segs, cudaStream_t s, bool inverse)
 }
 
 // one-segment launch: n_groups CTAs per limb
-inline NttSegs one_seg(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_groups)
+inline NttSegs1 one_seg(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_groups)
 {
-    NttSegs segs{};
+    NttSegs1 segs{};
     segs.n = 1;
     segs.s[0] = NttSeg{in, out, ctx->d_limbs, ctx->L, (uint32_t)n_groups, 0};
     return segs;

@@ -71,9 +71,9 @@ int default_variant(int kind, uint32_t logn)
 constexpr int kMacThreads = 256;
 constexpr int kMacStages = 3;
 
-template <int KC>
+template <int KC, int NS>
 __global__ void __launch_bounds__(kMacThreads)
-k_mac_conv(const __grid_constant__ MacSegs segs, int *err)
+k_mac_conv(const __grid_constant__ MacSegsT<NS> segs, int *err)
 {
     constexpr int H = kMacThreads / KC;
     constexpr uint32_t ROW_BYTES = KC * sizeof(uint64_t);
@@ -135,12 +135,12 @@ k_mac_conv(const __grid_constant__ MacSegs segs, int *err)
             fence_proxy_async();
             issue_w(i - 1 + kMacStages);  // into the stage that stage i - 1 used
         }
-        const uint32_t c0 = m0 + i * MS, jobs = min(MS, m1 - c0) * P;
+        const uint32_t c0 = m0 + i * MS, cnt = min(MS, m1 - c0);
         const uint64_t *wst = ws + (size_t)st * SR * KC + k;
         uint64_t *yk = Y + (size_t)limb * N + k0 + k + (size_t)c0 * P * LN;
-        uint32_t ml = h / P, p = h % P;  // row j = ml*P + p, stepping by H
-        for (uint32_t j = h; j < jobs; j += H) {
-            MacAcc acc0, acc1;  // two chains over alternating terms for latency hiding
+        // one output row: sum over the G channel groups (two chains for latency hiding)
+        auto row = [&](uint32_t ml, uint32_t p) {
+            MacAcc acc0, acc1;
             mac_zero(acc0);
             mac_zero(acc1);
             const uint64_t *xp = xs + (size_t)p * KC + k;
@@ -153,11 +153,21 @@ k_mac_conv(const __grid_constant__ MacSegs segs, int *err)
             }
             if (g < G) mac_add(acc0, xp[0], wk[g * KC]);
             mac_merge(acc0, acc1);
-            yk[(size_t)j * LN] = mac_reduce(acc0, q, nq, r64, r64_s, ones);
-            p += H;
-            while (p >= P) {
-                p -= P;
-                ++ml;
+            yk[(size_t)(ml * P + p) * LN] = mac_reduce(acc0, q, nq, r64, r64_s, ones);
+        };
+        if (P >= (uint32_t)H) {  // every row group has work in every channel
+            for (uint32_t ml = 0; ml < cnt; ++ml)
+                for (uint32_t p = h; p < P; p += H) row(ml, p);
+        } else {                 // few rows per channel: spread (channel, row) pairs over the groups
+            const uint32_t jobs = cnt * P;
+            uint32_t ml = h / P, p = h % P;
+            for (uint32_t j = h; j < jobs; j += H) {
+                row(ml, p);
+                p += H;
+                while (p >= P) {
+                    p -= P;
+                    ++ml;
+                }
             }
         }
     }
@@ -218,14 +228,15 @@ static MacSeg mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, u
     return sg;
 }
 
-static hc_status run_mac_segs(MacSegs &segs, size_t smem, int *err, cudaStream_t s)
+template <int NS>
+static hc_status run_mac_segs(MacSegsT<NS> &segs, size_t smem, int *err, cudaStream_t s)
 {
     static std::atomic<uint32_t> attr_done{0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!(attr_done.load() & (1u << (dev & 31)))) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_mac_conv<kMacKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMacSmemCap);
+        cudaError_t e = cudaFuncSetAttribute(k_mac_conv<kMacKC, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMacSmemCap);
         if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_mac_conv)");
         attr_done.fetch_or(1u << (dev & 31));
     }
@@ -236,7 +247,7 @@ static hc_status run_mac_segs(MacSegs &segs, size_t smem, int *err, cudaStream_t
     }
     if (begin == 0) return HC_OK;
     ProfileScope ps("k_mac_conv", s);
-    k_mac_conv<kMacKC><<<begin, kMacThreads, smem, s>>>(segs, err);
+    k_mac_conv<kMacKC, NS><<<begin, kMacThreads, smem, s>>>(segs, err);
     return after_launch_status("k_mac_conv");
 }
 
@@ -249,7 +260,7 @@ hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64
                           uint32_t B, uint32_t M, cudaStream_t s)
 {
     if (!mac_conv_fits(G, B) || ctx->N % kMacKC) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
-    MacSegs segs{};
+    MacSegs1 segs{};
     segs.n = 1;
     segs.s[0] = mac_seg(ctx, x_ntt, w_ntt, y, G, B, M);
     return run_mac_segs(segs, mac_smem(G, B, segs.s[0].MS), ctx->d_flag + 1, s);
@@ -272,6 +283,27 @@ hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *laye
         if (st != HC_OK) return st;
     }
     return HC_OK;
+}
+
+// Self-test of the bounded-wait error path: one CTA waits on an mbarrier that
+// nothing ever arrives at, gives up after `limit` attempts, records the
+// timeout in the context's device flag and returns.
+__global__ void k_wait_selftest(uint32_t limit, int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, limit);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 3);
+}
+
+hc_status launch_wait_selftest(const hc_ctx *ctx, uint32_t limit, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(limit, ctx->d_flag + 1);
+    return after_launch_status("k_wait_selftest");
 }
 
 namespace {
