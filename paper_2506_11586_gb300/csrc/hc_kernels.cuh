@@ -16,6 +16,7 @@
 
 #include <atomic>
 
+#include "hc_async.cuh"
 #include "hc_ntt.cuh"
 
 namespace hc {
@@ -35,6 +36,13 @@ template <> struct Variant<13, 2> { static constexpr int LOGC = 4, NP = 1, MINB 
 template <> struct Variant<14, 0> { static constexpr int LOGC = 5, NP = 1, MINB = 1; };   // T 512, 128 regs
 template <> struct Variant<14, 1> { static constexpr int LOGC = 4, NP = 1, MINB = 1; };   // T 1024, 64 regs
 template <> struct Variant<14, 2> { static constexpr int LOGC = 5, NP = 1, MINB = 1; };   // (same as 0)
+
+// shapes of the persistent TMA-fed inverse NTT (inverse kinds, variant 2, N <= 8192)
+template <int LOGN> struct InvTma;
+template <> struct InvTma<12> { using Cfg = NttCfg<12, 4, 1, 2>; };  // T 256, 2 x 32 KB
+template <> struct InvTma<13> { using Cfg = NttCfg<13, 4, 1, 1>; };  // T 512, 2 x 64 KB
+template <int LOGN, int V>
+constexpr bool use_inv_tma = V == 2 && LOGN <= 13;
 
 template <int LOGN, int V, bool SINGLE>
 using VCfg = NttCfg<LOGN, Variant<LOGN, V>::LOGC, SINGLE ? 1 : Variant<LOGN, V>::NP, Variant<LOGN, V>::MINB>;
@@ -225,6 +233,113 @@ k_mac_intt(const uint64_t *__restrict__ ct_ntt, const uint64_t *__restrict__ pt_
 }
 
 // ---------------------------------------------------------------------------
+// Persistent, TMA-fed inverse NTT of whole polynomial limbs.  A grid of
+// resident CTAs walks the units (one polynomial limb each, limb-major within
+// a segment) round robin; while a CTA transforms unit u from one
+// shared-memory buffer, the TMA engine already copies its next unit into the
+// other (one 1-D bulk copy of N words), so the global-load latency of the
+// next unit hides behind the current one's butterflies.  The copied buffer is
+// linear; thread tid needs words tid*C .. tid*C + C-1 (the inverse round-0
+// layout), which it reads as C/2 16-byte vectors in a per-thread rotated
+// order -- conflict-free for every quarter-warp -- and un-rotates in
+// registers.  The same buffer then serves the shared-memory exchanges.
+// Waits are bounded: a wait that runs out sets err = 2, drains the CTA's
+// copies in flight (bounded) and ends the CTA.
+template <int V>
+__device__ __forceinline__ void unrotate(ulonglong2 (&t)[V], uint32_t rho)
+{
+    constexpr int LOGV = V == 4 ? 2 : V == 8 ? 3 : V == 16 ? 4 : -1;
+    static_assert(LOGV > 0, "4, 8 or 16 vectors per thread");
+    static_for<0, LOGV>([&](auto kc) {
+        constexpr int S = 1 << decltype(kc)::value;
+        const bool c = (rho >> decltype(kc)::value) & 1;
+        ulonglong2 u[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) u[j] = c ? t[(j - S + V) % V] : t[j];
+#pragma unroll
+        for (int j = 0; j < V; ++j) t[j] = u[j];
+    });
+}
+
+template <class Cfg, int NS>
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
+k_ntt_inv_tma(const __grid_constant__ NttSegsT<NS> segs, uint32_t total, int *err)
+{
+    static_assert(Cfg::NP == 1, "one polynomial per unit");
+    extern __shared__ __align__(16) uint64_t sm[];  // [2][N]
+    __shared__ __align__(8) uint64_t bars[2];
+    constexpr int C = Cfg::C, N = Cfg::N, V = C / 2;
+    constexpr uint32_t BYTES = N * sizeof(uint64_t);
+    const int tid = threadIdx.x;
+    const uint32_t G = gridDim.x;
+
+    // unit u -> its segment, limb and polynomial (segment units: limb-major)
+    auto locate = [&](uint32_t u, uint32_t &si, uint32_t &limb, uint32_t &poly) {
+        si = 0;
+        while (si + 1 < segs.n && u >= segs.s[si + 1].cta_begin) ++si;
+        const uint32_t local = u - segs.s[si].cta_begin;
+        limb = local / segs.s[si].n_groups;
+        poly = local % segs.s[si].n_groups;
+    };
+    auto issue = [&](uint32_t u, int b) {
+        uint32_t si, limb, poly;
+        locate(u, si, limb, poly);
+        const NttSeg &sg = segs.s[si];
+        mbar_arrive_expect_tx(&bars[b], BYTES);
+        bulk_g2s(sm + (size_t)b * N, sg.in + ((size_t)poly * sg.L + limb) * N, BYTES, &bars[b]);
+    };
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0 && blockIdx.x < total) issue(blockIdx.x, 0);
+
+    bool ok = true;
+    uint32_t k = 0, u = blockIdx.x;
+    for (; u < total; u += G, ++k) {
+        const int b = k & 1;
+        __syncthreads();  // every thread is done with the other buffer (unit k - 1)
+        if (tid == 0 && u + G < total) {
+            fence_proxy_async();
+            issue(u + G, b ^ 1);
+        }
+        ok = mbar_wait(&bars[b], (k >> 1) & 1);
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+
+        uint32_t si, limb, poly;
+        locate(u, si, limb, poly);
+        const NttSeg &sg = segs.s[si];
+        const LimbConst &lc = sg.limbs[limb];
+        uint64_t *buf = sm + (size_t)b * N;
+        const uint32_t rho = V >= 8 ? (uint32_t)tid : (uint32_t)tid >> 1;
+        const ulonglong2 *vec = reinterpret_cast<const ulonglong2 *>(buf) + (size_t)tid * V;
+        ulonglong2 t[V];
+#pragma unroll
+        for (int r = 0; r < V; ++r) t[r] = vec[(r + rho) & (V - 1)];
+        unrotate<V>(t, rho);
+        uint64_t x[1][C];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            x[0][2 * j] = t[j].x;
+            x[0][2 * j + 1] = t[j].y;
+        }
+        inv_transform<Cfg>(x, buf, lc, lc.tw_i, tid);
+        uint64_t *dst = sg.out + ((size_t)poly * sg.L + limb) * N;
+#pragma unroll
+        for (int r = 0; r < C; ++r) dst[inv_out_elem<Cfg>(tid, r)] = x[0][r];
+    }
+    if (!ok && tid == 0) {
+        atomicExch(err, 2);
+        // drain: the copy this unit waited for, and the next one if it was issued
+        mbar_wait(&bars[k & 1], (k >> 1) & 1);
+        if (u + G < total) mbar_wait(&bars[(k + 1) & 1], ((k + 1) >> 1) & 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One task of a standalone product: NP components (comp0, comp0 + 1, ...) of
 // one limb.  ct is the product's ciphertext [2][L][N], pt its NTT-domain
 // plaintext [L][N], out its output ciphertext [2][L][N]:
@@ -367,6 +482,36 @@ hc_status run_ntt_segs(const NttSegsT<NS> &segs, cudaStream_t s, bool inverse)
     return after_launch("k_ntt_fwd");
 }
 
+// persistent TMA-fed inverse NTT: segs' cta_begin are unit offsets (n_groups
+// polynomials x L limbs per segment); one launch of resident CTAs
+template <class Cfg, int NS>
+hc_status run_ntt_inv_tma(const NttSegsT<NS> &segs, int *err, cudaStream_t s)
+{
+    uint32_t total = 0;
+    for (uint32_t i = 0; i < segs.n; ++i) total = segs.s[i].cta_begin + segs.s[i].n_groups * segs.s[i].L;
+    if (total == 0) return HC_OK;
+    constexpr size_t smem = 2 * Cfg::SMEM_BYTES;
+    auto kern = k_ntt_inv_tma<Cfg, NS>;
+    static std::atomic<int> resident[32];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int r = resident[dev & 31].load();
+    if (r == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0, sms = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::T, smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_error(e, "k_ntt_inv_tma set-up");
+        if (per_sm < 1) return set_error(HC_ERR_UNSUPPORTED, "k_ntt_inv_tma does not fit on an SM");
+        r = per_sm * sms;
+        resident[dev & 31].store(r);
+    }
+    const uint32_t grid = total < (uint32_t)r ? total : (uint32_t)r;
+    ProfileScope ps(kname<Cfg>(KK_INV), s);
+    kern<<<grid, Cfg::T, smem, s>>>(segs, total, err);
+    return after_launch("k_ntt_inv_tma");
+}
+
 // one-segment launch: n_groups CTAs per limb
 inline NttSegs1 one_seg(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_groups)
 {
@@ -433,6 +578,25 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
 {
     using Fused = VCfg<LOGN, V, false>;
     using Single = VCfg<LOGN, V, true>;
+    if constexpr (use_inv_tma<LOGN, V>) {
+        using TC = typename InvTma<LOGN>::Cfg;
+        if (kind == KK_INV || kind == KK_INVCT) {
+            const size_t polys = kind == KK_INV ? a.n : 2 * a.n;
+            if (polys == 0) return HC_OK;
+            if (polys * ctx->L > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
+            return detail::run_ntt_inv_tma<TC>(detail::one_seg(ctx, a.in, a.out, polys), ctx->d_flag + 1, s);
+        }
+        if (kind == KK_INVCT_SEGS) {
+            NttSegs segs = *a.segs;
+            uint32_t begin = 0;
+            for (uint32_t i = 0; i < segs.n; ++i) {
+                segs.s[i].n_groups *= 2;  // polynomials
+                segs.s[i].cta_begin = begin;
+                begin += segs.s[i].n_groups * segs.s[i].L;
+            }
+            return detail::run_ntt_inv_tma<TC>(segs, ctx->d_flag + 1, s);
+        }
+    }
     switch (kind) {
     case KK_FWD: return detail::run_ntt_fwd<Single>(ctx, a.in, a.out, a.n, s);
     case KK_INV: return detail::run_ntt_inv<Single>(ctx, a.in, a.out, a.n, s);

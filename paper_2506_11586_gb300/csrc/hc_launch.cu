@@ -139,12 +139,10 @@ k_mac_conv(const __grid_constant__ MacSegsT<NS> segs, int *err)
         const uint64_t *wst = ws + (size_t)st * SR * KC + k;
         uint64_t *yk = Y + (size_t)limb * N + k0 + k + (size_t)c0 * P * LN;
         // one output row: sum over the G channel groups (two chains for latency hiding)
-        auto row = [&](uint32_t ml, uint32_t p) {
+        auto row = [&](const uint64_t *xp, const uint64_t *wk, uint64_t *yp) {
             MacAcc acc0, acc1;
             mac_zero(acc0);
             mac_zero(acc1);
-            const uint64_t *xp = xs + (size_t)p * KC + k;
-            const uint64_t *wk = wst + (size_t)ml * G * KC;
             uint32_t g = 0;
             for (; g + 1 < G; g += 2) {
                 mac_add(acc0, xp[0], wk[g * KC]);
@@ -153,16 +151,19 @@ k_mac_conv(const __grid_constant__ MacSegsT<NS> segs, int *err)
             }
             if (g < G) mac_add(acc0, xp[0], wk[g * KC]);
             mac_merge(acc0, acc1);
-            yk[(size_t)(ml * P + p) * LN] = mac_reduce(acc0, q, nq, r64, r64_s, ones);
+            *yp = mac_reduce(acc0, q, nq, r64, r64_s, ones);
         };
+        const uint64_t *xk = xs + k;
         if (P >= (uint32_t)H) {  // every row group has work in every channel
-            for (uint32_t ml = 0; ml < cnt; ++ml)
-                for (uint32_t p = h; p < P; p += H) row(ml, p);
+            const uint64_t *wk = wst;
+            uint64_t *ym = yk;
+            for (uint32_t ml = 0; ml < cnt; ++ml, wk += G * KC, ym += P * LN)
+                for (uint32_t p = h; p < P; p += H) row(xk + p * KC, wk, ym + p * LN);
         } else {                 // few rows per channel: spread (channel, row) pairs over the groups
             const uint32_t jobs = cnt * P;
             uint32_t ml = h / P, p = h % P;
             for (uint32_t j = h; j < jobs; j += H) {
-                row(ml, p);
+                row(xk + p * KC, wst + (size_t)ml * G * KC, yk + (size_t)j * LN);
                 p += H;
                 while (p >= P) {
                     p -= P;
