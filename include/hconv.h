@@ -95,10 +95,15 @@ hc_status hc_selftest_wait_timeout(const hc_ctx *ctx, uint32_t limit, void *cuda
 /* Launch-shape tuning (no counterpart in the paper: a GPU scheduling knob).
  * Kernel families (kind): 0 forward NTT, 1 inverse NTT, 2 fused NTT-domain
  * MAC + inverse NTT, 3 fused standalone product, 4 forward NTT of whole
- * ciphertexts, 5 inverse NTT of whole ciphertexts, 6 blocked convolution MAC.
- * variant (0..2) selects, for kinds 0-5, the radix per register round, the
- * polynomials per CTA and the CTAs per SM for the context's N; for kind 6 the
- * weight rows per pipeline stage (about 8, 16 or 32).  Every variant
+ * ciphertexts, 5 inverse NTT of whole ciphertexts, 6 blocked convolution MAC,
+ * 7 convolution launch form.  variant (0..2) selects, for kinds 0-5, the radix
+ * per register round, the polynomials per CTA and the CTAs per SM for the
+ * context's N (variant 2 of the inverse kinds at N <= 8192 is a persistent,
+ * TMA-fed kernel); for kind 6 the weight rows per pipeline stage (about 8, 16
+ * or 32); for kind 7 either three launches per ring degree (forward NTTs,
+ * MACs, inverse NTTs: variant 0) or one persistent launch whose CTAs take the
+ * layers' NTT, MAC and INTT tasks in order and wait on per-limb completion
+ * counters (variants 1 and 2).  Every variant
  * computes the same bits, only speed differs.  hc_ctx_create picks defaults.
  * Changing a variant while other threads use the context is a data race.
  * Errors: HC_ERR_INVALID_ARG (bad handle, kind or variant). */

@@ -218,7 +218,8 @@ def hc_ctx_create(N, moduli, t, flags=0):
     return Ctx(out, N, [int(x) for x in m], t)
 
 
-KIND_NTT_FWD, KIND_NTT_INV, KIND_MAC_INTT, KIND_PRODUCT, KIND_NTT_FWD_CT, KIND_NTT_INV_CT, KIND_MAC_CONV = range(7)
+(KIND_NTT_FWD, KIND_NTT_INV, KIND_MAC_INTT, KIND_PRODUCT, KIND_NTT_FWD_CT, KIND_NTT_INV_CT, KIND_MAC_CONV,
+ KIND_CONV_FORM) = range(8)
 N_VARIANTS = 3
 
 

@@ -136,15 +136,24 @@ struct ScratchGuard {
 }  // namespace
 
 namespace hc {
-hc_status conv_layer(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out,
-                     uint64_t *scratch, cudaStream_t s)
+size_t conv_scratch_words(const hc_ctx *ctx, const hc_weights *w)
 {
-    hc_status st = launch_ntt_fwd_ct(ctx, d_in, scratch, w->I, s);
-    if (st != HC_OK) return st;
-    st = launch_mac_conv(ctx, scratch, w->d_pt, d_out, w->G, w->B, w->desc.M, s);
-    if (st == HC_OK) return launch_ntt_inv_ct(ctx, d_out, d_out, w->O, s);
-    if (st != HC_ERR_UNSUPPORTED) return st;
-    return launch_mac_intt(ctx, scratch, w->d_pt, MacTerms{w->d_term_ptr, w->d_terms}, d_out, w->O, s);
+    // NTT-domain inputs, then dependency counters of the fused form (two per 64-bit word)
+    return (size_t)w->I * 2 * ctx->L * ctx->N + (conv_counter_bound(ctx, w) + 1) / 2;
+}
+
+size_t conv_counter_bound(const hc_ctx *ctx, const hc_weights *w)
+{
+    return 1 + (size_t)ctx->L * (1 + w->desc.M);
+}
+
+hc_status conv_layer(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out,
+                     uint64_t *scratch, size_t scratch_words, cudaStream_t s)
+{
+    const size_t ntt_words = (size_t)w->I * 2 * ctx->L * ctx->N;
+    const ConvJob job{ctx, w, d_in, d_out, scratch, conv_job_blocked(ctx, w)};
+    uint32_t *ctr = scratch_words > ntt_words ? reinterpret_cast<uint32_t *>(scratch + ntt_words) : nullptr;
+    return launch_conv_jobs(&job, 1, s, ctr, ctr ? 2 * (scratch_words - ntt_words) : 0);
 }
 
 // checked mode: HC_ERR_RANGE if any residue of [n][L][N] is >= its q_i (synchronises s)
@@ -503,10 +512,10 @@ hc_status hc_conv_ct_pt(const hc_ctx *ctx, const hc_weights *w, const uint64_t *
     hc_status st = check_inputs(ctx, d_ct_in, (size_t)2 * w->I, s);
     if (st != HC_OK) return st;
     ScratchGuard scratch(s);
-    scratch.p = dev_alloc((size_t)w->I * 2 * ctx->L * ctx->N * sizeof(uint64_t), s);
+    const size_t words = conv_scratch_words(ctx, w);
+    scratch.p = dev_alloc(words * sizeof(uint64_t), s);
     if (!scratch.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
-    uint64_t *ct_ntt = (uint64_t *)scratch.p;
-    return conv_layer(ctx, w, d_ct_in, d_ct_out, ct_ntt, s);
+    return conv_layer(ctx, w, d_ct_in, d_ct_out, (uint64_t *)scratch.p, words, s);
 }
 
 hc_status hc_conv_ct_pt_plain(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in, uint64_t *d_ct_out,

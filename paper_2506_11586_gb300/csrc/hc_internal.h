@@ -34,7 +34,11 @@ struct LimbConst {
 static_assert(sizeof(LimbConst) == 128, "LimbConst is 128 bytes");
 
 // Kernel families whose launch shape is selectable per context.
-enum KernelKind { KK_FWD = 0, KK_INV = 1, KK_MAC = 2, KK_PROD = 3, KK_FWDCT = 4, KK_INVCT = 5, KK_MACB = 6, KK_COUNT = 7 };
+enum KernelKind {
+    KK_FWD = 0, KK_INV = 1, KK_MAC = 2, KK_PROD = 3, KK_FWDCT = 4, KK_INVCT = 5, KK_MACB = 6,
+    KK_CONV = 7,  // convolution launch form: 0 three launches per degree, 1 and 2 one fused persistent launch
+    KK_COUNT = 8
+};
 constexpr int kNumVariants = 3;
 
 }  // namespace hc
@@ -159,6 +163,10 @@ struct MacLayer {
     uint32_t G, B, M;
 };
 bool mac_conv_fits(uint32_t G, uint32_t B);
+// MAC task geometry of one layer (channels per stage from the context's variant)
+MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
+                    uint32_t M);
+size_t mac_seg_smem(const MacSeg &sg);
 // blocked MACs of n layers (layer i on ctxs[i]) in ceil(n / kMaxSegs) launches
 hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s);
 
@@ -176,9 +184,35 @@ struct ConvJob {
     bool blocked;         // blocked MAC fits (else fused MAC + inverse NTT)
 };
 bool conv_job_blocked(const hc_ctx *c, const hc_weights *w);
-// forward NTTs of all jobs (one launch per degree), their MACs (one launch),
-// their inverse NTTs (one launch per degree); at most kMaxSegs jobs per launch
-hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s);
+// The batched launch sequence of n conv jobs in stream order on s.  Per ring
+// degree, when the first job's context selects the fused form (KK_CONV) and
+// ctr holds enough words (conv_jobs_counter_words): one persistent fused
+// launch; otherwise forward NTTs (one launch per degree), MACs (one launch),
+// inverse NTTs (one launch per degree), at most kMaxSegs jobs per launch.
+hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s, uint32_t *ctr = nullptr,
+                           size_t ctr_words = 0);
+// counter words the fused form of these jobs needs (the largest degree's)
+size_t conv_jobs_counter_words(const ConvJob *jobs, size_t n);
+
+// one conv layer of a fused persistent launch (see k_conv_fused)
+struct FusedLayer {
+    MacSeg mac;               // X = NTT-domain scratch, W, Y, limbs and the MAC task geometry
+    const uint64_t *in;       // coefficient-domain inputs [I][2][L][N]
+    uint32_t I, O;
+    uint32_t t_fwd, t_mac, t_inv;  // first task of each phase (numbered over the whole launch)
+    uint32_t c_fwd, c_mac;         // counter offsets: c_fwd + limb; c_mac + group * L + limb
+};
+template <int NS>
+struct FusedLayersT {
+    uint32_t n, total;             // layers, tasks
+    FusedLayer s[NS];
+};
+constexpr int kFusedMaxLayers = 32;
+// counter words a fused launch over these jobs needs (one degree), 0 if none
+size_t fused_counter_words(const ConvJob *jobs, size_t n, uint32_t logN);
+// one fused launch over the blocked jobs of degree 2^logN (at most kFusedMaxLayers);
+// ctr: zero-initialised by this call on s
+hc_status launch_conv_fused(const ConvJob *jobs, size_t n, uint32_t logN, uint32_t *ctr, cudaStream_t s);
 
 // one standalone product of a mixed-degree batch (see k_product_mixed)
 struct MixItem {
@@ -252,7 +286,11 @@ hc_status launch_range_check(const hc_ctx *ctx, const uint64_t *p, size_t n_poly
 // place; falls back to the fused MAC + inverse NTT kernel for layers whose
 // input chunk does not fit the blocked MAC's shared memory
 hc_status conv_layer(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out,
-                     uint64_t *scratch, cudaStream_t s);
+                     uint64_t *scratch, size_t scratch_words, cudaStream_t s);
+// scratch words conv_layer uses at most (NTT-domain inputs + fused-form counters)
+size_t conv_scratch_words(const hc_ctx *ctx, const hc_weights *w);
+// an upper bound of the fused form's counter words for one layer (any MAC variant)
+size_t conv_counter_bound(const hc_ctx *ctx, const hc_weights *w);
 
 // checked mode only: HC_ERR_RANGE if a residue is >= its q_i (synchronises s); HC_OK otherwise
 hc_status check_inputs(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cudaStream_t s);

@@ -80,32 +80,23 @@ __device__ __forceinline__ void load_round0(uint64_t (&x)[Cfg::NP][Cfg::C], cons
 }
 
 // ---------------------------------------------------------------------------
-template <class Cfg, int NS>
-__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
-k_ntt_fwd(const __grid_constant__ NttSegsT<NS> segs)
+// Forward NTT of NP polynomials (src + p*pstride, p < NP) into dst (same
+// strides), canonical output, stored through shared memory as coalesced
+// 16-byte pairs.  One CTA task.
+template <class Cfg>
+__device__ __forceinline__ void fwd_task(uint64_t *sm, const uint64_t *src, uint64_t *dst, size_t pstride,
+                                         const LimbConst &lc, int tid)
 {
-    extern __shared__ uint64_t sm[];
     constexpr int NP = Cfg::NP, C = Cfg::C, T = Cfg::T, N = Cfg::N;
-    const int tid = threadIdx.x;
-    const NttSeg &sg = find_seg(segs);
-    const uint64_t *in = sg.in;
-    uint64_t *out = sg.out;
-    const uint32_t L = sg.L, n_groups = sg.n_groups;
-    const uint32_t local = blockIdx.x - sg.cta_begin;
-    const uint32_t limb = local / n_groups, grp = local % n_groups;
-    const LimbConst &lc = sg.limbs[limb];
     const uint64_t q = lc.q;
-
     uint64_t x[NP][C];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const uint64_t *src = in + ((size_t)(grp * NP + p) * L + limb) * N;
 #pragma unroll
-        for (int r = 0; r < C; ++r) x[p][r] = __ldg(src + tid + r * T);
+        for (int r = 0; r < C; ++r) x[p][r] = __ldg(src + p * pstride + tid + r * T);
     }
     fwd_transform<Cfg>(x, sm, lc.tw_f, q, tid);
 
-    // canonical residues, stored through shared memory as coalesced 16-byte pairs
     const uint32_t ones = (uint32_t)lc.one_s;
     const uint64_t nq = 0ull - q;
     __syncthreads();
@@ -117,42 +108,35 @@ k_ntt_fwd(const __grid_constant__ NttSegsT<NS> segs)
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(out + ((size_t)(grp * NP + p) * L + limb) * N);
+        ulonglong2 *d = reinterpret_cast<ulonglong2 *>(dst + p * pstride);
 #pragma unroll
         for (int r = 0; r < C / 2; ++r) {
             const int e = 2 * (tid + r * T);
             ulonglong2 v;
             v.x = sm[p * N + spos<Cfg>(e)];
             v.y = sm[p * N + spos<Cfg>(e + 1)];
-            dst[tid + r * T] = v;
+            d[tid + r * T] = v;
         }
     }
 }
 
-template <class Cfg, int NS>
-__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
-k_ntt_inv(const __grid_constant__ NttSegsT<NS> segs)
+// Inverse NTT of NP polynomials (src + p*pstride) into dst (may equal src).
+// COHERENT loads bypass the non-coherent read-only path, for inputs written
+// earlier by other CTAs of the same launch.  One CTA task.
+template <class Cfg, bool COHERENT = false>
+__device__ __forceinline__ void inv_task(uint64_t *sm, const uint64_t *src, uint64_t *dst, size_t pstride,
+                                         const LimbConst &lc, int tid)
 {
-    extern __shared__ uint64_t sm[];
     constexpr int NP = Cfg::NP, C = Cfg::C, N = Cfg::N;
-    const int tid = threadIdx.x;
-    const NttSeg &sg = find_seg(segs);
-    const uint64_t *in = sg.in;
-    uint64_t *out = sg.out;
-    const uint32_t L = sg.L, n_groups = sg.n_groups;
-    const uint32_t local = blockIdx.x - sg.cta_begin;
-    const uint32_t limb = local / n_groups, grp = local % n_groups;
-    const LimbConst &lc = sg.limbs[limb];
-
     // coalesced 16-byte loads into shared memory, then the round-0 layout
     // (element tid*C + r) out of it
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(in + ((size_t)(grp * NP + p) * L + limb) * N);
+        const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src + p * pstride);
 #pragma unroll
         for (int r = 0; r < C / 2; ++r) {
             const int e = 2 * (tid + r * Cfg::T);
-            const ulonglong2 v = __ldg(src + tid + r * Cfg::T);
+            const ulonglong2 v = COHERENT ? __ldcg(s2 + tid + r * Cfg::T) : __ldg(s2 + tid + r * Cfg::T);
             sm[p * N + spos<Cfg>(e)] = v.x;
             sm[p * N + spos<Cfg>(e + 1)] = v.y;
         }
@@ -162,10 +146,34 @@ k_ntt_inv(const __grid_constant__ NttSegsT<NS> segs)
     inv_transform<Cfg>(x, sm, lc, lc.tw_i, tid);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        uint64_t *dst = out + ((size_t)(grp * NP + p) * L + limb) * N;
+        uint64_t *d = dst + p * pstride;
 #pragma unroll
-        for (int r = 0; r < C; ++r) dst[inv_out_elem<Cfg>(tid, r)] = x[p][r];
+        for (int r = 0; r < C; ++r) d[inv_out_elem<Cfg>(tid, r)] = x[p][r];
     }
+}
+
+template <class Cfg, int NS>
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
+k_ntt_fwd(const __grid_constant__ NttSegsT<NS> segs)
+{
+    extern __shared__ uint64_t sm[];
+    const NttSeg &sg = find_seg(segs);
+    const uint32_t local = blockIdx.x - sg.cta_begin;
+    const uint32_t limb = local / sg.n_groups, grp = local % sg.n_groups;
+    const size_t off = ((size_t)grp * Cfg::NP * sg.L + limb) * Cfg::N;
+    fwd_task<Cfg>(sm, sg.in + off, sg.out + off, (size_t)sg.L * Cfg::N, sg.limbs[limb], threadIdx.x);
+}
+
+template <class Cfg, int NS>
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
+k_ntt_inv(const __grid_constant__ NttSegsT<NS> segs)
+{
+    extern __shared__ uint64_t sm[];
+    const NttSeg &sg = find_seg(segs);
+    const uint32_t local = blockIdx.x - sg.cta_begin;
+    const uint32_t limb = local / sg.n_groups, grp = local % sg.n_groups;
+    const size_t off = ((size_t)grp * Cfg::NP * sg.L + limb) * Cfg::N;
+    inv_task<Cfg>(sm, sg.in + off, sg.out + off, (size_t)sg.L * Cfg::N, sg.limbs[limb], threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------

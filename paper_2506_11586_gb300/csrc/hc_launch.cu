@@ -7,6 +7,7 @@
 #include "hc_arith.cuh"
 #include "hc_async.cuh"
 #include "hc_internal.h"
+#include "hc_mac.cuh"
 
 namespace hc {
 
@@ -55,133 +56,32 @@ int default_variant(int kind, uint32_t logn)
 }
 
 // ---------------------------------------------------------------------------
-// Convolution MAC in the NTT domain, blocked over coefficient chunks (Sec. 6.2):
-//   Y[m*B+b][c] = sum_g W[m*G+g] . X[g*B+b][c]      (slot-wise, mod q_limb)
-// A CTA owns one chunk of KC slots of one limb for every input ciphertext and
-// a group of MB output channels.  The input chunk (G*2B rows of KC slots) is
-// fetched once into shared memory by TMA bulk copies; the weight slices
-// stream through a ring of kMacStages shared-memory stages of MS channels
-// each (MS*G rows of KC slots), refilled while the other stages are in use.
-// Each weight slot is therefore read from memory once and each input slot
-// once per channel group.  Per stage the CTA computes MS*2B output rows of KC
-// slots: thread (k, h) owns slot k0 + k and the rows j = h (mod H), row
-// j = m*2B + p for channel m of the stage and component pair p = 2b + c.
-// Waits are bounded: a wait that runs out sets err = 2, drains this CTA's
-// copies in flight (bounded) and ends the CTA.
+// Blocked convolution MAC (the task in hc_mac.cuh): one task per CTA; the
+// CTAs of a launch cover the (chunk, limb, channel group) tasks of every
+// segment (layer) of the table.
 constexpr int kMacThreads = 256;
-constexpr int kMacStages = 3;
 
 template <int KC, int NS>
 __global__ void __launch_bounds__(kMacThreads)
 k_mac_conv(const __grid_constant__ MacSegsT<NS> segs, int *err)
 {
-    constexpr int H = kMacThreads / KC;
-    constexpr uint32_t ROW_BYTES = KC * sizeof(uint64_t);
     __shared__ __align__(8) uint64_t bars[1 + kMacStages];
     extern __shared__ __align__(16) uint64_t dsm[];
     uint32_t si = 0;
     while (si + 1 < segs.n && blockIdx.x >= segs.s[si + 1].cta_begin) ++si;
     const MacSeg &sg = segs.s[si];
-    const uint64_t *__restrict__ X = sg.X;
-    const uint64_t *__restrict__ W = sg.W;
-    uint64_t *__restrict__ Y = sg.Y;
-    const uint32_t N = sg.N, L = sg.L, G = sg.G, B = sg.B, M = sg.M, MB = sg.MB, MS = sg.MS;
     const uint32_t local = blockIdx.x - sg.cta_begin;
     const uint32_t chunk = local % sg.chunks, rest = local / sg.chunks;
-    const uint32_t P = 2 * B, rows = G * P, SR = MS * G;
-    uint64_t *xs = dsm;                          // [rows][KC]
-    uint64_t *ws = dsm + (size_t)rows * KC;      // [kMacStages][SR][KC]
-    const uint32_t k0 = chunk * KC, limb = rest % L;
-    const uint32_t m0 = (rest / L) * MB, m1 = min(M, m0 + MB);
-    const uint32_t nm = m1 > m0 ? m1 - m0 : 0;
-    const uint32_t nst = (nm + MS - 1) / MS;     // stages of this CTA
-    const size_t LN = (size_t)L * N;
-    const uint64_t *xsrc = X + (size_t)limb * N + k0;   // input row r at xsrc + r*LN
-    const uint64_t *wsrc = W + (size_t)limb * N + k0;   // weight poly j at wsrc + j*LN
-    const int tid = threadIdx.x;
-
-    auto issue_w = [&](uint32_t i) {  // channels m0 + i*MS ... into stage i % kMacStages
-        const uint32_t st = i % kMacStages, c0 = m0 + i * MS;
-        const uint32_t nr = min(MS, m1 - c0) * G;
-        mbar_arrive_expect_tx(&bars[1 + st], nr * ROW_BYTES);
-        const uint64_t *src = wsrc + (size_t)c0 * G * LN;
-        uint64_t *dst = ws + (size_t)st * SR * KC;
-        for (uint32_t r = 0; r < nr; ++r) bulk_g2s(dst + (size_t)r * KC, src + r * LN, ROW_BYTES, &bars[1 + st]);
-    };
-    if (tid == 0) {
+    const uint32_t limb = rest % sg.L;
+    const uint32_t m0 = (rest / sg.L) * sg.MB, m1 = min(sg.M, m0 + sg.MB);
+    if (threadIdx.x == 0) {
         for (int i = 0; i < 1 + kMacStages; ++i) mbar_init(&bars[i], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bars[0], rows * ROW_BYTES);
-        for (uint32_t r = 0; r < rows; ++r) bulk_g2s(xs + (size_t)r * KC, xsrc + r * LN, ROW_BYTES, &bars[0]);
-        for (uint32_t i = 0; i < (uint32_t)kMacStages && i < nst; ++i) issue_w(i);
-    }
-
-    const LimbConst &lc = sg.limbs[limb];
-    const uint64_t q = lc.q, nq = 0ull - q, r64 = lc.r64, r64_s = lc.r64_s;
-    const uint32_t ones = (uint32_t)lc.one_s;
-    const uint32_t k = tid % KC, h = tid / KC;  // h is warp-uniform
-    const uint32_t xstep = P * KC;
-    bool ok = mbar_wait(&bars[0], 0);
-    uint32_t i = 0;
-    for (; i < nst; ++i) {
-        const uint32_t st = i % kMacStages;
-        ok = mbar_wait(&bars[1 + st], (i / kMacStages) & 1) && ok;
-        ok = __syncthreads_and(ok);  // also: every thread has finished stage i - 1
-        if (!ok) break;
-        if (tid == 0 && i >= 1 && i - 1 + kMacStages < nst) {
-            fence_proxy_async();
-            issue_w(i - 1 + kMacStages);  // into the stage that stage i - 1 used
-        }
-        const uint32_t c0 = m0 + i * MS, cnt = min(MS, m1 - c0);
-        const uint64_t *wst = ws + (size_t)st * SR * KC + k;
-        uint64_t *yk = Y + (size_t)limb * N + k0 + k + (size_t)c0 * P * LN;
-        // one output row: sum over the G channel groups (two chains for latency hiding)
-        auto row = [&](const uint64_t *xp, const uint64_t *wk, uint64_t *yp) {
-            MacAcc acc0, acc1;
-            mac_zero(acc0);
-            mac_zero(acc1);
-            uint32_t g = 0;
-            for (; g + 1 < G; g += 2) {
-                mac_add(acc0, xp[0], wk[g * KC]);
-                mac_add(acc1, xp[xstep], wk[(g + 1) * KC]);
-                xp += 2 * xstep;
-            }
-            if (g < G) mac_add(acc0, xp[0], wk[g * KC]);
-            mac_merge(acc0, acc1);
-            *yp = mac_reduce(acc0, q, nq, r64, r64_s, ones);
-        };
-        const uint64_t *xk = xs + k;
-        if (P >= (uint32_t)H) {  // every row group has work in every channel
-            const uint64_t *wk = wst;
-            uint64_t *ym = yk;
-            for (uint32_t ml = 0; ml < cnt; ++ml, wk += G * KC, ym += P * LN)
-                for (uint32_t p = h; p < P; p += H) row(xk + p * KC, wk, ym + p * LN);
-        } else {                 // few rows per channel: spread (channel, row) pairs over the groups
-            const uint32_t jobs = cnt * P;
-            uint32_t ml = h / P, p = h % P;
-            for (uint32_t j = h; j < jobs; j += H) {
-                row(xk + p * KC, wst + (size_t)ml * G * KC, yk + (size_t)j * LN);
-                p += H;
-                while (p >= P) {
-                    p -= P;
-                    ++ml;
-                }
-            }
-        }
-    }
-    if (!ok && tid == 0) {
-        atomicExch(err, 2);
-        // drain this CTA's bulk copies still in flight before its shared memory is released
-        mbar_wait(&bars[0], 0);
-        const uint32_t last = i == 0 ? min(nst, (uint32_t)kMacStages) : min(nst, i - 1 + kMacStages);
-        for (uint32_t j = i; j < last; ++j) mbar_wait(&bars[1 + j % kMacStages], (j / kMacStages) & 1);
-    }
+    MacRing ring{0, 0};
+    mac_task<KC, kMacThreads>(sg, chunk, limb, m0, m1, dsm, bars, ring, err);
 }
-
-constexpr int kMacKC = 64;
 
 // stage rows targeted by each launch variant of the blocked MAC
 constexpr uint32_t kMacStageRows[kNumVariants] = {8, 16, 32};
@@ -203,7 +103,7 @@ static uint32_t mac_stage_channels(uint32_t G, uint32_t B, uint32_t M, int varia
 }
 
 // fill the launch geometry of one segment: enough CTAs for about four waves
-static MacSeg mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
+MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
                       uint32_t M)
 {
     MacSeg sg{};
@@ -252,6 +152,11 @@ static hc_status run_mac_segs(MacSegsT<NS> &segs, size_t smem, int *err, cudaStr
     return after_launch_status("k_mac_conv");
 }
 
+size_t mac_seg_smem(const MacSeg &sg)
+{
+    return mac_smem(sg.G, sg.B, sg.MS);
+}
+
 bool mac_conv_fits(uint32_t G, uint32_t B)
 {
     return mac_smem(G, B, 1) <= kMacSmemCap;
@@ -263,7 +168,7 @@ hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64
     if (!mac_conv_fits(G, B) || ctx->N % kMacKC) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
     MacSegs1 segs{};
     segs.n = 1;
-    segs.s[0] = mac_seg(ctx, x_ntt, w_ntt, y, G, B, M);
+    segs.s[0] = make_mac_seg(ctx, x_ntt, w_ntt, y, G, B, M);
     return run_mac_segs(segs, mac_smem(G, B, segs.s[0].MS), ctx->d_flag + 1, s);
 }
 
@@ -276,7 +181,7 @@ hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *laye
         for (size_t i = i0; i < i1; ++i) {
             const MacLayer &ly = layers[i];
             if (!mac_conv_fits(ly.G, ly.B)) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
-            segs.s[segs.n] = mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M);
+            segs.s[segs.n] = make_mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M);
             const size_t sm = mac_smem(ly.G, ly.B, segs.s[segs.n++].MS);
             if (sm > smem) smem = sm;
         }

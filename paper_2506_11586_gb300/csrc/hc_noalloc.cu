@@ -65,5 +65,7 @@ extern "C" hc_status hc_conv_ct_pt_noalloc(const hc_ctx *ctx, const hc_weights *
     if (st != HC_OK) return st;
     // the forward NTT overwrites every scratch word the later phases read, so
     // nothing left over from an earlier call is ever used
-    return conv_layer(ctx, w, d_ct_in, d_ct_out, scratch, s);
+    const size_t use = conv_scratch_words(ctx, w) < kStaticScratchWords ? conv_scratch_words(ctx, w)
+                                                                        : kStaticScratchWords;
+    return conv_layer(ctx, w, d_ct_in, d_ct_out, scratch, use, s);
 }

@@ -36,6 +36,8 @@ struct hc_plan {
     std::vector<PlanProd> prods;
     std::vector<const hc_ctx *> ctxs;   // distinct contexts, first-use order
     void *d_scratch = nullptr;          // conv NTT'd inputs
+    uint32_t *d_ctr = nullptr;          // dependency counters of the fused form
+    size_t ctr_words = 0;
     void *d_mix = nullptr;              // MixItem[] | units[] | counter
     MixItem *d_items = nullptr;
     uint32_t *d_units = nullptr;
@@ -108,7 +110,7 @@ hc_status check_overlaps(const std::vector<hc_work_item> &items)
 // ---- the batched launch sequence ---------------------------------------------
 hc_status run_batched(hc_plan *p, cudaStream_t s)
 {
-    hc_status st = launch_conv_jobs(p->convs.data(), p->convs.size(), s);
+    hc_status st = launch_conv_jobs(p->convs.data(), p->convs.size(), s, p->d_ctr, p->ctr_words);
     if (st != HC_OK) return st;
     // every standalone product, one persistent launch
     if (p->n_units) {
@@ -119,11 +121,25 @@ hc_status run_batched(hc_plan *p, cudaStream_t s)
     return HC_OK;
 }
 
+// kernels one batched run launches (the fused form counts one per degree)
 uint32_t count_launches(const hc_plan *p)
 {
     uint32_t n = 0, fit = 0;
     uint32_t per_n[3] = {0, 0, 0}, per_n_fit[3] = {0, 0, 0};
+    bool fused[3] = {false, false, false};
+    for (int d = 0; d < 3; ++d) {
+        uint32_t cnt = 0;
+        const PlanConv *first = nullptr;
+        for (const PlanConv &c : p->convs)
+            if (c.ctx->logN == (uint32_t)(12 + d) && c.blocked) {
+                if (!first) first = &c;
+                ++cnt;
+            }
+        fused[d] = first && first->ctx->variant[KK_CONV] != 0 && cnt <= (uint32_t)kFusedMaxLayers && p->d_ctr;
+        if (fused[d]) ++n;
+    }
     for (const PlanConv &c : p->convs) {
+        if (c.blocked && fused[c.ctx->logN - 12]) continue;
         ++per_n[c.ctx->logN - 12];
         if (c.blocked) {
             ++per_n_fit[c.ctx->logN - 12];
@@ -235,17 +251,57 @@ hc_status time_batched(hc_plan *p, cudaStream_t s, int reps, float *ms)
 namespace hc {
 bool conv_job_blocked(const hc_ctx *c, const hc_weights *w) { return mac_conv_fits(w->G, w->B) && c->N % 64 == 0; }
 
-// the batched launch sequence of n conv jobs (all degrees), in stream order on s
-hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s)
+size_t conv_jobs_counter_words(const ConvJob *jobs, size_t n)
 {
-    // forward NTT of every conv input, one launch per ring degree (per kMaxSegs jobs)
+    size_t w = 0;
+    for (uint32_t logN = 12; logN <= 14; ++logN) {
+        const size_t x = fused_counter_words(jobs, n, logN);
+        if (x > w) w = x;
+    }
+    return w;
+}
+
+// the batched launch sequence of n conv jobs (all degrees), in stream order on s
+hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s, uint32_t *ctr, size_t ctr_words)
+{
+    // degrees whose blocked jobs run as one fused persistent launch
+    bool fused[3] = {false, false, false};
+    for (uint32_t logN = 12; logN <= 14; ++logN) {
+        const ConvJob *first = nullptr;
+        size_t count = 0;
+        for (size_t i = 0; i < n; ++i)
+            if (jobs[i].ctx->logN == logN && jobs[i].blocked) {
+                if (!first) first = &jobs[i];
+                ++count;
+            }
+        if (!first || first->ctx->variant[KK_CONV] == 0 || count > (size_t)kFusedMaxLayers || !ctr) continue;
+        const size_t words = fused_counter_words(jobs, n, logN);
+        if (words > ctr_words) continue;
+        hc_status st = launch_conv_fused(jobs, n, logN, ctr, s);
+        if (st != HC_OK) return st;
+        fused[logN - 12] = true;
+    }
+    if (n == 1 && !fused[jobs[0].ctx->logN - 12]) {
+        // one layer: the single-segment launchers (small parameter blocks, no host tables)
+        const ConvJob &c = jobs[0];
+        hc_status st = launch_ntt_fwd_ct(c.ctx, c.in, c.ntt, c.w->I, s);
+        if (st != HC_OK) return st;
+        if (!c.blocked)
+            return launch_mac_intt(c.ctx, c.ntt, c.w->d_pt, MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out, c.w->O,
+                                   s);
+        st = launch_mac_conv(c.ctx, c.ntt, c.w->d_pt, c.out, c.w->G, c.w->B, c.w->desc.M, s);
+        if (st != HC_OK) return st;
+        return launch_ntt_inv_ct(c.ctx, c.out, c.out, c.w->O, s);
+    }
+    auto done = [&](const ConvJob &c) { return c.blocked && fused[c.ctx->logN - 12]; };
+    // forward NTT of every other conv input, one launch per ring degree (per kMaxSegs jobs)
     for (uint32_t logN = 12; logN <= 14; ++logN) {
         NttSegs segs{};
         const hc_ctx *first = nullptr;
         for (size_t i = 0; i <= n; ++i) {
             if (i < n) {
                 const ConvJob &c = jobs[i];
-                if (c.ctx->logN != logN) continue;
+                if (c.ctx->logN != logN || done(c)) continue;
                 if (!first) first = c.ctx;
                 segs.s[segs.n++] = NttSeg{c.in, c.ntt, c.ctx->d_limbs, c.ctx->L, c.w->I, 0};
             }
@@ -262,6 +318,7 @@ hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s)
     std::vector<MacLayer> layers;
     for (size_t i = 0; i < n; ++i) {
         const ConvJob &c = jobs[i];
+        if (done(c)) continue;
         if (c.blocked) {
             mctx.push_back(c.ctx);
             layers.push_back(MacLayer{c.ntt, c.w->d_pt, c.out, c.w->G, c.w->B, c.w->desc.M});
@@ -282,7 +339,7 @@ hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s)
         for (size_t i = 0; i <= n; ++i) {
             if (i < n) {
                 const ConvJob &c = jobs[i];
-                if (c.ctx->logN != logN || !c.blocked) continue;
+                if (c.ctx->logN != logN || !c.blocked || done(c)) continue;
                 if (!first) first = c.ctx;
                 segs.s[segs.n++] = NttSeg{c.out, c.out, c.ctx->d_limbs, c.ctx->L, c.w->O, 0};
             }
@@ -304,6 +361,7 @@ void plan_destroy(hc_plan *p)
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     dev_free_persistent(p->d_scratch);
     dev_free_persistent(p->d_mix);
+    dev_free_persistent(p->d_ctr);
     p->magic = kMagicDead;
     delete p;
 }
@@ -377,6 +435,14 @@ hc_status hc_plan_create(const hc_work_item *items, size_t n, hc_plan **out)
         }
     p->n_units = (uint32_t)units.size();
 
+    for (const PlanConv &c : p->convs) p->ctr_words += conv_counter_bound(c.ctx, c.w);
+    if (p->ctr_words) {
+        p->d_ctr = (uint32_t *)dev_alloc_persistent(p->ctr_words * sizeof(uint32_t));
+        if (!p->d_ctr) {
+            hc_free(p);
+            return set_error(HC_ERR_OOM, "plan counter allocation failed");
+        }
+    }
     if (scratch_words) {
         p->d_scratch = dev_alloc_persistent(scratch_words * sizeof(uint64_t));
         if (!p->d_scratch) {
@@ -484,6 +550,7 @@ hc_status hc_plan_autotune(hc_plan *p, const char *cache_path, void *cuda_stream
         if (blocked) knobs.push_back(Knob{mc, KK_MACB});
         if (blocked) knobs.push_back(Knob{mc, KK_INVCT});
         if (fused) knobs.push_back(Knob{mc, KK_MAC});
+        if (blocked) knobs.push_back(Knob{mc, KK_CONV});  // last: the form, with the tuned kernels
     }
 
     std::vector<std::pair<std::string, int>> cache;
@@ -541,7 +608,7 @@ hc_status hc_plan_info(const hc_plan *p, uint64_t *n_products, uint64_t *alg_byt
     if (!plan_ok(p)) return set_error(HC_ERR_INVALID_ARG, "invalid plan");
     if (n_products) *n_products = p->n_products;
     if (alg_bytes) *alg_bytes = p->alg_bytes;
-    if (n_launches) *n_launches = p->n_launches;
+    if (n_launches) *n_launches = count_launches(p);
     return HC_OK;
 }
 

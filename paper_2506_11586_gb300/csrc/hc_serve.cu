@@ -120,6 +120,8 @@ struct hc_server {
     std::vector<Batch *> inflight;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
+    std::vector<uint32_t *> ctrs;        // per stream slot: fused-form counters
+    size_t ctr_words = 1u << 18;
     std::vector<bool> slot_busy;
     uint64_t next_ticket = 1;
     bool stopping = false, sched_exited = false, joined = false;
@@ -174,7 +176,7 @@ hc_status enqueue_batch(hc_server *s, const std::vector<ConvJob> &jobs, const st
     cudaStream_t st = s->streams[slot];
     for (size_t i = 0; i < jobs.size(); ++i)
         HC_CUDA_TRY(cudaMemcpyAsync((void *)jobs[i].in, h_in[i], in_bytes[i], cudaMemcpyHostToDevice, st));
-    hc_status rc = launch_conv_jobs(jobs.data(), jobs.size(), st);
+    hc_status rc = launch_conv_jobs(jobs.data(), jobs.size(), st, s->ctrs[slot], s->ctr_words);
     if (rc != HC_OK) return rc;
     for (size_t i = 0; i < jobs.size(); ++i)
         if (h_out[i])
@@ -319,6 +321,7 @@ void server_destroy(hc_server *s)
     DeviceGuard g(s->device);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+    for (uint32_t *c : s->ctrs) dev_free_persistent(c);
     dev_free_persistent(s->d_pool);
     s->magic = kMagicDead;
     delete s;
@@ -360,6 +363,9 @@ hc_status hc_server_create(const hc_server_config *cfg, hc_server **out)
         if (e == cudaSuccess) s->streams.push_back(st);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) s->events.push_back(ev);
+        uint32_t *ctr = e == cudaSuccess ? (uint32_t *)dev_alloc_persistent(s->ctr_words * sizeof(uint32_t)) : nullptr;
+        if (ctr) s->ctrs.push_back(ctr);
+        if (e == cudaSuccess && !ctr) e = cudaErrorMemoryAllocation;
         if (e != cudaSuccess) {
             hc::server_destroy(s);
             return cuda_error(e, "server stream/event creation");

@@ -187,9 +187,9 @@ def test_plan_autotune_keeps_bits_and_caches(L, ctxs, tmp_path):
     L.hc_plan_autotune(plan, cache)
     lines = open(cache).read().split("\n")
     lines = [x for x in lines if x]
-    assert len(lines) == 2 * 3        # fwd_ct, blocked MAC and inv_ct for each of the two contexts
+    assert len(lines) == 2 * 4        # fwd_ct, blocked MAC, inv_ct and launch form for each of the two contexts
     chosen = {k: L.hc_ctx_get_variant(ctxs[(4096, 2)], k)
-              for k in (L.KIND_NTT_FWD_CT, L.KIND_MAC_CONV, L.KIND_NTT_INV_CT)}
+              for k in (L.KIND_NTT_FWD_CT, L.KIND_MAC_CONV, L.KIND_NTT_INV_CT, L.KIND_CONV_FORM)}
     for _ in range(2):                 # direct run, then graph captured with the tuned variants
         L.hc_plan_run(plan)
     torch.cuda.synchronize()
@@ -199,7 +199,7 @@ def test_plan_autotune_keeps_bits_and_caches(L, ctxs, tmp_path):
     for k in chosen:
         L.hc_ctx_set_variant(ctxs[(4096, 2)], k, (chosen[k] + 1) % L.N_VARIANTS)
     L.hc_plan_autotune(plan, cache)
-    assert len([x for x in open(cache).read().split("\n") if x]) == 6
+    assert len([x for x in open(cache).read().split("\n") if x]) == 8
     assert {k: L.hc_ctx_get_variant(ctxs[(4096, 2)], k) for k in chosen} == chosen
 
 
