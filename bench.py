@@ -133,9 +133,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+DEVICE_SOURCES = ("*.cuh", "hc_internal.h", "hc_launch.cu", "hc_kernels_n*.cu", "hc_mixed.cu", "hc_fused.cu")
+
+
 def source_hash():
+    """Hash of the files that define the kernels (not the host-only runtime)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2506_11586_gb300", "csrc", "*"))):
+    files = set()
+    for pat in DEVICE_SOURCES:
+        files.update(glob.glob(os.path.join(ROOT, "paper_2506_11586_gb300", "csrc", pat)))
+    for f in sorted(files):
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode() + fh.read())
     return h.hexdigest()[:16]

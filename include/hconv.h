@@ -307,8 +307,9 @@ hc_status hc_plan_run_plain(hc_plan *plan, void *cuda_stream);
  * context, by timing the plan itself (CUDA events on cuda_stream, median of
  * several runs), and set it in the contexts (hc_ctx_set_variant).  Variants
  * change speed only, never results.  cache_path (NULL = no cache) names a
- * text file of earlier choices keyed by GPU, N, L and moduli; cached choices
- * are applied without timing and new ones are appended.  The plan's outputs
+ * text file of earlier choices keyed by GPU, N, L, moduli and a signature of
+ * the plan's work (its layer shapes and product counts); cached choices are
+ * applied without timing and new ones are appended.  The plan's outputs
  * hold unspecified values afterwards.  Errors: as hc_plan_run, plus
  * HC_ERR_INVALID_ARG (unreadable cache lines are ignored, not errors). */
 hc_status hc_plan_autotune(hc_plan *plan, const char *cache_path, void *cuda_stream);

@@ -199,7 +199,34 @@ hc_status capture(hc_plan *p)
 }
 
 // ---- autotuner ------------------------------------------------------------------
-std::string tune_key(const hc_ctx *c, int kind, const char *gpu, int sms)
+// signature of the work a plan runs (shapes only, not addresses): tuned
+// choices depend on the layer mix, so they are cached per signature
+uint64_t plan_signature(const hc_plan *p)
+{
+    uint64_t h = 1469598103934665603ull;  // FNV-1a
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (v >> (8 * i)) & 0xff;
+            h *= 1099511628211ull;
+        }
+    };
+    for (const PlanConv &c : p->convs) {
+        mix(c.ctx->N);
+        mix(c.ctx->L);
+        mix(c.w->G);
+        mix(c.w->B);
+        mix(c.w->desc.M);
+        mix(c.w->I);
+        mix(c.w->O);
+    }
+    for (const PlanProd &q : p->prods) {
+        mix(q.ctx->N | (uint64_t)q.ctx->L << 32);
+        mix(q.n);
+    }
+    return h;
+}
+
+std::string tune_key(const hc_ctx *c, int kind, const char *gpu, int sms, uint64_t sig)
 {
     std::string k = gpu;
     for (char &ch : k)
@@ -211,7 +238,7 @@ std::string tune_key(const hc_ctx *c, int kind, const char *gpu, int sms)
         snprintf(buf, sizeof buf, "|%llx", (unsigned long long)c->q[i]);
         k += buf;
     }
-    snprintf(buf, sizeof buf, "|kind%d", kind);
+    snprintf(buf, sizeof buf, "|work%016llx|kind%d", (unsigned long long)sig, kind);
     return k + buf;
 }
 
@@ -553,6 +580,7 @@ hc_status hc_plan_autotune(hc_plan *p, const char *cache_path, void *cuda_stream
         if (blocked) knobs.push_back(Knob{mc, KK_CONV});  // last: the form, with the tuned kernels
     }
 
+    const uint64_t sig = plan_signature(p);
     std::vector<std::pair<std::string, int>> cache;
     if (cache_path) {
         if (FILE *f = fopen(cache_path, "r")) {
@@ -567,7 +595,7 @@ hc_status hc_plan_autotune(hc_plan *p, const char *cache_path, void *cuda_stream
     }
     std::vector<size_t> pending;
     for (size_t i = 0; i < knobs.size(); ++i) {
-        const std::string k = tune_key(knobs[i].ctx, knobs[i].kind, prop.name, prop.multiProcessorCount);
+        const std::string k = tune_key(knobs[i].ctx, knobs[i].kind, prop.name, prop.multiProcessorCount, sig);
         int v = -1;
         for (const auto &e : cache)
             if (e.first == k) v = e.second;  // last entry wins
@@ -597,7 +625,7 @@ hc_status hc_plan_autotune(hc_plan *p, const char *cache_path, void *cuda_stream
         kb.ctx->variant[kb.kind] = (uint8_t)best;
         if (st != HC_OK) break;
         if (out)
-            fprintf(out, "%s %d\n", tune_key(kb.ctx, kb.kind, prop.name, prop.multiProcessorCount).c_str(), best);
+            fprintf(out, "%s %d\n", tune_key(kb.ctx, kb.kind, prop.name, prop.multiProcessorCount, sig).c_str(), best);
     }
     if (out) fclose(out);
     return st;
