@@ -260,3 +260,55 @@ def conv_ct_pt(ct_in, Kpoly, p: Partition, moduli, ks=None, outputs=None):
                     acc += prod.astype(object)
                 out[row, comp, li] = np.mod(acc, q).astype(np.uint64)
     return out
+
+
+# ---- the server's step around the convolution (Sec. 7, Sec. 6.2) ---------------
+# The client sends encryptions of its activation share; the server adds its own
+# share, runs the convolution with the NTT-preprocessed weights, subtracts a
+# random mask (its output share) and returns only the output coefficients.
+# With Delta = floor(Q/t) (the BFV scale of bfv.Params), adding Delta*m to c0
+# adds m to the plaintext, and subtracting Delta*r from c0 subtracts r.
+
+def delta_residues(moduli, t):
+    """Delta = floor(prod(moduli) / t) reduced mod every q_i (exact integers)."""
+    Q = 1
+    for q in moduli:
+        Q *= int(q)
+    d = Q // int(t)
+    return [d % int(q) for q in moduli]
+
+
+def share_add(ct_in, x_s, p: Partition, moduli, t):
+    """Client ciphertexts [I][2][L][N] plus the server share x_s (C, H, W) in [0, t),
+    packed like the input: c0 += Delta * pack(x_s) mod q_i; c1 unchanged."""
+    packed = pack_input(np.asarray(x_s, dtype=np.int64), p).astype(object)   # [I][N], values < t
+    out = np.array(ct_in, dtype=np.uint64, copy=True)
+    d = delta_residues(moduli, t)
+    for li, q in enumerate(moduli):
+        c0 = out[:, 0, li].astype(object)
+        out[:, 0, li] = ((c0 + d[li] * packed) % int(q)).astype(np.uint64)
+    return out
+
+
+def slot_count(p: Partition):
+    return p.oh * p.ow
+
+
+def extract_masked(ct_out, r, p: Partition, moduli, t):
+    """Output ciphertexts [O][2][L][N] and the server's output mask r (M, Ho, Wo) in
+    [0, t) -> [O][L][S] with S = oh*ow: slot s = i*ow + j of output (m, b) holds
+    c0[offset + i*Ww + j] - Delta * r[m, i0+i, j0+j] mod q_l for outputs inside the
+    Ho x Wo map, and 0 for the slots of an edge block that fall outside it."""
+    S = slot_count(p)
+    d = delta_residues(moduli, t)
+    out = np.zeros((p.O, len(moduli), S), dtype=np.uint64)
+    for m in range(p.M):
+        for b in range(p.B):
+            o = m * p.B + b
+            i0, j0 = block_origin(p, b)
+            for k, row, col in output_slots(p, b):
+                rel = k - p.offset
+                s = (rel // p.Ww) * p.ow + rel % p.Ww
+                for li, q in enumerate(moduli):
+                    out[o, li, s] = (int(ct_out[o, 0, li, k]) - d[li] * int(r[m, row, col])) % int(q)
+    return out
