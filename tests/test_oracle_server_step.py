@@ -10,9 +10,10 @@ from oracle import bfv, conv
 from paper_2506_11586_gb300.inputs import CANONICAL_PRIMES, T_PLAIN, Stream
 
 
-def _setup(C_, H, W, M, kh, kw, pad, N, nl, seed):
+def _setup(C_, H, W, M, kh, kw, pad, N, nl, seed, part=None):
     s = Stream(seed, 31)
-    p = conv.canonical_partition(C_, H, W, M, kh, kw, pad, N)
+    p = conv.Partition(C_, H, W, M, kh, kw, pad, N, *part) if part else \
+        conv.canonical_partition(C_, H, W, M, kh, kw, pad, N)
     params = bfv.Params(N, CANONICAL_PRIMES[:nl], T_PLAIN)
     sk = s.ternary(N)
     x_c = s.below(T_PLAIN, C_ * H * W).astype(np.int64).reshape(C_, H, W)
@@ -44,7 +45,10 @@ def test_share_add_adds_the_share_to_the_plaintext():
 
 
 def test_server_step_decrypts_to_masked_convolution():
-    p, params, sk, x_c, x_s, K, r, ct = _setup(5, 7, 6, 3, 3, 3, 1, 4096, 2, 2)
+    # explicit partition Cw = 3, Hw = 6, Ww = 5: two channel groups (one ragged)
+    # and 2 x 2 spatial blocks whose last row of blocks is ragged
+    p, params, sk, x_c, x_s, K, r, ct = _setup(5, 7, 6, 3, 3, 3, 1, 4096, 2, 2, part=(3, 6, 5))
+    assert (p.G, p.Bh, p.Bw) == (2, 2, 2) and p.Ho % p.oh != 0
     ct1 = conv.share_add(ct, x_s, p, params.moduli, T_PLAIN)
     out = conv.conv_ct_pt(ct1, conv.pack_weights(K, p), p, params.moduli)
     slots = conv.extract_masked(out, r, p, params.moduli, T_PLAIN)
