@@ -526,6 +526,23 @@ def run_gb300(args):
                "d2h_bytes_per_step": int(h_out.numel() * 8), "ms_per_step": 1000 * statistics.mean(ts),
                "bit_exact_vs_device": bool(torch.equal(h_out, d_out.cpu()))}
 
+    # the server's whole step on the same layer: share add, convolution, output mask, slot extraction
+    step_full = None
+    if args.plain_steps > 0:
+        s_share = torch.from_numpy(Stream(2, 90).below(T_PLAIN, sh.C * sh.H * sh.W).view(np.int64)).cuda()
+        ho, wo = sh.H + 2 * sh.pad - sh.kh + 1, sh.W + 2 * sh.pad - sh.kw + 1
+        s_mask = torch.from_numpy(Stream(2, 91).below(T_PLAIN, sh.M * ho * wo).view(np.int64)).cuda()
+        n_slots = L.slot_count(w)
+        d_slots = torch.empty(geo["O"] * nl * n_slots, dtype=torch.int64, device="cuda")
+        d_full = torch.empty_like(d_out)
+        fn = lambda: L.hc_conv_server_step(ctx, w, d_in, s_share, s_mask, d_full, d_slots, stream)
+        for _ in range(3):
+            fn()
+        sms = _events_ms(fn, 50, stream, flush)
+        step_full = {"ms_per_layer": statistics.median(sms), "value": geo["products"] / (statistics.median(sms) / 1e3),
+                     "unit": UNIT, "slots_per_output": n_slots,
+                     "returned_bytes": int(d_slots.numel() * 8 + geo["O"] * nl * N * 8)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, outs, prods, el, threads = cpu_oracle_rate(args.cpu_seconds)
@@ -557,7 +574,7 @@ def run_gb300(args):
                    "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps"},
         "p50_ms": statistics.median(step_ms), "p99_ms": p99, "layer_gbs": layer_gbs,
         "roofline": roofline, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
-        "batched": batched, "serving": serving,
+        "server_step": step_full, "batched": batched, "serving": serving,
         "gpu_launches": launches, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
         "offline_weights_s": offline_s, "launch_variants": tuned, "clocks": clocks, "device": torch.cuda.get_device_name(local),
     }

@@ -234,6 +234,29 @@ hc_status hc_conv_ct_pt_host(const hc_ctx *ctx, const hc_weights *w, const uint6
 hc_status hc_conv_ct_pt_noalloc(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in,
                                 uint64_t *d_ct_out, void *cuda_stream);
 
+/* The server's whole step of one linear layer (Sec. 7: the server adds its own
+ * activation share to the client's ciphertexts, runs the convolution with the
+ * NTT-preprocessed weights and applies a random mask; Sec. 6.2: the results
+ * are sparse and only the output coefficients are returned).  With
+ * Delta = floor(Q/t) (Q the product of the context's moduli, t its plaintext
+ * modulus):
+ *   1. c0 += Delta * pack(d_share), packed like the input ciphertexts
+ *      (d_share: device [C][H][W] residues in [0, t), or NULL to skip);
+ *   2. d_ct_out = hc_conv_ct_pt of the result (full [O][2][L][N]; its c1
+ *      components are what the client needs beside the slots);
+ *   3. d_c0_slots[o][l][s] = c0[offset + i*Ww + j] - Delta * r[m][i0+i][j0+j]
+ *      mod q_l for output ct o = m*B + b and slot s = i*(Ww-kw+1) + j, with
+ *      r = d_mask (device [M][Ho][Wo] in [0, t), or NULL for r = 0), and 0 for
+ *      slots of edge blocks outside the Ho x Wo output map.  S slots per
+ *      ciphertext and limb, S = (Hw-kh+1)*(Ww-kw+1) of the resolved partition.
+ * The client decrypts slot s of output o from (d_c0_slots, c1 of d_ct_out) as
+ * conv(x_c + x_s) - r mod t.  Share and mask values must lie in [0, t).
+ * Device scratch of (2I)*2*L*N*8 bytes plus small counters comes from the
+ * allocator.  Errors: as hc_conv_ct_pt. */
+hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in,
+                              const uint64_t *d_share, const uint64_t *d_mask, uint64_t *d_ct_out,
+                              uint64_t *d_c0_slots, void *cuda_stream);
+
 /* --------------------------------------------------- generic ct x pt MAC --
  * The NTT-domain multiply-accumulate of Sec. 6.2 for arbitrary products:
  *   d_out[s] = sum_{j : h_slot[j] == s} INTT( NTT(d_ct[j]) . d_pt_ntt[j] )

@@ -96,6 +96,7 @@ _SIGS = {
     "hc_conv_ct_pt_host": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_conv_ct_pt_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_ctpt_mac": (C.c_int, [_P, _P, _P, _P, C.c_size_t, _P, C.c_size_t, _P]),
+    "hc_conv_server_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "hc_plan_create": (C.c_int, [_P, C.c_size_t, C.POINTER(_P)]),
     "hc_plan_run": (C.c_int, [_P, _P]),
     "hc_plan_run_plain": (C.c_int, [_P, _P]),
@@ -333,6 +334,19 @@ def hc_conv_ct_pt_noalloc(ctx, w, ct_in, ct_out, stream=None):
 
 def hc_conv_ct_pt_host(ctx, w, h_in, h_out, stream=None):
     _check(lib().hc_conv_ct_pt_host(ctx.ptr, w.ptr, _hptr(h_in), _hptr(h_out), _stream(stream)))
+
+
+def slot_count(w):
+    """Output slots per output ciphertext and limb of a layer: (Hw-kh+1)*(Ww-kw+1)."""
+    d = w.desc
+    return (d.Hw - d.kh + 1) * (d.Ww - d.kw + 1)
+
+
+def hc_conv_server_step(ctx, w, ct_in, share, mask, ct_out, c0_slots, stream=None):
+    """share: device [C][H][W] or None; mask: device [M][Ho][Wo] or None; c0_slots: [O][L][S]."""
+    _check(lib().hc_conv_server_step(ctx.ptr, w.ptr, _dptr(ct_in), _dptr(share) if share is not None else None,
+                                     _dptr(mask) if mask is not None else None, _dptr(ct_out), _dptr(c0_slots),
+                                     _stream(stream)))
 
 
 def hc_ctpt_mac(ctx, ct, pt_ntt, slots, out, stream=None):

@@ -241,6 +241,8 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
     // host tables: per limb, forward and inverse twiddles with Shoup companions
     std::vector<ulonglong2> tw((size_t)2 * L * N);
     std::vector<LimbConst> lcs(L);
+    std::vector<uint64_t> delta(L);
+    delta_residues(moduli, L, t, delta.data());
     for (uint32_t i = 0; i < L; ++i) {
         const uint64_t q = moduli[i];
         const uint64_t psi = min_primitive_2n_root(q, N);
@@ -274,6 +276,8 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
         lc.ninv_s = shoup_companion(lc.ninv, q);
         lc.ninvw = mulmod_u64(lc.ninv, b[1].x, q);
         lc.ninvw_s = shoup_companion(lc.ninvw, q);
+        lc.delta = delta[i];
+        lc.delta_s = shoup_companion(delta[i], q);
     }
 
     c->table_bytes = tw.size() * sizeof(ulonglong2);

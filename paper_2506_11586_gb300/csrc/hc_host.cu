@@ -166,6 +166,34 @@ uint64_t min_primitive_2n_root(uint64_t q, uint32_t N)
 
 uint64_t shoup_companion(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
 
+void delta_residues(const uint64_t *moduli, uint32_t L, uint64_t t, uint64_t *out)
+{
+    // Q = prod q_i as little-endian 64-bit words (L <= 8 limbs of < 50 bits: < 7 words)
+    uint64_t Q[9] = {1, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t i = 0; i < L; ++i) {
+        u128 carry = 0;
+        for (int w = 0; w < 9; ++w) {
+            const u128 v = (u128)Q[w] * moduli[i] + carry;
+            Q[w] = (uint64_t)v;
+            carry = v >> 64;
+        }
+    }
+    // D = floor(Q / t) by short division from the top word
+    uint64_t D[9];
+    u128 rem = 0;
+    for (int w = 8; w >= 0; --w) {
+        const u128 cur = (rem << 64) | Q[w];
+        D[w] = (uint64_t)(cur / t);
+        rem = cur % t;
+    }
+    // D mod q_i by Horner over the words
+    for (uint32_t i = 0; i < L; ++i) {
+        u128 r = 0;
+        for (int w = 8; w >= 0; --w) r = ((r << 64) | D[w]) % moduli[i];
+        out[i] = (uint64_t)r;
+    }
+}
+
 uint32_t bit_reverse(uint32_t k, uint32_t logn)
 {
     uint32_t r = 0;

@@ -29,7 +29,8 @@ struct LimbConst {
     uint64_t ninvw, ninvw_s;  // N^-1 * psi^-rev(1) mod q, companion (last GS stage)
     const ulonglong2 *tw_f;   // [N] {psi^rev(k), companion}, rev over log2 N bits
     const ulonglong2 *tw_i;   // [N] {psi^-rev(k), companion}
-    uint64_t pad_[6];         // 128-byte stride
+    uint64_t delta, delta_s;  // BFV scale floor(Q/t) mod q (Q = product of all limbs), companion
+    uint64_t pad_[4];         // 128-byte stride
 };
 static_assert(sizeof(LimbConst) == 128, "LimbConst is 128 bytes");
 
@@ -116,6 +117,8 @@ bool is_prime_u64(uint64_t n);
 uint64_t mulmod_u64(uint64_t a, uint64_t b, uint64_t q);
 uint64_t powmod_u64(uint64_t a, uint64_t e, uint64_t q);
 uint64_t min_primitive_2n_root(uint64_t q, uint32_t N);
+// floor(prod(moduli) / t) mod q_i for every limb (exact multi-precision)
+void delta_residues(const uint64_t *moduli, uint32_t L, uint64_t t, uint64_t *out);
 uint64_t shoup_companion(uint64_t w, uint64_t q);
 uint32_t bit_reverse(uint32_t k, uint32_t logn);
 

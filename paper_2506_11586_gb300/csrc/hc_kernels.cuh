@@ -29,10 +29,10 @@ namespace hc {
 template <int LOGN, int V> struct Variant;
 template <> struct Variant<12, 0> { static constexpr int LOGC = 3, NP = 2, MINB = 1; };   // T 512, 128 regs
 template <> struct Variant<12, 1> { static constexpr int LOGC = 4, NP = 2, MINB = 2; };   // T 256, 128 regs
-template <> struct Variant<12, 2> { static constexpr int LOGC = 4, NP = 1, MINB = 2; };   // T 256, 128 regs
+template <> struct Variant<12, 2> { static constexpr int LOGC = 3, NP = 1, MINB = 2; };   // T 512, 64 regs
 template <> struct Variant<13, 0> { static constexpr int LOGC = 4, NP = 2, MINB = 1; };   // T 512, 128 regs
 template <> struct Variant<13, 1> { static constexpr int LOGC = 5, NP = 1, MINB = 2; };   // T 256, 128 regs
-template <> struct Variant<13, 2> { static constexpr int LOGC = 4, NP = 1, MINB = 2; };   // T 512, 64 regs
+template <> struct Variant<13, 2> { static constexpr int LOGC = 3, NP = 1, MINB = 1; };   // T 1024, 64 regs
 template <> struct Variant<14, 0> { static constexpr int LOGC = 5, NP = 1, MINB = 1; };   // T 512, 128 regs
 template <> struct Variant<14, 1> { static constexpr int LOGC = 4, NP = 1, MINB = 1; };   // T 1024, 64 regs
 template <> struct Variant<14, 2> { static constexpr int LOGC = 5, NP = 1, MINB = 1; };   // (same as 0)

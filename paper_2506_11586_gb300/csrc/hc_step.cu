@@ -1,0 +1,155 @@
+// hc_step.cu -- the server's step around the convolution (Sec. 7): add the
+// server's activation share to the client's ciphertexts, run the convolution
+// with the NTT-preprocessed weights, subtract the server's random output mask,
+// and extract only the output coefficients of c0 (Sec. 6.2: the results are
+// sparse and only the output elements go back to the client).
+//
+// With Delta = floor(Q/t), adding Delta*x to c0 adds x to the plaintext and
+// subtracting Delta*r subtracts r.  Both are elementwise and bound by HBM.
+#include <cstring>
+
+#include "hc_arith.cuh"
+#include "hc_internal.h"
+
+namespace hc {
+namespace {
+
+struct StepGeom {
+    uint32_t C, H, W, pad, Cw, Hw, Ww, B, Bw, oh, ow, Ho, Wo, M, offset, S;
+};
+
+StepGeom geom_of(const hc_weights *w)
+{
+    const hc_conv_desc &d = w->desc;
+    StepGeom g;
+    g.C = d.C;
+    g.H = d.H;
+    g.W = d.W;
+    g.pad = d.pad;
+    g.Cw = d.Cw;
+    g.Hw = d.Hw;
+    g.Ww = d.Ww;
+    g.B = w->B;
+    g.oh = d.Hw - d.kh + 1;
+    g.ow = d.Ww - d.kw + 1;
+    g.Ho = d.H + 2 * d.pad - d.kh + 1;
+    g.Wo = d.W + 2 * d.pad - d.kw + 1;
+    g.Bw = (g.Wo + g.ow - 1) / g.ow;
+    g.M = d.M;
+    g.offset = (d.Cw - 1) * d.Hw * d.Ww + (d.kh - 1) * d.Ww + (d.kw - 1);
+    g.S = g.oh * g.ow;
+    return g;
+}
+
+// out = in with c0 += Delta * (server share packed like the input), c1 copied
+__global__ void k_share_add(const uint64_t *__restrict__ in, const uint64_t *__restrict__ share,
+                            uint64_t *__restrict__ out, const LimbConst *__restrict__ limbs, uint32_t L, uint32_t N,
+                            StepGeom g, size_t total)
+{
+    const uint32_t area = g.Hw * g.Ww;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        uint64_t v = in[i];
+        const uint32_t k = (uint32_t)(i % N);
+        const size_t rest = i / N;
+        const uint32_t limb = (uint32_t)(rest % L), comp = (uint32_t)((rest / L) % 2);
+        const uint32_t item = (uint32_t)(rest / ((size_t)2 * L));
+        if (comp == 0 && k < g.Cw * area) {
+            const uint32_t c = k / area, rem = k % area, ii = rem / g.Ww, jj = rem % g.Ww;
+            const uint32_t grp = item / g.B, b = item % g.B;
+            const uint32_t ch = grp * g.Cw + c;
+            const uint32_t r = (b / g.Bw) * g.oh + ii, s = (b % g.Bw) * g.ow + jj;  // padded coordinates
+            if (ch < g.C && r >= g.pad && r < g.H + g.pad && s >= g.pad && s < g.W + g.pad) {
+                const uint64_t x = share[((size_t)ch * g.H + (r - g.pad)) * g.W + (s - g.pad)];
+                const LimbConst &lc = limbs[limb];
+                const uint64_t q = lc.q;
+                const uint64_t dx = canon4(shoup_lazy(x, lc.delta, lc.delta_s, 0ull - q), q);
+                v = csub(v + dx, q);
+            }
+        }
+        out[i] = v;
+    }
+}
+
+// slots[o][l][s] = c0[offset + i*Ww + j] - Delta * r[m][row][col] (or 0 outside the output map)
+__global__ void k_extract_mask(const uint64_t *__restrict__ ct_out, const uint64_t *__restrict__ mask,
+                               uint64_t *__restrict__ slots, const LimbConst *__restrict__ limbs, uint32_t L,
+                               uint32_t N, StepGeom g, size_t total)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t s = (uint32_t)(i % g.S);
+        const size_t rest = i / g.S;
+        const uint32_t limb = (uint32_t)(rest % L), o = (uint32_t)(rest / L);
+        const uint32_t m = o / g.B, b = o % g.B;
+        const uint32_t ii = s / g.ow, jj = s % g.ow;
+        const uint32_t row = (b / g.Bw) * g.oh + ii, col = (b % g.Bw) * g.ow + jj;
+        uint64_t v = 0;
+        if (row < g.Ho && col < g.Wo) {
+            const uint32_t k = g.offset + ii * g.Ww + jj;
+            v = ct_out[(((size_t)o * 2) * L + limb) * N + k];
+            if (mask) {
+                const LimbConst &lc = limbs[limb];
+                const uint64_t q = lc.q;
+                const uint64_t r = mask[((size_t)m * g.Ho + row) * g.Wo + col];
+                const uint64_t dr = canon4(shoup_lazy(r, lc.delta, lc.delta_s, 0ull - q), q);
+                v = v >= dr ? v - dr : v + q - dr;
+            }
+        }
+        slots[i] = v;
+    }
+}
+
+unsigned grid_for(size_t total)
+{
+    const size_t b = (total + 255) / 256;
+    return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
+}
+
+struct Scratch {
+    void *p = nullptr;
+    cudaStream_t s;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() { dev_free(p, s); }
+};
+
+}  // namespace
+}  // namespace hc
+
+extern "C" hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in,
+                                         const uint64_t *d_share, const uint64_t *d_mask, uint64_t *d_ct_out,
+                                         uint64_t *d_c0_slots, void *cuda_stream)
+{
+    using namespace hc;
+    if (!ctx || ctx->magic != kMagicCtx || !w || w->magic != kMagicWeights)
+        return set_error(HC_ERR_INVALID_ARG, "invalid context or weights");
+    if (w->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "weights were preprocessed for another context");
+    if (!d_ct_in || !d_ct_out || !d_c0_slots) return set_error(HC_ERR_INVALID_ARG, "null buffer");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    hc_status st = check_inputs(ctx, d_ct_in, (size_t)2 * w->I, s);
+    if (st != HC_OK) return st;
+    const StepGeom g = geom_of(w);
+    const size_t in_words = (size_t)w->I * 2 * ctx->L * ctx->N;
+    const size_t conv_words = conv_scratch_words(ctx, w);
+    Scratch scratch(s);
+    scratch.p = dev_alloc((conv_words + (d_share ? in_words : 0)) * sizeof(uint64_t), s);
+    if (!scratch.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+    uint64_t *conv_scr = (uint64_t *)scratch.p;
+    const uint64_t *src = d_ct_in;
+    if (d_share) {
+        uint64_t *shared_in = conv_scr + conv_words;
+        ProfileScope ps("k_share_add", s);
+        k_share_add<<<grid_for(in_words), 256, 0, s>>>(d_ct_in, d_share, shared_in, ctx->d_limbs, ctx->L, ctx->N, g,
+                                                       in_words);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "launch k_share_add");
+        src = shared_in;
+    }
+    st = conv_layer(ctx, w, src, d_ct_out, conv_scr, conv_words, s);
+    if (st != HC_OK) return st;
+    const size_t slot_words = (size_t)w->O * ctx->L * g.S;
+    ProfileScope ps("k_extract_mask", s);
+    k_extract_mask<<<grid_for(slot_words), 256, 0, s>>>(d_ct_out, d_mask, d_c0_slots, ctx->d_limbs, ctx->L, ctx->N, g,
+                                                        slot_words);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HC_OK : cuda_error(e, "launch k_extract_mask");
+}
