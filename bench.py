@@ -313,9 +313,14 @@ def batched_squeezenet(L, stream, reps=20, with_plain=True):
                                                uniform_residues)
     ctx = L.hc_ctx_create(8192, CANONICAL_PRIMES[:3], T_PLAIN)
     items = []
-    for i, sh in enumerate(SQUEEZENET_1_1):
-        _, K = conv_tensors(sh, seed=3)
-        w = L.hc_weights_preprocess(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), K)
+    kernels = [conv_tensors(sh, seed=3)[1] for sh in SQUEEZENET_1_1]
+    torch.cuda.synchronize()
+    t_pre = time.perf_counter()
+    ws = [L.hc_weights_preprocess(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), K)
+          for sh, K in zip(SQUEEZENET_1_1, kernels)]
+    torch.cuda.synchronize()
+    offline_s = time.perf_counter() - t_pre
+    for i, (sh, w) in enumerate(zip(SQUEEZENET_1_1, ws)):
         ct = uniform_residues(Stream(3, 100 + i), CANONICAL_PRIMES[:3], (w.I, 2), 8192)
         items.append((w, torch.from_numpy(ct.view(np.int64)).cuda(),
                       torch.empty(w.O * 2 * 3 * 8192, dtype=torch.int64, device="cuda")))
@@ -347,6 +352,7 @@ def batched_squeezenet(L, stream, reps=20, with_plain=True):
            "speedup_vs_per_layer": statistics.median(pl) / ms,
            "speedup_vs_plain": pp[0] / ms if pp[0] is not None else None,
            "bit_exact_vs_per_layer": exact_layers, "bit_exact_vs_plain": exact_plain, "kernels": kern,
+           "offline_weight_ntt_s": offline_s,
            "variants": {name: L.hc_ctx_get_variant(ctx, k) for name, k in KIND_NAMES.items()}}
     plan.close()
     return out
@@ -543,6 +549,21 @@ def run_gb300(args):
                      "unit": UNIT, "slots_per_output": n_slots,
                      "returned_bytes": int(d_slots.numel() * 8 + geo["O"] * nl * N * 8)}
 
+    # the same layer with online NTT preprocessing and with none (Sec. 9's preprocessing modes)
+    modes = None
+    if args.plain_steps > 0:
+        modes = {"offline_ntt_ms": max_total_ms / args.steps}
+        for name, mode in (("online_ntt_ms", L.HC_WEIGHTS_NTT_ONLINE), ("no_ntt_ms", L.HC_WEIGHTS_NO_NTT)):
+            wm = L.hc_weights_preprocess_ex(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), K,
+                                            mode)
+            d_m = torch.empty_like(d_out)
+            fn = lambda: L.hc_conv_ct_pt(ctx, wm, d_in, d_m, stream)
+            fn()
+            ms = _events_ms(fn, 5 if mode == L.HC_WEIGHTS_NO_NTT else 20, stream, flush)
+            modes[name] = statistics.median(ms)
+            modes[name.replace("_ms", "_bit_exact")] = bool(torch.equal(d_m, d_out))
+            wm.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, outs, prods, el, threads = cpu_oracle_rate(args.cpu_seconds)
@@ -574,7 +595,7 @@ def run_gb300(args):
                    "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps"},
         "p50_ms": statistics.median(step_ms), "p99_ms": p99, "layer_gbs": layer_gbs,
         "roofline": roofline, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
-        "server_step": step_full, "batched": batched, "serving": serving,
+        "server_step": step_full, "preprocessing_modes": modes, "batched": batched, "serving": serving,
         "gpu_launches": launches, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
         "offline_weights_s": offline_s, "launch_variants": tuned, "clocks": clocks, "device": torch.cuda.get_device_name(local),
     }

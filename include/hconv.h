@@ -174,6 +174,27 @@ hc_status hc_conv_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *
 hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K,
                                 hc_weights **out, void *cuda_stream);
 
+/* NTT preprocessing modes (the paper's linear layers run "with online,
+ * offline or no NTT preprocessing", Sec. 9; Sec. 6.2 describes the offline
+ * one).  HC_WEIGHTS_NTT_OFFLINE (what hc_weights_preprocess does): packed,
+ * lifted and NTT'd once, resident in the NTT domain.  HC_WEIGHTS_NTT_ONLINE:
+ * packed and lifted, resident in the coefficient domain, NTT'd again by every
+ * hc_conv_ct_pt call (P*L*N*8 more bytes of scratch per call).
+ * HC_WEIGHTS_NO_NTT: the int8 kernel is kept as given and hc_conv_ct_pt
+ * computes every output coefficient as a direct negacyclic product sum in the
+ * coefficient domain (no transform at all).  All three give the same bits.
+ * Plans, the server, hc_conv_ct_pt_plain and hc_weights_data/export take
+ * offline weights only (online weights also export, in the coefficient
+ * domain); hc_conv_ct_pt_noalloc takes offline and no-NTT weights; the others
+ * return HC_ERR_UNSUPPORTED. */
+typedef enum {
+    HC_WEIGHTS_NTT_OFFLINE = 0,
+    HC_WEIGHTS_NTT_ONLINE = 1,
+    HC_WEIGHTS_NO_NTT = 2
+} hc_weights_mode;
+hc_status hc_weights_preprocess_ex(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K,
+                                   uint32_t mode, hc_weights **out, void *cuda_stream);
+
 /* Geometry of preprocessed weights.  Any output pointer may be NULL. */
 hc_status hc_conv_geometry(const hc_weights *w, uint32_t *n_in_ct, uint32_t *n_out_ct,
                            uint32_t *Cw, uint32_t *Hw, uint32_t *Ww);

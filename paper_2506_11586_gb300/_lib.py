@@ -88,6 +88,7 @@ _SIGS = {
     "hc_conv_partition": (C.c_int, [C.POINTER(hc_conv_desc), C.c_uint32, C.POINTER(hc_conv_desc),
                                     C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "hc_weights_preprocess": (C.c_int, [_P, C.POINTER(hc_conv_desc), _P, C.POINTER(_P), _P]),
+    "hc_weights_preprocess_ex": (C.c_int, [_P, C.POINTER(hc_conv_desc), _P, C.c_uint32, C.POINTER(_P), _P]),
     "hc_conv_geometry": (C.c_int, [_P] + [C.POINTER(C.c_uint32)] * 5),
     "hc_weights_data": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_size_t)]),
     "hc_weights_export": (C.c_int, [_P, _P, _P]),
@@ -285,13 +286,20 @@ def hc_conv_partition(desc, N):
     return res, i.value, p.value, o.value
 
 
+HC_WEIGHTS_NTT_OFFLINE, HC_WEIGHTS_NTT_ONLINE, HC_WEIGHTS_NO_NTT = 0, 1, 2
+
+
 def hc_weights_preprocess(ctx, desc, K, stream=None):
+    return hc_weights_preprocess_ex(ctx, desc, K, HC_WEIGHTS_NTT_OFFLINE, stream)
+
+
+def hc_weights_preprocess_ex(ctx, desc, K, mode, stream=None):
     K = np.ascontiguousarray(K, dtype=np.int8)
     if K.size != desc.M * desc.C * desc.kh * desc.kw:
         raise ValueError("K must have M*C*kh*kw entries")
     out = C.c_void_p()
-    _check(lib().hc_weights_preprocess(ctx.ptr, C.byref(desc), C.c_void_p(K.ctypes.data), C.byref(out),
-                                       _stream(stream)))
+    _check(lib().hc_weights_preprocess_ex(ctx.ptr, C.byref(desc), C.c_void_p(K.ctypes.data), mode, C.byref(out),
+                                          _stream(stream)))
     i, o, cw, hw, ww = (C.c_uint32() for _ in range(5))
     _check(lib().hc_conv_geometry(out, C.byref(i), C.byref(o), C.byref(cw), C.byref(hw), C.byref(ww)))
     res = hc_conv_desc(desc.C, desc.H, desc.W, desc.M, desc.kh, desc.kw, desc.stride, desc.pad,

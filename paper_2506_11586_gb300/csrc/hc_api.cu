@@ -148,12 +148,32 @@ size_t conv_counter_bound(const hc_ctx *ctx, const hc_weights *w)
 }
 
 hc_status conv_layer(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out,
-                     uint64_t *scratch, size_t scratch_words, cudaStream_t s)
+                     uint64_t *scratch, size_t scratch_words, cudaStream_t s, const uint64_t *wpt)
 {
     const size_t ntt_words = (size_t)w->I * 2 * ctx->L * ctx->N;
-    const ConvJob job{ctx, w, d_in, d_out, scratch, conv_job_blocked(ctx, w)};
+    const ConvJob job{ctx, w, d_in, d_out, scratch, conv_job_blocked(ctx, w), wpt};
     uint32_t *ctr = scratch_words > ntt_words ? reinterpret_cast<uint32_t *>(scratch + ntt_words) : nullptr;
     return launch_conv_jobs(&job, 1, s, ctr, ctr ? 2 * (scratch_words - ntt_words) : 0);
+}
+
+// one layer in the weights' preprocessing mode, scratch from the allocator
+hc_status conv_any(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out, cudaStream_t s)
+{
+    if (w->mode == HC_WEIGHTS_NO_NTT) return launch_conv_direct(ctx, w, d_in, d_out, s);
+    const size_t words = conv_scratch_words(ctx, w);
+    // the online weights start on a 256-byte boundary: the transforms store 16-byte
+    // pairs and the MAC reads them with TMA bulk copies (16-byte aligned addresses)
+    const size_t woff = (words + 31) & ~(size_t)31;
+    const size_t wwords = w->mode == HC_WEIGHTS_NTT_ONLINE ? (size_t)w->P * ctx->L * ctx->N : 0;
+    ScratchGuard scratch(s);
+    scratch.p = dev_alloc((wwords ? woff + wwords : words) * sizeof(uint64_t), s);
+    if (!scratch.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+    uint64_t *base = (uint64_t *)scratch.p;
+    if (!wwords) return conv_layer(ctx, w, d_in, d_out, base, words, s);
+    // online NTT preprocessing: transform this query's weights first
+    hc_status st = launch_ntt_fwd(ctx, w->d_pt, base + woff, w->P, s);
+    if (st != HC_OK) return st;
+    return conv_layer(ctx, w, d_in, d_out, base, words, s, base + woff);
 }
 
 // checked mode: HC_ERR_RANGE if any residue of [n][L][N] is >= its q_i (synchronises s)
@@ -409,10 +429,17 @@ hc_status hc_conv_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *
 hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K, hc_weights **out,
                                 void *cuda_stream)
 {
+    return hc_weights_preprocess_ex(ctx, desc, h_K, HC_WEIGHTS_NTT_OFFLINE, out, cuda_stream);
+}
+
+hc_status hc_weights_preprocess_ex(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K, uint32_t mode,
+                                   hc_weights **out, void *cuda_stream)
+{
     if (!out) return set_error(HC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
     if (!h_K) return set_error(HC_ERR_INVALID_ARG, "h_K is NULL");
+    if (mode > HC_WEIGHTS_NO_NTT) return set_error(HC_ERR_INVALID_ARG, "unknown weights mode %u", mode);
     hc_conv_desc res{};
     Geom g{};
     hc_status st = resolve_partition(desc, ctx->N, &res, &g);
@@ -447,6 +474,20 @@ hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, con
     w->I = g.I;
     w->P = g.P;
     w->O = g.O;
+    w->mode = mode;
+    if (mode == HC_WEIGHTS_NO_NTT) {
+        // keep the small signed weights as given; nothing is packed, lifted or transformed
+        const size_t kbytes = (size_t)res.M * res.C * res.kh * res.kw;
+        w->d_k = (int8_t *)dev_alloc_persistent(kbytes);
+        cudaError_t e = w->d_k ? cudaMemcpy(w->d_k, h_K, kbytes, cudaMemcpyHostToDevice) : cudaErrorMemoryAllocation;
+        if (e != cudaSuccess) {
+            hc_free(w);
+            return e == cudaErrorMemoryAllocation ? set_error(HC_ERR_OOM, "device allocation of weights failed")
+                                                  : cuda_error(e, "uploading weights");
+        }
+        *out = w;
+        return HC_OK;
+    }
     w->d_pt = (uint64_t *)dev_alloc_persistent((size_t)g.P * L * N * sizeof(uint64_t));
     w->d_term_ptr = (uint32_t *)dev_alloc_persistent(term_ptr.size() * sizeof(uint32_t));
     w->d_terms = (uint32_t *)dev_alloc_persistent(terms.size() * sizeof(uint32_t));
@@ -465,7 +506,7 @@ hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, con
     if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_terms, terms.data(), terms.size() * 4, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(cuda_error(e, "uploading weights"));
     st = launch_lift_int8(ctx, d_packed, w->d_pt, g.P, s);
-    if (st == HC_OK) st = launch_ntt_fwd(ctx, w->d_pt, w->d_pt, g.P, s);
+    if (st == HC_OK && mode == HC_WEIGHTS_NTT_OFFLINE) st = launch_ntt_fwd(ctx, w->d_pt, w->d_pt, g.P, s);
     if (st != HC_OK) return fail(st);
     dev_free(d_packed, s);
     d_packed = nullptr;
@@ -490,6 +531,7 @@ hc_status hc_conv_geometry(const hc_weights *w, uint32_t *n_in_ct, uint32_t *n_o
 hc_status hc_weights_data(const hc_weights *w, const uint64_t **d_pt_ntt, size_t *n_pt)
 {
     if (!weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid weights handle");
+    if (w->mode == HC_WEIGHTS_NO_NTT) return set_error(HC_ERR_UNSUPPORTED, "weights kept without NTT have no plaintexts");
     if (d_pt_ntt) *d_pt_ntt = w->d_pt;
     if (n_pt) *n_pt = w->P;
     return HC_OK;
@@ -499,6 +541,7 @@ hc_status hc_weights_export(const hc_weights *w, uint64_t *d_dst, void *cuda_str
 {
     if (!weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid weights handle");
     if (!d_dst) return set_error(HC_ERR_INVALID_ARG, "d_dst is NULL");
+    if (w->mode == HC_WEIGHTS_NO_NTT) return set_error(HC_ERR_UNSUPPORTED, "weights kept without NTT have no plaintexts");
     DeviceGuard g(w->device);
     const size_t bytes = (size_t)w->P * w->ctx->L * w->ctx->N * sizeof(uint64_t);
     HC_CUDA_TRY(cudaMemcpyAsync(d_dst, w->d_pt, bytes, cudaMemcpyDeviceToDevice, as_stream(cuda_stream)));
@@ -515,11 +558,7 @@ hc_status hc_conv_ct_pt(const hc_ctx *ctx, const hc_weights *w, const uint64_t *
     cudaStream_t s = as_stream(cuda_stream);
     hc_status st = check_inputs(ctx, d_ct_in, (size_t)2 * w->I, s);
     if (st != HC_OK) return st;
-    ScratchGuard scratch(s);
-    const size_t words = conv_scratch_words(ctx, w);
-    scratch.p = dev_alloc(words * sizeof(uint64_t), s);
-    if (!scratch.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
-    return conv_layer(ctx, w, d_ct_in, d_ct_out, (uint64_t *)scratch.p, words, s);
+    return conv_any(ctx, w, d_ct_in, d_ct_out, s);
 }
 
 hc_status hc_conv_ct_pt_plain(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in, uint64_t *d_ct_out,
@@ -528,6 +567,8 @@ hc_status hc_conv_ct_pt_plain(const hc_ctx *ctx, const hc_weights *w, const uint
     if (!ctx_ok(ctx) || !weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid context or weights");
     if (w->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "weights were preprocessed for another context");
     if (!d_ct_in || !d_ct_out) return set_error(HC_ERR_INVALID_ARG, "null ciphertext buffer");
+    if (w->mode != HC_WEIGHTS_NTT_OFFLINE)
+        return set_error(HC_ERR_UNSUPPORTED, "the plain form needs NTT-preprocessed (offline) weights");
     DeviceGuard g(ctx->device);
     cudaStream_t s = as_stream(cuda_stream);
     hc_status st = check_inputs(ctx, d_ct_in, (size_t)2 * w->I, s);
@@ -638,6 +679,7 @@ void hc_free(void *handle)
         hc_weights *w = (hc_weights *)handle;
         DeviceGuard g(w->device);
         dev_free_persistent(w->d_pt);
+        dev_free_persistent(w->d_k);
         dev_free_persistent(w->d_term_ptr);
         dev_free_persistent(w->d_terms);
         w->magic = kMagicDead;

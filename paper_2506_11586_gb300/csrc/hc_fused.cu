@@ -203,7 +203,7 @@ hc_status fused_for_ns(const ConvJob *jobs, size_t n, uint32_t *ctr, cudaStream_
         idx[P.n] = &jobs[i];
         FusedLayer &ly = P.s[P.n++];
         const ConvJob &j = jobs[i];
-        ly.mac = make_mac_seg(j.ctx, j.ntt, j.w->d_pt, j.out, j.w->G, j.w->B, j.w->desc.M);
+        ly.mac = make_mac_seg(j.ctx, j.ntt, job_weights(j), j.out, j.w->G, j.w->B, j.w->desc.M);
         ly.in = j.in;
         ly.I = j.w->I;
         ly.O = j.w->O;
@@ -256,7 +256,7 @@ size_t fused_counter_words(const ConvJob *jobs, size_t n, uint32_t logN)
     size_t words = 0;
     for (size_t i = 0; i < n; ++i) {
         if (jobs[i].ctx->logN != logN || !jobs[i].blocked) continue;
-        const MacSeg sg = make_mac_seg(jobs[i].ctx, jobs[i].ntt, jobs[i].w->d_pt, jobs[i].out, jobs[i].w->G,
+        const MacSeg sg = make_mac_seg(jobs[i].ctx, jobs[i].ntt, job_weights(jobs[i]), jobs[i].out, jobs[i].w->G,
                                        jobs[i].w->B, jobs[i].w->desc.M);
         words += jobs[i].ctx->L * (1 + sg.groups);
     }

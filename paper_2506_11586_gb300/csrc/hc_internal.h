@@ -65,7 +65,9 @@ struct hc_weights {
     int device;
     hc_conv_desc desc;        // resolved partition
     uint32_t G, B, I, P, O;
-    uint64_t *d_pt;           // [P][L][N] NTT domain (owned)
+    uint32_t mode;            // hc_weights_mode
+    uint64_t *d_pt;           // [P][L][N] NTT domain (offline mode) or coefficient domain (online mode), owned
+    int8_t *d_k;              // [M][C][kh][kw] (no-NTT mode), owned
     uint32_t *d_terms;        // CSR of output terms (owned): see mac kernels
     uint32_t *d_term_ptr;     // [O+1]
 };
@@ -185,7 +187,9 @@ struct ConvJob {
     uint64_t *out;        // [O][2][L][N] coefficient domain
     uint64_t *ntt;        // scratch: NTT-domain inputs [I][2][L][N]
     bool blocked;         // blocked MAC fits (else fused MAC + inverse NTT)
+    const uint64_t *wpt = nullptr;  // NTT-domain weights [P][L][N]; nullptr: the resident ones
 };
+inline const uint64_t *job_weights(const ConvJob &c) { return c.wpt ? c.wpt : c.w->d_pt; }
 bool conv_job_blocked(const hc_ctx *c, const hc_weights *w);
 // The batched launch sequence of n conv jobs in stream order on s.  Per ring
 // degree, when the first job's context selects the fused form (KK_CONV) and
@@ -289,7 +293,11 @@ hc_status launch_range_check(const hc_ctx *ctx, const uint64_t *p, size_t n_poly
 // place; falls back to the fused MAC + inverse NTT kernel for layers whose
 // input chunk does not fit the blocked MAC's shared memory
 hc_status conv_layer(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out,
-                     uint64_t *scratch, size_t scratch_words, cudaStream_t s);
+                     uint64_t *scratch, size_t scratch_words, cudaStream_t s, const uint64_t *wpt = nullptr);
+// one layer in the weights' preprocessing mode (offline NTT, online NTT, no NTT)
+hc_status conv_any(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out, cudaStream_t s);
+hc_status launch_conv_direct(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out,
+                             cudaStream_t s);
 // scratch words conv_layer uses at most (NTT-domain inputs + fused-form counters)
 size_t conv_scratch_words(const hc_ctx *ctx, const hc_weights *w);
 // an upper bound of the fused form's counter words for one layer (any MAC variant)

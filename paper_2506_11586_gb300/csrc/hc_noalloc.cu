@@ -51,6 +51,14 @@ extern "C" hc_status hc_conv_ct_pt_noalloc(const hc_ctx *ctx, const hc_weights *
         return set_error(HC_ERR_INVALID_ARG, "invalid context or weights");
     if (w->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "weights were preprocessed for another context");
     if (!d_ct_in || !d_ct_out) return set_error(HC_ERR_INVALID_ARG, "null ciphertext buffer");
+    if (w->mode == HC_WEIGHTS_NO_NTT) {  // needs no scratch at all
+        DeviceGuard g(ctx->device);
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+        hc_status st = check_inputs(ctx, d_ct_in, (size_t)2 * w->I, s);
+        return st == HC_OK ? launch_conv_direct(ctx, w, d_ct_in, d_ct_out, s) : st;
+    }
+    if (w->mode != HC_WEIGHTS_NTT_OFFLINE)
+        return set_error(HC_ERR_UNSUPPORTED, "online NTT preprocessing needs allocated scratch");
     const size_t words = (size_t)w->I * 2 * ctx->L * ctx->N;
     if (words > kStaticScratchWords)
         return set_error(HC_ERR_BUDGET,

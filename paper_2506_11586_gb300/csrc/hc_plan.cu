@@ -314,9 +314,9 @@ hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s, uint32
         hc_status st = launch_ntt_fwd_ct(c.ctx, c.in, c.ntt, c.w->I, s);
         if (st != HC_OK) return st;
         if (!c.blocked)
-            return launch_mac_intt(c.ctx, c.ntt, c.w->d_pt, MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out, c.w->O,
+            return launch_mac_intt(c.ctx, c.ntt, job_weights(c), MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out, c.w->O,
                                    s);
-        st = launch_mac_conv(c.ctx, c.ntt, c.w->d_pt, c.out, c.w->G, c.w->B, c.w->desc.M, s);
+        st = launch_mac_conv(c.ctx, c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->desc.M, s);
         if (st != HC_OK) return st;
         return launch_ntt_inv_ct(c.ctx, c.out, c.out, c.w->O, s);
     }
@@ -348,9 +348,9 @@ hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s, uint32
         if (done(c)) continue;
         if (c.blocked) {
             mctx.push_back(c.ctx);
-            layers.push_back(MacLayer{c.ntt, c.w->d_pt, c.out, c.w->G, c.w->B, c.w->desc.M});
+            layers.push_back(MacLayer{c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->desc.M});
         } else {
-            hc_status st = launch_mac_intt(c.ctx, c.ntt, c.w->d_pt, MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out,
+            hc_status st = launch_mac_intt(c.ctx, c.ntt, job_weights(c), MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out,
                                            c.w->O, s);
             if (st != HC_OK) return st;
         }
@@ -413,6 +413,8 @@ hc_status hc_plan_create(const hc_work_item *items, size_t n, hc_plan **out)
         if (it.kind == HC_WORK_CONV) {
             if (!weights_ok(it.weights) || it.weights->ctx != it.ctx)
                 return set_error(HC_ERR_INVALID_ARG, "item %zu: weights invalid or of another context", i);
+            if (it.weights->mode != HC_WEIGHTS_NTT_OFFLINE)
+                return set_error(HC_ERR_UNSUPPORTED, "item %zu: plans need NTT-preprocessed (offline) weights", i);
         } else if (it.kind == HC_WORK_PRODUCTS) {
             if (it.n == 0 || !it.d_pt_ntt) return set_error(HC_ERR_INVALID_ARG, "item %zu: empty product list", i);
         } else {

@@ -400,6 +400,8 @@ hc_status hc_server_add_layer(hc_server *s, const hc_ctx *ctx, const hc_weights 
     if (!ctx || ctx->magic != kMagicCtx || !w || w->magic != kMagicWeights || w->ctx != ctx)
         return set_error(HC_ERR_INVALID_ARG, "invalid context or weights");
     if (ctx->device != s->device) return set_error(HC_ERR_INVALID_ARG, "context on another device");
+    if (w->mode != HC_WEIGHTS_NTT_OFFLINE)
+        return set_error(HC_ERR_UNSUPPORTED, "the server needs NTT-preprocessed (offline) weights");
     Layer ly;
     ly.ctx = ctx;
     ly.w = w;

@@ -129,14 +129,12 @@ extern "C" hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w,
     if (st != HC_OK) return st;
     const StepGeom g = geom_of(w);
     const size_t in_words = (size_t)w->I * 2 * ctx->L * ctx->N;
-    const size_t conv_words = conv_scratch_words(ctx, w);
     Scratch scratch(s);
-    scratch.p = dev_alloc((conv_words + (d_share ? in_words : 0)) * sizeof(uint64_t), s);
-    if (!scratch.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
-    uint64_t *conv_scr = (uint64_t *)scratch.p;
     const uint64_t *src = d_ct_in;
     if (d_share) {
-        uint64_t *shared_in = conv_scr + conv_words;
+        scratch.p = dev_alloc(in_words * sizeof(uint64_t), s);
+        if (!scratch.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+        uint64_t *shared_in = (uint64_t *)scratch.p;
         ProfileScope ps("k_share_add", s);
         k_share_add<<<grid_for(in_words), 256, 0, s>>>(d_ct_in, d_share, shared_in, ctx->d_limbs, ctx->L, ctx->N, g,
                                                        in_words);
@@ -144,7 +142,7 @@ extern "C" hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w,
         if (e != cudaSuccess) return cuda_error(e, "launch k_share_add");
         src = shared_in;
     }
-    st = conv_layer(ctx, w, src, d_ct_out, conv_scr, conv_words, s);
+    st = conv_any(ctx, w, src, d_ct_out, s);  // any preprocessing mode
     if (st != HC_OK) return st;
     const size_t slot_words = (size_t)w->O * ctx->L * g.S;
     ProfileScope ps("k_extract_mask", s);
