@@ -298,6 +298,8 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
         lc.ninvw_s = shoup_companion(lc.ninvw, q);
         lc.delta = delta[i];
         lc.delta_s = shoup_companion(delta[i], q);
+        const uint64_t c50 = (1ull << 50) - q;
+        lc.special_c = c50 > 0 && c50 < (1ull << 22) ? c50 : 0;
     }
 
     c->table_bytes = tw.size() * sizeof(ulonglong2);

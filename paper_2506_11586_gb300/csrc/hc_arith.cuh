@@ -174,4 +174,37 @@ __device__ __forceinline__ uint64_t mac_reduce(const MacAcc &a, uint64_t q, uint
     return canon4(s, q);
 }
 
+// canonical V mod q for q = 2^50 - c with 0 < c < 2^22, V < 2^104 (at most 16
+// terms of products of residues below 2^50): with A = V >> 50 and
+// B = V mod 2^50, V = A*2^50 + B = A*c + B (mod q); folding A*c (< 2^76) once
+// more the same way leaves B + B2 + A2*c < 2.25 * 2^50 < 3q.  Three wide
+// 32-bit products instead of the generic reduction's Shoup step.
+__device__ __forceinline__ uint64_t mac_reduce_special(const MacAcc &a, uint64_t q, uint32_t c)
+{
+    uint64_t lo, hi;
+    asm("{\n\t"
+        ".reg .u32 sl, sh, l0, l1, h0;\n\t"
+        ".reg .u64 t;\n\t"
+        "mov.b64 {sl, sh}, %3;\n\t"
+        "mov.b64 {l0, l1}, %2;\n\t"
+        "add.cc.u32 l1, l1, sl;\n\t"
+        "addc.u32 h0, %5, sh;\n\t"
+        "mov.b64 %0, {l0, l1};\n\t"
+        "cvt.u64.u32 t, h0;\n\t"
+        "add.u64 %1, %4, t;\n\t"
+        "}"
+        : "=l"(lo), "=l"(hi)
+        : "l"(a.s0), "l"(a.s1), "l"(a.s2), "r"(a.c0));
+    constexpr uint64_t M50 = (1ull << 50) - 1;
+    const uint64_t A = (hi << 14) | (lo >> 50);  // < 2^54
+    const uint64_t B = lo & M50;
+    const uint64_t p0 = (uint64_t)(uint32_t)A * c;          // < 2^54
+    const uint64_t p1 = (uint64_t)(uint32_t)(A >> 32) * c;  // < 2^44
+    const uint64_t plo = p0 + (p1 << 32);
+    const uint64_t phi = (p1 >> 32) + (plo < p0 ? 1 : 0);
+    const uint64_t A2 = (phi << 14) | (plo >> 50);          // < 2^26
+    const uint64_t r = B + (plo & M50) + (uint64_t)(uint32_t)A2 * c;
+    return canon3(r, q);
+}
+
 }  // namespace hc

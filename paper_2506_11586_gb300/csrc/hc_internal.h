@@ -30,7 +30,8 @@ struct LimbConst {
     const ulonglong2 *tw_f;   // [N] {psi^rev(k), companion}, rev over log2 N bits
     const ulonglong2 *tw_i;   // [N] {psi^-rev(k), companion}
     uint64_t delta, delta_s;  // BFV scale floor(Q/t) mod q (Q = product of all limbs), companion
-    uint64_t pad_[4];         // 128-byte stride
+    uint64_t special_c;       // c when q = 2^50 - c with 0 < c < 2^22 (cheaper MAC reduction), else 0
+    uint64_t pad_[3];         // 128-byte stride
 };
 static_assert(sizeof(LimbConst) == 128, "LimbConst is 128 bytes");
 

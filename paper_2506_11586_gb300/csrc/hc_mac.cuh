@@ -73,6 +73,10 @@ __device__ __forceinline__ bool mac_task(const MacSeg &sg, uint32_t chunk, uint3
     const LimbConst &lc = sg.limbs[limb];
     const uint64_t q = lc.q, nq = 0ull - q, r64 = lc.r64, r64_s = lc.r64_s;
     const uint32_t ones = (uint32_t)lc.one_s;
+    // inputs are canonical forward-NTT outputs (< q < 2^50), so with at most 16 terms
+    // per row the special-form reduction applies whenever q = 2^50 - c, c small
+    const uint32_t sc = (uint32_t)lc.special_c;
+    const bool special = sc != 0 && G <= 16;
     const uint32_t k = tid % KC, h = tid / KC;  // h is warp-uniform
     const uint32_t xstep = P * KC;
     bool ok = mbar_wait(&bars[0], ring.xuse & 1);
@@ -102,7 +106,7 @@ __device__ __forceinline__ bool mac_task(const MacSeg &sg, uint32_t chunk, uint3
             }
             if (g < G) mac_add(acc0, xp[0], wk[g * KC]);
             mac_merge(acc0, acc1);
-            *yp = mac_reduce(acc0, q, nq, r64, r64_s, ones);
+            *yp = special ? mac_reduce_special(acc0, q, sc) : mac_reduce(acc0, q, nq, r64, r64_s, ones);
         };
         const uint64_t *xk = xs + k;
         if (P >= (uint32_t)H) {  // every row group has work in every channel

@@ -7,7 +7,8 @@ import pytest
 
 from gpu_util import sample_indices, to_dev, to_host
 from oracle import bfv, conv, core
-from paper_2506_11586_gb300.inputs import (CANONICAL_PRIMES, CONV_56x56x64, T_PLAIN, Stream, conv_tensors)
+from paper_2506_11586_gb300.inputs import (CANONICAL_PRIMES, CONV_56x56x64, T_PLAIN, Stream, conv_tensors,
+                                           uniform_residues)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -162,3 +163,38 @@ def test_conv_argument_errors(L):
     L.hc_conv_ct_pt(ctx, w, buf, out)                 # all-zero input -> all-zero output
     torch.cuda.synchronize()
     assert int(out.abs().sum()) == 0
+
+
+@pytest.mark.parametrize("moduli_kind", ["far_from_2^50", "canonical_G_over_16"])
+def test_generic_reduction_paths(L, moduli_kind):
+    """The MAC's reduction has a special form for q = 2^50 - c with small c (the
+    canonical primes) and a generic one; this covers the generic one twice:
+    primes far below 2^50, and canonical primes with more than 16 channel groups
+    (where the special form's input bound does not hold)."""
+    N = 8192
+    if moduli_kind == "far_from_2^50":
+        moduli = tuple(core.ntt_primes(47, 15, 3))
+        shape, part = (9, 11, 11, 5, 3, 3, 1), None
+    else:
+        moduli = CANONICAL_PRIMES[:3]
+        shape, part = (34, 6, 6, 3, 1, 1, 0), (2, 6, 6)    # Cw = 2 -> G = 17
+    C_, H, W, M, kh, kw, pad = shape
+    assert all(2 ** 32 < q < 2 ** 50 and q % (2 * N) == 1 for q in moduli)
+    s = Stream(77, len(moduli))
+    K = s.int8(M * C_ * kh * kw).astype(np.int64).reshape(M, C_, kh, kw)
+    p = conv.Partition(C_, H, W, M, kh, kw, pad, N, *part) if part else \
+        conv.canonical_partition(C_, H, W, M, kh, kw, pad, N)
+    if part:
+        assert p.G == 17
+    else:
+        assert all((1 << 50) - q >= (1 << 22) for q in moduli)
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    w = L.hc_weights_preprocess(ctx, L.make_desc(C_, H, W, M, kh, kw, pad=pad, Cw=p.Cw, Hw=p.Hw, Ww=p.Ww),
+                                K.astype(np.int8))
+    ct = uniform_residues(s, moduli, (p.I, 2), N)
+    out = torch.empty(p.O * 2 * len(moduli) * N, dtype=torch.int64, device="cuda")
+    L.hc_conv_ct_pt(ctx, w, to_dev(ct), out)
+    torch.cuda.synchronize()
+    ks = sample_indices(N, 24, 9)
+    want = conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, moduli, ks)
+    assert np.array_equal(to_host(out).reshape(p.O, 2, len(moduli), N)[..., ks], want)
