@@ -495,6 +495,18 @@ def run_gb300(args):
                      "kernel_ms": k_avg_ms, "kernel_share": kms / total_ms if total_ms else None})
     layer_gbs = bytes_layer * args.steps / (total_ms / 1000.0) / 1e9
 
+    # the same layer as a one-item plan replayed from a CUDA graph (same stream, same L2 flush)
+    graph = None
+    if args.plain_steps > 0:
+        plan1 = L.hc_plan_create([L.work_conv(ctx, w, d_in, d_out)])
+        for _ in range(3):
+            L.hc_plan_run(plan1, stream)
+        gms = _events_ms(lambda: L.hc_plan_run(plan1, stream), 200, stream, flush)
+        graph = {"ms_per_step": statistics.median(gms), "p99_ms": sorted(gms)[int(0.99 * (len(gms) - 1))],
+                 "value": geo["products"] / (statistics.median(gms) / 1e3), "unit": UNIT,
+                 "launches_per_step": L.hc_plan_info(plan1)[2]}
+        plan1.close()
+
     # plain one-launch-per-product path on the same inputs (comparison)
     plain = None
     if args.plain_steps > 0:
@@ -594,7 +606,7 @@ def run_gb300(args):
                    "products_per_layer": geo["products"], "partition": [geo["Cw"], geo["Hw"], geo["Ww"]],
                    "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps"},
         "p50_ms": statistics.median(step_ms), "p99_ms": p99, "layer_gbs": layer_gbs,
-        "roofline": roofline, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
+        "roofline": roofline, "graph": graph, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
         "server_step": step_full, "preprocessing_modes": modes, "batched": batched, "serving": serving,
         "gpu_launches": launches, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
         "offline_weights_s": offline_s, "launch_variants": tuned, "clocks": clocks, "device": torch.cuda.get_device_name(local),

@@ -153,7 +153,7 @@ struct MacSeg {
     const uint64_t *W;
     uint64_t *Y;
     const LimbConst *limbs;
-    uint32_t N, L, G, B, M, MB, MS, chunks, groups, cta_begin;
+    uint32_t N, L, G, B, M, MB, MS, KC, chunks, groups, cta_begin;
 };
 template <int NS>
 struct MacSegsT {
@@ -170,8 +170,9 @@ struct MacLayer {
 };
 bool mac_conv_fits(uint32_t G, uint32_t B);
 // MAC task geometry of one layer (channels per stage from the context's variant)
+// (kc = 0: the chunk width of the context's variant; 32 or 64 forces it)
 MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
-                    uint32_t M);
+                    uint32_t M, uint32_t kc = 0);
 size_t mac_seg_smem(const MacSeg &sg);
 // blocked MACs of n layers (layer i on ctxs[i]) in ceil(n / kMaxSegs) launches
 hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s);

@@ -83,29 +83,32 @@ k_mac_conv(const __grid_constant__ MacSegsT<NS> segs, int *err)
     mac_task<KC, kMacThreads>(sg, chunk, limb, m0, m1, dsm, bars, ring, err);
 }
 
-// stage rows targeted by each launch variant of the blocked MAC
-constexpr uint32_t kMacStageRows[kNumVariants] = {8, 16, 32};
+// launch variants of the blocked MAC: (slots per chunk, weight rows per stage)
+constexpr uint32_t kMacVariantKC[kNumVariants] = {64, 64, 32};
+constexpr uint32_t kMacStageRows[kNumVariants] = {8, 16, 16};
 constexpr size_t kMacSmemCap = 200 * 1024;
 
-static size_t mac_smem(uint32_t G, uint32_t B, uint32_t MS)
+static size_t mac_smem(uint32_t G, uint32_t B, uint32_t MS, uint32_t kc)
 {
-    return ((size_t)G * 2 * B + (size_t)kMacStages * MS * G) * kMacKC * sizeof(uint64_t);
+    return ((size_t)G * 2 * B + (size_t)kMacStages * MS * G) * kc * sizeof(uint64_t);
 }
 
 // channels per stage: about the variant's stage rows, within the shared-memory cap
-static uint32_t mac_stage_channels(uint32_t G, uint32_t B, uint32_t M, int variant)
+static uint32_t mac_stage_channels(uint32_t G, uint32_t B, uint32_t M, int variant, uint32_t kc)
 {
     uint32_t ms = kMacStageRows[variant] / G;
     if (ms < 1) ms = 1;
     if (ms > M) ms = M;
-    while (ms > 1 && mac_smem(G, B, ms) > kMacSmemCap / 2) --ms;  // keep two CTAs per SM where possible
+    while (ms > 1 && mac_smem(G, B, ms, kc) > kMacSmemCap / 2) --ms;  // keep two CTAs per SM where possible
     return ms;
 }
 
 // fill the launch geometry of one segment: enough CTAs for about four waves
 MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
-                      uint32_t M)
+                    uint32_t M, uint32_t kc)
 {
+    const int v = ctx->variant[KK_MACB];
+    if (kc == 0) kc = kMacVariantKC[v];
     MacSeg sg{};
     sg.X = x;
     sg.W = w;
@@ -116,10 +119,11 @@ MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uin
     sg.G = G;
     sg.B = B;
     sg.M = M;
-    sg.MS = mac_stage_channels(G, B, M, ctx->variant[KK_MACB]);
-    const size_t smem = mac_smem(G, B, sg.MS);
+    sg.KC = kc;
+    sg.MS = mac_stage_channels(G, B, M, v, kc);
+    const size_t smem = mac_smem(G, B, sg.MS, kc);
     const uint32_t per_sm = (uint32_t)(kMacSmemCap / smem) < 4 ? (uint32_t)(kMacSmemCap / smem) : 4;
-    sg.chunks = ctx->N / kMacKC;
+    sg.chunks = ctx->N / kc;
     const uint32_t target = 152 * (per_sm ? per_sm : 1) * 4;
     const uint32_t want = (target + sg.chunks * ctx->L - 1) / (sg.chunks * ctx->L);
     const uint32_t groups = want < 1 ? 1 : (want > M ? M : want);
@@ -129,14 +133,14 @@ MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uin
     return sg;
 }
 
-template <int NS>
-static hc_status run_mac_segs(MacSegsT<NS> &segs, size_t smem, int *err, cudaStream_t s)
+template <int KC, int NS>
+static hc_status run_mac_segs_kc(MacSegsT<NS> &segs, size_t smem, int *err, cudaStream_t s)
 {
     static std::atomic<uint32_t> attr_done{0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!(attr_done.load() & (1u << (dev & 31)))) {
-        cudaError_t e = cudaFuncSetAttribute(k_mac_conv<kMacKC, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_mac_conv<KC, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kMacSmemCap);
         if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_mac_conv)");
         attr_done.fetch_or(1u << (dev & 31));
@@ -148,28 +152,36 @@ static hc_status run_mac_segs(MacSegsT<NS> &segs, size_t smem, int *err, cudaStr
     }
     if (begin == 0) return HC_OK;
     ProfileScope ps("k_mac_conv", s);
-    k_mac_conv<kMacKC, NS><<<begin, kMacThreads, smem, s>>>(segs, err);
+    k_mac_conv<KC, NS><<<begin, kMacThreads, smem, s>>>(segs, err);
     return after_launch_status("k_mac_conv");
+}
+
+// every segment of one launch has the same chunk width
+template <int NS>
+static hc_status run_mac_segs(MacSegsT<NS> &segs, size_t smem, int *err, cudaStream_t s)
+{
+    return segs.s[0].KC == 32 ? run_mac_segs_kc<32, NS>(segs, smem, err, s)
+                              : run_mac_segs_kc<64, NS>(segs, smem, err, s);
 }
 
 size_t mac_seg_smem(const MacSeg &sg)
 {
-    return mac_smem(sg.G, sg.B, sg.MS);
+    return mac_smem(sg.G, sg.B, sg.MS, sg.KC);
 }
 
 bool mac_conv_fits(uint32_t G, uint32_t B)
 {
-    return mac_smem(G, B, 1) <= kMacSmemCap;
+    return mac_smem(G, B, 1, 64) <= kMacSmemCap;
 }
 
 hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64_t *w_ntt, uint64_t *y, uint32_t G,
                           uint32_t B, uint32_t M, cudaStream_t s)
 {
-    if (!mac_conv_fits(G, B) || ctx->N % kMacKC) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
+    if (!mac_conv_fits(G, B) || ctx->N % 64) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
     MacSegs1 segs{};
     segs.n = 1;
     segs.s[0] = make_mac_seg(ctx, x_ntt, w_ntt, y, G, B, M);
-    return run_mac_segs(segs, mac_smem(G, B, segs.s[0].MS), ctx->d_flag + 1, s);
+    return run_mac_segs(segs, mac_seg_smem(segs.s[0]), ctx->d_flag + 1, s);
 }
 
 hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s)
@@ -178,11 +190,12 @@ hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *laye
         MacSegs segs{};
         size_t smem = 0;
         const size_t i1 = i0 + kMaxSegs < n ? i0 + kMaxSegs : n;
+        const uint32_t kc = kMacVariantKC[ctxs[i0]->variant[KK_MACB]];  // one chunk width per launch
         for (size_t i = i0; i < i1; ++i) {
             const MacLayer &ly = layers[i];
             if (!mac_conv_fits(ly.G, ly.B)) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
-            segs.s[segs.n] = make_mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M);
-            const size_t sm = mac_smem(ly.G, ly.B, segs.s[segs.n++].MS);
+            segs.s[segs.n] = make_mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M, kc);
+            const size_t sm = mac_seg_smem(segs.s[segs.n++]);
             if (sm > smem) smem = sm;
         }
         hc_status st = run_mac_segs(segs, smem, ctxs[i0]->d_flag + 1, s);
