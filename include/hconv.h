@@ -99,8 +99,8 @@ hc_status hc_selftest_wait_timeout(const hc_ctx *ctx, uint32_t limit, void *cuda
  * 7 convolution launch form.  variant (0..2) selects, for kinds 0-5, the radix
  * per register round, the polynomials per CTA and the CTAs per SM for the
  * context's N (variant 2 of the inverse kinds at N <= 8192 is a persistent,
- * TMA-fed kernel); for kind 6 the chunk width and the weight rows per pipeline
- * stage (64 slots and about 8 rows, 64 and 16, 32 and 16); for kind 7 either three launches per ring degree (forward NTTs,
+ * TMA-fed kernel); for kind 6 the weight rows per pipeline stage (about 8, 16
+ * or 32; a 32-slot chunk width is supported by the kernel but measured slower); for kind 7 either three launches per ring degree (forward NTTs,
  * MACs, inverse NTTs: variant 0) or one persistent launch whose CTAs take the
  * layers' NTT, MAC and INTT tasks in order and wait on per-limb completion
  * counters (variants 1 and 2).  Every variant

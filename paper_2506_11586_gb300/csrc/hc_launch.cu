@@ -84,8 +84,8 @@ k_mac_conv(const __grid_constant__ MacSegsT<NS> segs, int *err)
 }
 
 // launch variants of the blocked MAC: (slots per chunk, weight rows per stage)
-constexpr uint32_t kMacVariantKC[kNumVariants] = {64, 64, 32};
-constexpr uint32_t kMacStageRows[kNumVariants] = {8, 16, 16};
+constexpr uint32_t kMacVariantKC[kNumVariants] = {64, 64, 64};
+constexpr uint32_t kMacStageRows[kNumVariants] = {8, 16, 32};
 constexpr size_t kMacSmemCap = 200 * 1024;
 
 static size_t mac_smem(uint32_t G, uint32_t B, uint32_t MS, uint32_t kc)

@@ -19,6 +19,8 @@
 // makes the task return false.
 #pragma once
 
+#include <type_traits>
+
 #include "hc_arith.cuh"
 #include "hc_async.cuh"
 #include "hc_internal.h"
@@ -108,12 +110,52 @@ __device__ __forceinline__ bool mac_task(const MacSeg &sg, uint32_t chunk, uint3
             mac_merge(acc0, acc1);
             *yp = special ? mac_reduce_special(acc0, q, sc) : mac_reduce(acc0, q, nq, r64, r64_s, ones);
         };
+        // CR channels x RR rows (rows p and p + H) at once: each input slot and each
+        // weight slot read from shared memory once per tile instead of once per term
+        auto tile = [&](auto cr, auto rr, const uint64_t *xp, const uint64_t *wk, uint64_t *yp) {
+            constexpr int CR = decltype(cr)::value, RR = decltype(rr)::value;
+            MacAcc acc[CR][RR];
+#pragma unroll
+            for (int c = 0; c < CR; ++c)
+#pragma unroll
+                for (int r = 0; r < RR; ++r) mac_zero(acc[c][r]);
+            for (uint32_t g = 0; g < G; ++g, xp += xstep, wk += KC) {
+                uint64_t xv[RR], wv[CR];
+#pragma unroll
+                for (int r = 0; r < RR; ++r) xv[r] = xp[r * H * KC];
+#pragma unroll
+                for (int c = 0; c < CR; ++c) wv[c] = wk[(size_t)c * G * KC];
+#pragma unroll
+                for (int c = 0; c < CR; ++c)
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) mac_add(acc[c][r], xv[r], wv[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < CR; ++c)
+#pragma unroll
+                for (int r = 0; r < RR; ++r)
+                    yp[(size_t)c * P * LN + (size_t)r * H * LN] =
+                        special ? mac_reduce_special(acc[c][r], q, sc) : mac_reduce(acc[c][r], q, nq, r64, r64_s, ones);
+        };
+        using I1 = std::integral_constant<int, 1>;
+        using I2 = std::integral_constant<int, 2>;
         const uint64_t *xk = xs + k;
         if (P >= (uint32_t)H) {  // every row group has work in every channel
-            const uint64_t *wk = wst;
-            uint64_t *ym = yk;
-            for (uint32_t ml = 0; ml < cnt; ++ml, wk += G * KC, ym += P * LN)
-                for (uint32_t p = h; p < P; p += H) row(xk + p * KC, wk, ym + p * LN);
+            uint32_t ml = 0;
+            for (; ml + 1 < cnt; ml += 2) {  // channel pairs
+                const uint64_t *wk = wst + (size_t)ml * G * KC;
+                uint64_t *ym = yk + (size_t)ml * P * LN;
+                uint32_t p = h;
+                for (; p + H < P; p += 2 * H) tile(I2{}, I2{}, xk + p * KC, wk, ym + p * LN);
+                if (p < P) tile(I2{}, I1{}, xk + p * KC, wk, ym + p * LN);
+            }
+            if (ml < cnt) {  // the last channel alone
+                const uint64_t *wk = wst + (size_t)ml * G * KC;
+                uint64_t *ym = yk + (size_t)ml * P * LN;
+                uint32_t p = h;
+                for (; p + H < P; p += 2 * H) tile(I1{}, I2{}, xk + p * KC, wk, ym + p * LN);
+                if (p < P) row(xk + p * KC, wk, ym + p * LN);
+            }
         } else {                 // few rows per channel: spread (channel, row) pairs over the groups
             const uint32_t jobs = cnt * P;
             uint32_t ml = h / P, p = h % P;
