@@ -112,7 +112,7 @@ __device__ __forceinline__ bool mac_task(const MacSeg &sg, uint32_t chunk, uint3
         };
         // CR channels x RR rows (rows p and p + H) at once: each input slot and each
         // weight slot read from shared memory once per tile instead of once per term
-        auto tile = [&](auto cr, auto rr, const uint64_t *xp, const uint64_t *wk, uint64_t *yp) {
+        auto tile = [&](auto cr, auto rr, const uint64_t *xp, const uint64_t *wk, uint64_t *yp, uint32_t cs) {
             constexpr int CR = decltype(cr)::value, RR = decltype(rr)::value;
             MacAcc acc[CR][RR];
 #pragma unroll
@@ -124,7 +124,7 @@ __device__ __forceinline__ bool mac_task(const MacSeg &sg, uint32_t chunk, uint3
 #pragma unroll
                 for (int r = 0; r < RR; ++r) xv[r] = xp[r * H * KC];
 #pragma unroll
-                for (int c = 0; c < CR; ++c) wv[c] = wk[(size_t)c * G * KC];
+                for (int c = 0; c < CR; ++c) wv[c] = wk[(size_t)c * cs * G * KC];
 #pragma unroll
                 for (int c = 0; c < CR; ++c)
 #pragma unroll
@@ -134,7 +134,7 @@ __device__ __forceinline__ bool mac_task(const MacSeg &sg, uint32_t chunk, uint3
             for (int c = 0; c < CR; ++c)
 #pragma unroll
                 for (int r = 0; r < RR; ++r)
-                    yp[(size_t)c * P * LN + (size_t)r * H * LN] =
+                    yp[(size_t)c * cs * P * LN + (size_t)r * H * LN] =
                         special ? mac_reduce_special(acc[c][r], q, sc) : mac_reduce(acc[c][r], q, nq, r64, r64_s, ones);
         };
         using I1 = std::integral_constant<int, 1>;
@@ -146,16 +146,22 @@ __device__ __forceinline__ bool mac_task(const MacSeg &sg, uint32_t chunk, uint3
                 const uint64_t *wk = wst + (size_t)ml * G * KC;
                 uint64_t *ym = yk + (size_t)ml * P * LN;
                 uint32_t p = h;
-                for (; p + H < P; p += 2 * H) tile(I2{}, I2{}, xk + p * KC, wk, ym + p * LN);
-                if (p < P) tile(I2{}, I1{}, xk + p * KC, wk, ym + p * LN);
+                for (; p + H < P; p += 2 * H) tile(I2{}, I2{}, xk + p * KC, wk, ym + p * LN, 1);
+                if (p < P) tile(I2{}, I1{}, xk + p * KC, wk, ym + p * LN, 1);
             }
             if (ml < cnt) {  // the last channel alone
                 const uint64_t *wk = wst + (size_t)ml * G * KC;
                 uint64_t *ym = yk + (size_t)ml * P * LN;
                 uint32_t p = h;
-                for (; p + H < P; p += 2 * H) tile(I1{}, I2{}, xk + p * KC, wk, ym + p * LN);
+                for (; p + H < P; p += 2 * H) tile(I1{}, I2{}, xk + p * KC, wk, ym + p * LN, 1);
                 if (p < P) row(xk + p * KC, wk, ym + p * LN);
             }
+        } else if (H % P == 0) {  // few rows per channel: row p = h mod P of channels h/P, h/P + H/P, ...
+            const uint32_t p = h % P, cs = H / P;
+            uint32_t ml = h / P;
+            for (; ml + cs < cnt; ml += 2 * cs)  // channel pairs (ml, ml + cs) share the input loads
+                tile(I2{}, I1{}, xk + p * KC, wst + (size_t)ml * G * KC, yk + ((size_t)ml * P + p) * LN, cs);
+            if (ml < cnt) row(xk + p * KC, wst + (size_t)ml * G * KC, yk + ((size_t)ml * P + p) * LN);
         } else {                 // few rows per channel: spread (channel, row) pairs over the groups
             const uint32_t jobs = cnt * P;
             uint32_t ml = h / P, p = h % P;
