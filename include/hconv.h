@@ -278,6 +278,17 @@ hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w, const uint
                               const uint64_t *d_share, const uint64_t *d_mask, uint64_t *d_ct_out,
                               uint64_t *d_c0_slots, void *cuda_stream);
 
+/* Checkpoint / resume of preprocessed weights (the paper's server keeps its
+ * NTT-preprocessed weights until the model changes, Sec. 8.1).  hc_weights_save
+ * writes w (any preprocessing mode) with its ring parameters and an integrity
+ * hash to the file `path` (synchronous).  hc_weights_load reads it back for a
+ * context with the same N, moduli and t and returns a handle that computes the
+ * same bits as the saved one.  Errors: HC_ERR_INVALID_ARG (bad handle or path,
+ * unreadable, truncated, corrupt or foreign file, other ring parameters),
+ * HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_weights_save(const hc_weights *w, const char *path);
+hc_status hc_weights_load(const hc_ctx *ctx, const char *path, hc_weights **out);
+
 /* --------------------------------------------------- generic ct x pt MAC --
  * The NTT-domain multiply-accumulate of Sec. 6.2 for arbitrary products:
  *   d_out[s] = sum_{j : h_slot[j] == s} INTT( NTT(d_ct[j]) . d_pt_ntt[j] )

@@ -92,6 +92,8 @@ _SIGS = {
     "hc_conv_geometry": (C.c_int, [_P] + [C.POINTER(C.c_uint32)] * 5),
     "hc_weights_data": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_size_t)]),
     "hc_weights_export": (C.c_int, [_P, _P, _P]),
+    "hc_weights_save": (C.c_int, [_P, C.c_char_p]),
+    "hc_weights_load": (C.c_int, [_P, C.c_char_p, C.POINTER(_P)]),
     "hc_conv_ct_pt": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_conv_ct_pt_plain": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_conv_ct_pt_host": (C.c_int, [_P, _P, _P, _P, _P]),
@@ -318,6 +320,22 @@ def hc_weights_data(w):
     p, n = C.c_void_p(), C.c_size_t()
     _check(lib().hc_weights_data(w.ptr, C.byref(p), C.byref(n)))
     return p.value, n.value
+
+
+def hc_weights_save(w, path):
+    _check(lib().hc_weights_save(w.ptr, str(path).encode()))
+
+
+def hc_weights_load(ctx, path, like_desc=None):
+    """Load saved weights for ctx; returns a Weights handle (its desc from the file's geometry)."""
+    out = C.c_void_p()
+    _check(lib().hc_weights_load(ctx.ptr, str(path).encode(), C.byref(out)))
+    i, o, cw, hw, ww = (C.c_uint32() for _ in range(5))
+    _check(lib().hc_conv_geometry(out, C.byref(i), C.byref(o), C.byref(cw), C.byref(hw), C.byref(ww)))
+    d = like_desc
+    res = hc_conv_desc(d.C, d.H, d.W, d.M, d.kh, d.kw, d.stride, d.pad, cw.value, hw.value, ww.value) \
+        if d is not None else hc_conv_desc(0, 0, 0, 0, 0, 0, 1, 0, cw.value, hw.value, ww.value)
+    return Weights(out, ctx, res, i.value, o.value)
 
 
 def hc_weights_export(w, dst, stream=None):
