@@ -38,7 +38,8 @@ static_assert(sizeof(LimbConst) == 128, "LimbConst is 128 bytes");
 // Kernel families whose launch shape is selectable per context.
 enum KernelKind {
     KK_FWD = 0, KK_INV = 1, KK_MAC = 2, KK_PROD = 3, KK_FWDCT = 4, KK_INVCT = 5, KK_MACB = 6,
-    KK_CONV = 7,  // convolution launch form: 0 three launches per degree, 1 and 2 one fused persistent launch
+    KK_CONV = 7,  // convolution launch form: 0 three launches per degree, 1 one fused persistent launch,
+                  // 2 three launches per limb, the limbs' chains on parallel streams
     KK_COUNT = 8
 };
 constexpr int kNumVariants = 3;
@@ -138,7 +139,9 @@ struct NttSeg {
     uint64_t *out;
     const LimbConst *limbs;
     uint32_t L, n_groups, cta_begin;
+    uint32_t Lc = 0, limb0 = 0;  // limbs [limb0, limb0 + Lc) only (Lc = 0: all L); L stays the layout stride
 };
+__host__ __device__ inline uint32_t seg_limbs(const NttSeg &s) { return s.Lc ? s.Lc : s.L; }
 constexpr int kMaxSegs = 48;
 template <int NS>
 struct NttSegsT {
@@ -154,7 +157,9 @@ struct MacSeg {
     uint64_t *Y;
     const LimbConst *limbs;
     uint32_t N, L, G, B, M, MB, MS, KC, chunks, groups, cta_begin;
+    uint32_t Lc = 0, limb0 = 0;  // limbs [limb0, limb0 + Lc) only (Lc = 0: all L); L stays the layout stride
 };
+__host__ __device__ inline uint32_t seg_limbs(const MacSeg &s) { return s.Lc ? s.Lc : s.L; }
 template <int NS>
 struct MacSegsT {
     uint32_t n;
@@ -167,6 +172,7 @@ struct MacLayer {
     const uint64_t *w;
     uint64_t *y;
     uint32_t G, B, M;
+    uint32_t Lc = 0, limb0 = 0;  // limbs [limb0, limb0 + Lc) only (Lc = 0: all)
 };
 bool mac_conv_fits(uint32_t G, uint32_t B);
 // MAC task geometry of one layer (channels per stage from the context's variant)

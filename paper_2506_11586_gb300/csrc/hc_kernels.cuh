@@ -159,7 +159,7 @@ k_ntt_fwd(const __grid_constant__ NttSegsT<NS> segs)
     extern __shared__ uint64_t sm[];
     const NttSeg &sg = find_seg(segs);
     const uint32_t local = blockIdx.x - sg.cta_begin;
-    const uint32_t limb = local / sg.n_groups, grp = local % sg.n_groups;
+    const uint32_t limb = sg.limb0 + local / sg.n_groups, grp = local % sg.n_groups;
     const size_t off = ((size_t)grp * Cfg::NP * sg.L + limb) * Cfg::N;
     fwd_task<Cfg>(sm, sg.in + off, sg.out + off, (size_t)sg.L * Cfg::N, sg.limbs[limb], threadIdx.x);
 }
@@ -171,7 +171,7 @@ k_ntt_inv(const __grid_constant__ NttSegsT<NS> segs)
     extern __shared__ uint64_t sm[];
     const NttSeg &sg = find_seg(segs);
     const uint32_t local = blockIdx.x - sg.cta_begin;
-    const uint32_t limb = local / sg.n_groups, grp = local % sg.n_groups;
+    const uint32_t limb = sg.limb0 + local / sg.n_groups, grp = local % sg.n_groups;
     const size_t off = ((size_t)grp * Cfg::NP * sg.L + limb) * Cfg::N;
     inv_task<Cfg>(sm, sg.in + off, sg.out + off, (size_t)sg.L * Cfg::N, sg.limbs[limb], threadIdx.x);
 }
@@ -286,7 +286,7 @@ k_ntt_inv_tma(const __grid_constant__ NttSegsT<NS> segs, uint32_t total, int *er
         si = 0;
         while (si + 1 < segs.n && u >= segs.s[si + 1].cta_begin) ++si;
         const uint32_t local = u - segs.s[si].cta_begin;
-        limb = local / segs.s[si].n_groups;
+        limb = segs.s[si].limb0 + local / segs.s[si].n_groups;
         poly = local % segs.s[si].n_groups;
     };
     auto issue = [&](uint32_t u, int b) {
@@ -472,7 +472,7 @@ template <class Cfg, int KIND, int NS>
 hc_status run_ntt_segs(const NttSegsT<NS> &segs, cudaStream_t s, bool inverse)
 {
     uint32_t items = 0;
-    for (uint32_t i = 0; i < segs.n; ++i) items = segs.s[i].cta_begin + segs.s[i].n_groups * segs.s[i].L;
+    for (uint32_t i = 0; i < segs.n; ++i) items = segs.s[i].cta_begin + segs.s[i].n_groups * seg_limbs(segs.s[i]);
     if (items == 0) return HC_OK;
     if (inverse) {
         auto kern = k_ntt_inv<Cfg, NS>;
@@ -496,7 +496,7 @@ template <class Cfg, int NS>
 hc_status run_ntt_inv_tma(const NttSegsT<NS> &segs, int *err, cudaStream_t s)
 {
     uint32_t total = 0;
-    for (uint32_t i = 0; i < segs.n; ++i) total = segs.s[i].cta_begin + segs.s[i].n_groups * segs.s[i].L;
+    for (uint32_t i = 0; i < segs.n; ++i) total = segs.s[i].cta_begin + segs.s[i].n_groups * seg_limbs(segs.s[i]);
     if (total == 0) return HC_OK;
     constexpr size_t smem = 2 * Cfg::SMEM_BYTES;
     auto kern = k_ntt_inv_tma<Cfg, NS>;
@@ -600,7 +600,7 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
             for (uint32_t i = 0; i < segs.n; ++i) {
                 segs.s[i].n_groups *= 2;  // polynomials
                 segs.s[i].cta_begin = begin;
-                begin += segs.s[i].n_groups * segs.s[i].L;
+                begin += segs.s[i].n_groups * seg_limbs(segs.s[i]);
             }
             return detail::run_ntt_inv_tma<TC>(segs, ctx->d_flag + 1, s);
         }
@@ -618,7 +618,7 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
         for (uint32_t i = 0; i < segs.n; ++i) {
             segs.s[i].n_groups *= 2 / Fused::NP;
             segs.s[i].cta_begin = begin;
-            begin += segs.s[i].n_groups * segs.s[i].L;
+            begin += segs.s[i].n_groups * seg_limbs(segs.s[i]);
         }
         return kind == KK_FWDCT_SEGS ? detail::run_ntt_segs<Fused, KK_FWDCT>(segs, s, false)
                                      : detail::run_ntt_segs<Fused, KK_INVCT>(segs, s, true);

@@ -72,8 +72,9 @@ k_mac_conv(const __grid_constant__ MacSegsT<NS> segs, int *err)
     const MacSeg &sg = segs.s[si];
     const uint32_t local = blockIdx.x - sg.cta_begin;
     const uint32_t chunk = local % sg.chunks, rest = local / sg.chunks;
-    const uint32_t limb = rest % sg.L;
-    const uint32_t m0 = (rest / sg.L) * sg.MB, m1 = min(sg.M, m0 + sg.MB);
+    const uint32_t lc = seg_limbs(sg);
+    const uint32_t limb = sg.limb0 + rest % lc;
+    const uint32_t m0 = (rest / lc) * sg.MB, m1 = min(sg.M, m0 + sg.MB);
     if (threadIdx.x == 0) {
         for (int i = 0; i < 1 + kMacStages; ++i) mbar_init(&bars[i], 1);
         mbar_fence_init();
@@ -148,7 +149,7 @@ static hc_status run_mac_segs_kc(MacSegsT<NS> &segs, size_t smem, int *err, cuda
     uint32_t begin = 0;
     for (uint32_t i = 0; i < segs.n; ++i) {
         segs.s[i].cta_begin = begin;
-        begin += segs.s[i].chunks * segs.s[i].L * segs.s[i].groups;
+        begin += segs.s[i].chunks * seg_limbs(segs.s[i]) * segs.s[i].groups;
     }
     if (begin == 0) return HC_OK;
     ProfileScope ps("k_mac_conv", s);
@@ -195,6 +196,8 @@ hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *laye
             const MacLayer &ly = layers[i];
             if (!mac_conv_fits(ly.G, ly.B)) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
             segs.s[segs.n] = make_mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M, kc);
+            segs.s[segs.n].Lc = ly.Lc;
+            segs.s[segs.n].limb0 = ly.limb0;
             const size_t sm = mac_seg_smem(segs.s[segs.n++]);
             if (sm > smem) smem = sm;
         }

@@ -135,8 +135,15 @@ uint32_t count_launches(const hc_plan *p)
                 if (!first) first = &c;
                 ++cnt;
             }
-        fused[d] = first && first->ctx->variant[KK_CONV] != 0 && cnt <= (uint32_t)kFusedMaxLayers && p->d_ctr;
+        fused[d] = first && first->ctx->variant[KK_CONV] == 1 && cnt <= (uint32_t)kFusedMaxLayers && p->d_ctr;
         if (fused[d]) ++n;
+        if (first && first->ctx->variant[KK_CONV] == 2 && !fused[d]) {
+            uint32_t maxl = 0;
+            for (const PlanConv &c : p->convs)
+                if (c.ctx->logN == (uint32_t)(12 + d) && c.blocked && c.ctx->L > maxl) maxl = c.ctx->L;
+            n += 3 * maxl * ((cnt + kMaxSegs - 1) / kMaxSegs);
+            fused[d] = true;  // counted here, not below
+        }
     }
     for (const PlanConv &c : p->convs) {
         if (c.blocked && fused[c.ctx->logN - 12]) continue;
@@ -278,6 +285,89 @@ hc_status time_batched(hc_plan *p, cudaStream_t s, int reps, float *ms)
 namespace hc {
 bool conv_job_blocked(const hc_ctx *c, const hc_weights *w) { return mac_conv_fits(w->G, w->B) && c->N % 64 == 0; }
 
+// per host thread and device: side streams and events for fork / join (made once, kept)
+struct SidePool {
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ev;  // [0]: fork, [1 + i]: join of side stream i
+};
+
+hc_status side_pool(uint32_t need, SidePool **out)
+{
+    static thread_local SidePool pools[32];
+    int dev = 0;
+    HC_CUDA_TRY(cudaGetDevice(&dev));
+    SidePool &p = pools[dev & 31];
+    if (p.ev.empty()) {
+        cudaEvent_t e = nullptr;
+        HC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p.ev.push_back(e);
+    }
+    while (p.st.size() < need) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t e = nullptr;
+        HC_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        p.st.push_back(st);
+        HC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p.ev.push_back(e);
+    }
+    *out = &p;
+    return HC_OK;
+}
+
+// Limbs are independent through all three phases, so the blocked jobs of one
+// degree split into one forward -> MAC -> inverse chain per limb; the chains run
+// on parallel streams (parallel branches under graph capture), and the tail
+// of one chain's kernel overlaps the next kernels of the others.
+hc_status launch_limb_chains(const ConvJob *jobs, size_t n, uint32_t logN, cudaStream_t s)
+{
+    uint32_t maxl = 0;
+    for (size_t i = 0; i < n; ++i)
+        if (jobs[i].ctx->logN == logN && jobs[i].blocked && jobs[i].ctx->L > maxl) maxl = jobs[i].ctx->L;
+    if (!maxl) return HC_OK;
+    SidePool *pool = nullptr;
+    hc_status st = side_pool(maxl - 1, &pool);
+    if (st != HC_OK) return st;
+    HC_CUDA_TRY(cudaEventRecord(pool->ev[0], s));
+    for (uint32_t l = 1; l < maxl; ++l) HC_CUDA_TRY(cudaStreamWaitEvent(pool->st[l - 1], pool->ev[0], 0));
+    for (uint32_t l = 0; l < maxl; ++l) {
+        cudaStream_t sl = l == 0 ? s : pool->st[l - 1];
+        for (size_t i0 = 0; i0 < n;) {  // at most kMaxSegs jobs per launch
+            NttSegs fwd{}, inv{};
+            std::vector<const hc_ctx *> mctx;
+            std::vector<MacLayer> layers;
+            const hc_ctx *first = nullptr;
+            size_t i = i0;
+            for (; i < n && fwd.n < (uint32_t)kMaxSegs; ++i) {
+                const ConvJob &c = jobs[i];
+                if (c.ctx->logN != logN || !c.blocked || c.ctx->L <= l) continue;
+                if (!first) first = c.ctx;
+                NttSeg f{c.in, c.ntt, c.ctx->d_limbs, c.ctx->L, c.w->I, 0};
+                f.Lc = 1;
+                f.limb0 = l;
+                fwd.s[fwd.n++] = f;
+                NttSeg v{c.out, c.out, c.ctx->d_limbs, c.ctx->L, c.w->O, 0};
+                v.Lc = 1;
+                v.limb0 = l;
+                inv.s[inv.n++] = v;
+                MacLayer ly{c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->desc.M};
+                ly.Lc = 1;
+                ly.limb0 = l;
+                mctx.push_back(c.ctx);
+                layers.push_back(ly);
+            }
+            i0 = i;
+            if (!first) continue;
+            st = launch_ntt_ct_segs(first, fwd, false, sl);
+            if (st == HC_OK) st = launch_mac_conv_layers(mctx.data(), layers.data(), layers.size(), sl);
+            if (st == HC_OK) st = launch_ntt_ct_segs(first, inv, true, sl);
+            if (st != HC_OK) return st;
+        }
+        if (l > 0) HC_CUDA_TRY(cudaEventRecord(pool->ev[l], sl));
+    }
+    for (uint32_t l = 1; l < maxl; ++l) HC_CUDA_TRY(cudaStreamWaitEvent(s, pool->ev[l], 0));
+    return HC_OK;
+}
+
 size_t conv_jobs_counter_words(const ConvJob *jobs, size_t n)
 {
     size_t w = 0;
@@ -301,14 +391,21 @@ hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s, uint32
                 if (!first) first = &jobs[i];
                 ++count;
             }
-        if (!first || first->ctx->variant[KK_CONV] == 0 || count > (size_t)kFusedMaxLayers || !ctr) continue;
+        if (!first) continue;
+        if (first->ctx->variant[KK_CONV] == 2) {
+            hc_status st = launch_limb_chains(jobs, n, logN, s);
+            if (st != HC_OK) return st;
+            fused[logN - 12] = true;
+            continue;
+        }
+        if (first->ctx->variant[KK_CONV] != 1 || count > (size_t)kFusedMaxLayers || !ctr) continue;
         const size_t words = fused_counter_words(jobs, n, logN);
         if (words > ctr_words) continue;
         hc_status st = launch_conv_fused(jobs, n, logN, ctr, s);
         if (st != HC_OK) return st;
         fused[logN - 12] = true;
     }
-    if (n == 1 && !fused[jobs[0].ctx->logN - 12]) {
+    if (n == 1 && !fused[jobs[0].ctx->logN - 12] && jobs[0].ctx->variant[KK_CONV] != 2) {
         // one layer: the single-segment launchers (small parameter blocks, no host tables)
         const ConvJob &c = jobs[0];
         hc_status st = launch_ntt_fwd_ct(c.ctx, c.in, c.ntt, c.w->I, s);

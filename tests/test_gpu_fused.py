@@ -1,10 +1,11 @@
-"""GPU parity of the fused persistent convolution launch (Sec. 6.2: NTT of the
-inputs, NTT-domain MAC and INTT of the outputs in one launch whose CTAs take
-tasks in order and wait on per-limb completion counters).  Every output must
-equal, bit for bit, the three-launch form and the oracle's schoolbook
-convolution, for single layers of every degree, many layers of one degree
-in one launch, and mixed degrees; repeated runs (counters reset) and graph
-replays too."""
+"""GPU parity of the alternative launch forms of the convolution (Sec. 6.2:
+NTT of the inputs, NTT-domain MAC, INTT of the outputs): form 1, one fused
+persistent launch whose CTAs take tasks in order and wait on per-limb
+completion counters; form 2, one forward -> MAC -> inverse chain per limb on
+parallel streams.  Every output must equal, bit for bit, the three-launch
+form (0) and the oracle's schoolbook convolution, for single layers of every
+degree, many layers of one degree, and mixed degrees; repeated runs (counters
+reset) and graph replays too."""
 import numpy as np
 import pytest
 
@@ -57,13 +58,14 @@ def _form(L, ctxs, v):
         L.hc_ctx_set_variant(c, L.KIND_CONV_FORM, v)
 
 
-def test_fused_single_layers_match_three_launch_form_and_oracle(L, ctxs):
+@pytest.mark.parametrize("form", [1, 2])
+def test_fused_single_layers_match_three_launch_form_and_oracle(L, ctxs, form):
     for i, sh in enumerate(LAYERS):
         it = _item(L, ctxs, sh, 900 + i)
         _form(L, ctxs, 0)
         ref = torch.empty_like(it["d_out"])
         L.hc_conv_ct_pt(it["ctx"], it["w"], it["d_in"], ref)
-        _form(L, ctxs, 1)
+        _form(L, ctxs, form)
         for _ in range(2):                         # counters are reset by every launch
             it["d_out"].fill_(-1)
             L.hc_conv_ct_pt(it["ctx"], it["w"], it["d_in"], it["d_out"])
@@ -79,7 +81,8 @@ def test_fused_single_layers_match_three_launch_form_and_oracle(L, ctxs):
     _form(L, ctxs, 0)
 
 
-def test_fused_plan_many_layers_and_degrees(L, ctxs):
+@pytest.mark.parametrize("form", [1, 2])
+def test_fused_plan_many_layers_and_degrees(L, ctxs, form):
     items = [_item(L, ctxs, sh, 950 + i) for i, sh in enumerate(LAYERS + LAYERS[1:4])]
     _form(L, ctxs, 0)
     refs = []
@@ -87,9 +90,10 @@ def test_fused_plan_many_layers_and_degrees(L, ctxs):
         r = torch.empty_like(it["d_out"])
         L.hc_conv_ct_pt(it["ctx"], it["w"], it["d_in"], r)
         refs.append(r)
-    _form(L, ctxs, 1)
+    _form(L, ctxs, form)
     plan = L.hc_plan_create([L.work_conv(it["ctx"], it["w"], it["d_in"], it["d_out"]) for it in items])
-    assert L.hc_plan_info(plan)[2] == 3            # one fused launch per ring degree
+    # form 1: one fused launch per ring degree; form 2: three launches per limb and degree
+    assert L.hc_plan_info(plan)[2] == (3 if form == 1 else 3 * (2 + 3 + 4))
     for rnd in range(4):                           # direct, capture, replays
         for it in items:
             it["d_out"].fill_(-1)
