@@ -6,4 +6,6 @@ NTT-domain ciphertext x plaintext multiply-accumulate of its linear layers
   build    -- compiles csrc/*.cu into _build/libhconv.so with nvcc
   _lib     -- ctypes binding with the C entry points' names
   inputs   -- seeded synthetic workloads (random numbers and shapes only)
+  serving  -- Poisson-arrival driver of the library's request loop
+  replicas -- one-process-per-GPU replica plumbing (barrier, max-over-ranks)
 """
