@@ -14,6 +14,9 @@ Contents
   conv   -- Cheetah coefficient packing of a stride-1 convolution, canonical
             partition, plaintext convolution mod t, and the ct x pt conv
             computed by schoolbook products (Sec. 6.1, 6.2).
+  layers -- strided convolutions as stride-1 layers of the phase-split input
+            (polyphase reading) and fully connected layers by matrix-vector
+            packing, with their server steps (Sec. 6.1, Sec. 8.1 networks).
   bfv    -- BFV secret-key encryption / decryption (App. C), client-side
             test harness only (Sec. 6.3: the server never holds the key).
 
