@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--conv-form", type=int, default=None, choices=[0, 1, 2],
                     help="force the layer's launch form instead of the autotuned one")
     ap.add_argument("--batched-reps", type=int, default=20)
+    ap.add_argument("--no-networks", action="store_true",
+                    help="skip the whole-network plans (SqueezeNet-1.1 and ResNet-50, every linear layer)")
     ap.add_argument("--no-batched-plain", action="store_true", help="skip the one-launch-per-product comparisons")
     ap.add_argument("--serving-requests", type=int, default=6000)
     ap.add_argument("--serving-rate", type=float, default=200.0)
@@ -360,6 +362,78 @@ def batched_squeezenet(L, stream, reps=20, with_plain=True):
     return out
 
 
+def whole_networks(L, stream, reps=10):
+    """Every linear layer of SqueezeNet-1.1 (26: conv1 stride 2 and the 25 stride-1
+    layers; N = 8192, L = 3) and of ResNet-50 (54: 46 stride-1 and 7 strided
+    convolutions and the fully connected classifier; N = 16384, L = 4), each
+    network one plan replayed from a CUDA graph, vs one call per layer."""
+    import numpy as np
+    import torch
+    from paper_2506_11586_gb300.inputs import (CANONICAL_PRIMES, RESNET50_FC, RESNET50_STRIDED, SQUEEZENET_1_1,
+                                               SQUEEZENET_CONV1, T_PLAIN, Stream, conv_tensors, resnet50_instances,
+                                               uniform_residues)
+    nets = {
+        "squeezenet1.1_all26_N8192_L3": ([SQUEEZENET_CONV1] + list(SQUEEZENET_1_1), 8192, 3),
+        "resnet50_all54_N16384_L4": ([sh for sh, _ in resnet50_instances()] + list(RESNET50_STRIDED)
+                                     + [RESNET50_FC], 16384, 4),
+    }
+    out = {}
+    for seed, (name, (shapes, N, nl)) in enumerate(nets.items()):
+        ctx = L.hc_ctx_create(N, CANONICAL_PRIMES[:nl], T_PLAIN)
+        torch.cuda.synchronize()
+        t_pre = time.perf_counter()
+        ws, kinds = [], {"stride1": 0, "strided": 0, "fc": 0}
+        for i, sh in enumerate(shapes):
+            if isinstance(sh, tuple):                         # fully connected (C, M)
+                Wm = Stream(4 + seed, 300 + i).int8(sh[0] * sh[1]).reshape(sh[1], sh[0])
+                w = L.hc_weights_preprocess_fc(ctx, L.make_fc_desc(sh[0], sh[1]), Wm)
+                kinds["fc"] += w.products
+            else:
+                K = conv_tensors(sh, seed=4 + seed + 1000 * i)[1]
+                st = getattr(sh, "stride", 1)
+                w = L.hc_weights_preprocess(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad,
+                                                             stride=st), K)
+                kinds["strided" if st > 1 else "stride1"] += w.products
+            ws.append(w)
+        torch.cuda.synchronize()
+        offline_s = time.perf_counter() - t_pre
+        items = []
+        for i, w in enumerate(ws):
+            ct = uniform_residues(Stream(4 + seed, 100 + i), CANONICAL_PRIMES[:nl], (w.I, 2), N)
+            items.append((w, torch.from_numpy(ct.view(np.int64)).cuda(),
+                          torch.empty(w.O * 2 * nl * N, dtype=torch.int64, device="cuda")))
+        plan = L.hc_plan_create([L.work_conv(ctx, w, a, b) for w, a, b in items])
+        products, nbytes, launches = L.hc_plan_info(plan)
+        L.hc_plan_autotune(plan, TUNE_CACHE, stream)
+        for _ in range(3):
+            L.hc_plan_run(plan, stream)
+        g = _events_ms(lambda: L.hc_plan_run(plan, stream), reps, stream)
+        batched = [b.clone() for _, _, b in items]
+
+        def per_layer():
+            for w, a, b in items:
+                L.hc_conv_ct_pt(ctx, w, a, b, stream)
+        per_layer()
+        pl = _events_ms(per_layer, max(3, reps // 2), stream)
+        exact = all(bool(torch.equal(x, b)) for x, (_, _, b) in zip(batched, items))
+        kern = _kernel_trace(L, lambda: L.hc_plan_run(plan, stream), name)
+        ms = statistics.median(g)
+        out[name] = {"layers": len(shapes), "products": products, "products_by_kind": kinds, "alg_bytes": nbytes,
+                     "resident_weight_bytes": sum(L.hc_weights_data(w)[1] * nl * N * 8 for w in ws),
+                     "launches_per_pass": launches, "batched_ms": ms, "batched_p99_ms": max(g),
+                     "value": products / (ms / 1e3), "unit": UNIT, "alg_gbs": nbytes / (ms / 1e3) / 1e9,
+                     "per_layer_ms": statistics.median(pl), "speedup_vs_per_layer": statistics.median(pl) / ms,
+                     "bit_exact_vs_per_layer": exact, "offline_weight_ntt_s": offline_s, "kernels": kern,
+                     "variants": {k: L.hc_ctx_get_variant(ctx, v) for k, v in KIND_NAMES.items()}}
+        plan.close()
+        del items, batched
+        for w in ws:
+            w.close()
+        ctx.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def batched_uneven(L, stream, reps=20, with_plain=True):
     """2000 standalone products of mixed degree in one persistent launch vs per-degree vs plain."""
     import numpy as np
@@ -613,6 +687,9 @@ def run_gb300(args):
         wp = not args.no_batched_plain
         batched = {"squeezenet": batched_squeezenet(L, stream, args.batched_reps, wp),
                    "uneven": batched_uneven(L, stream, args.batched_reps, wp)}
+    networks = None
+    if rank == 0 and not args.no_networks:
+        networks = whole_networks(L, stream, max(5, args.batched_reps // 2))
     if rank == 0 and args.serving_requests > 0:
         from paper_2506_11586_gb300 import serving as srv_mod
         layers = srv_mod.ServingLayers()
@@ -632,8 +709,8 @@ def run_gb300(args):
                    "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps"},
         "p50_ms": statistics.median(step_ms), "p99_ms": p99, "layer_gbs": layer_gbs,
         "roofline": roofline, "graph": graph, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
-        "server_step": step_full, "preprocessing_modes": modes, "batched": batched, "serving": serving,
-        "gpu_launches": launches, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+        "server_step": step_full, "preprocessing_modes": modes, "batched": batched, "networks": networks,
+        "serving": serving, "gpu_launches": launches, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
         "launch_form": form,
         "offline_weights_s": offline_s, "launch_variants": tuned, "clocks": clocks, "device": torch.cuda.get_device_name(local),
     }

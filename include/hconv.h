@@ -53,7 +53,7 @@ typedef enum {
     HC_ERR_BUDGET = 5,       /* admission: request exceeds the memory budget */
     HC_ERR_TIMEOUT = 6,      /* a bounded device-side wait expired */
     HC_ERR_CUDA = 7,         /* a CUDA runtime call failed (see hc_last_error) */
-    HC_ERR_UNSUPPORTED = 8   /* valid but not supported here (e.g. stride != 1) */
+    HC_ERR_UNSUPPORTED = 8   /* valid but not supported for these arguments (e.g. a plan with online weights) */
 } hc_status;
 
 /* Context flags. */
@@ -147,22 +147,62 @@ hc_status hc_ntt_inv(const hc_ctx *ctx, uint64_t *d_polys, size_t n_polys, void 
  * one minimising 2I + P + 2O polynomials moved (I = G*B inputs, P = M*G
  * weights, O = M*B outputs), ties to larger Hw*Ww, then larger Cw, then
  * larger Ww, over Cw <= C, kh <= Hw <= H+2pad, kw <= Ww <= W+2pad,
- * Cw*Hw*Ww <= N. */
+ * Cw*Hw*Ww <= N.
+ *
+ * Strided layers (the stride-2 convolutions of SqueezeNet-1.1 and ResNet-50,
+ * Sec. 8.1).  A stride-s convolution with padding p is computed as the
+ * stride-1 convolution without padding of the phase-split input
+ *   x'[(a*pb + b)*C + c][i][j] = x_pad[c][s*i + a][s*j + b]   (0 past x_pad)
+ * with kernel K'[m][(a*pb + b)*C + c][u][v] = K[m][c][s*u + a][s*v + b]
+ * (0 past kh, kw), for phases a < pa = min(s, kh), b < pb = min(s, kw):
+ * C' = pa*pb*C channels, kernel kh' = ceil(kh/s) x kw' = ceil(kw/s), input
+ * H' = Ho + kh' - 1 by W' = Wo + kw' - 1 where Ho = (H + 2p - kh)/s + 1,
+ * Wo = (W + 2p - kw)/s + 1 are the strided output sizes.  The library
+ * splits K itself; the client packs x' (not x) with the stride-1 packing
+ * above, using the descriptor hc_conv_partition returns.  Outputs are the
+ * strided layer's Ho x Wo map.  An explicit Cw/Hw/Ww in a strided
+ * descriptor is a partition of that stride-1 layer. */
 typedef struct {
     uint32_t C, H, W;       /* input channels, height, width */
     uint32_t M;             /* output channels */
     uint32_t kh, kw;        /* kernel height, width */
-    uint32_t stride, pad;   /* stride must be 1 */
+    uint32_t stride, pad;   /* stride >= 1, zero padding on every side */
     uint32_t Cw, Hw, Ww;    /* 0,0,0 = canonical partition */
 } hc_conv_desc;
 
 /* Host-only: resolve the partition of `desc` for ring degree N.  *resolved
- * gets desc with Cw/Hw/Ww filled in; counts may be NULL.
- * Errors: HC_ERR_INVALID_ARG (null desc/resolved, zero dims, kernel larger
- * than the padded input, a given partition with Cw*Hw*Ww > N),
- * HC_ERR_UNSUPPORTED (stride != 1). */
+ * gets the stride-1 layer computed, with Cw/Hw/Ww filled in: desc itself for
+ * stride 1, the phase-split layer above (stride 1, pad 0) otherwise; counts
+ * may be NULL.  Errors: HC_ERR_INVALID_ARG (null desc/resolved, zero dims,
+ * stride 0, kernel larger than the padded input, a given partition with
+ * Cw*Hw*Ww > N). */
 hc_status hc_conv_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *resolved,
                             uint32_t *n_in_ct, uint32_t *n_pt, uint32_t *n_out_ct);
+
+/* Fully connected layers (ResNet-50's classifier, Sec. 8.1): y = W x with W
+ * int8 [M][C], by matrix-vector coefficient packing.  With Cw inputs per input
+ * polynomial and No output rows per output polynomial (No*Cw <= N):
+ *   input ct  g = 0..G-1      : coeff [c] = x[g*Cw + c]            (G = ceil(C/Cw))
+ *   weight pt p = m'*G + g    : coeff [r*Cw + Cw-1 - c] = W[m'*No + r][g*Cw + c]
+ *   output ct m' = 0..Mp-1    : coeff [r*Cw + Cw-1] encrypts y[m'*No + r]   (Mp = ceil(M/No))
+ * A product term lands at r*Cw + Cw-1 + (c_in - c) with |c_in - c| < Cw, so
+ * rows never mix and no wrapped term reaches an output coefficient.  The
+ * layer is the 1x1 convolution on a 1x1 image with partition (Cw, 1, 1) and
+ * No output channels sharing an output ciphertext: every call that takes
+ * weights takes FC weights too (I = G inputs, O = Mp outputs, [..][2][L][N]).
+ * Cw = No = 0 selects the canonical partition: minimal 2I + P + 2O, then
+ * fewer P, then larger Cw, then smaller No. */
+typedef struct {
+    uint32_t C, M;          /* inputs, outputs */
+    uint32_t Cw, No;        /* 0,0 = canonical partition */
+} hc_fc_desc;
+
+/* Host-only: resolve the partition of a fully connected layer for ring
+ * degree N (counts may be NULL).  Errors: HC_ERR_INVALID_ARG (null desc or
+ * resolved, zero dims, a given partition with Cw > C, No > M or
+ * Cw*No > N). */
+hc_status hc_fc_partition(const hc_fc_desc *desc, uint32_t N, hc_fc_desc *resolved,
+                          uint32_t *n_in_ct, uint32_t *n_pt, uint32_t *n_out_ct);
 
 /* Offline weight preprocessing (Sec. 6.2, Sec. 8.1): pack h_K (host int8,
  * [M][C][kh][kw], copied) into P = M*G plaintext polynomials, lift to every
@@ -170,7 +210,7 @@ hc_status hc_conv_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *
  * (*out).  Enqueued on cuda_stream; the handle is usable by later calls on
  * any stream once that work completes (the call synchronises the stream
  * before returning, so it is immediately usable).
- * Errors: HC_ERR_INVALID_ARG, HC_ERR_UNSUPPORTED, HC_ERR_OOM, HC_ERR_CUDA. */
+ * Errors: HC_ERR_INVALID_ARG, HC_ERR_OOM, HC_ERR_CUDA. */
 hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K,
                                 hc_weights **out, void *cuda_stream);
 
@@ -194,6 +234,21 @@ typedef enum {
 } hc_weights_mode;
 hc_status hc_weights_preprocess_ex(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K,
                                    uint32_t mode, hc_weights **out, void *cuda_stream);
+
+/* Preprocessed weights of a fully connected layer: h_W host int8 [M][C]
+ * (copied), mode as in hc_weights_preprocess_ex.  Errors: as
+ * hc_weights_preprocess_ex. */
+hc_status hc_weights_preprocess_fc(const hc_ctx *ctx, const hc_fc_desc *desc, const int8_t *h_W,
+                                   uint32_t mode, hc_weights **out, void *cuda_stream);
+
+/* Layout of preprocessed weights: *computed = the stride-1 layer computed
+ * (with its partition; for FC weights the 1x1 convolution {C,1,1,M,1,1,1,0,
+ * Cw,1,1}), *kind = 0 convolution / 1 fully connected, *No = output channels
+ * per output ciphertext (1 for convolutions), *n_slots = output slots per
+ * output ciphertext and limb of hc_conv_server_step,
+ * No*(Hw-kh+1)*(Ww-kw+1) of *computed.  Any output pointer may be NULL. */
+hc_status hc_weights_layout(const hc_weights *w, hc_conv_desc *computed, uint32_t *kind,
+                            uint32_t *No, uint32_t *n_slots);
 
 /* Geometry of preprocessed weights.  Any output pointer may be NULL. */
 hc_status hc_conv_geometry(const hc_weights *w, uint32_t *n_in_ct, uint32_t *n_out_ct,
@@ -262,16 +317,21 @@ hc_status hc_conv_ct_pt_noalloc(const hc_ctx *ctx, const hc_weights *w, const ui
  * Delta = floor(Q/t) (Q the product of the context's moduli, t its plaintext
  * modulus):
  *   1. c0 += Delta * pack(d_share), packed like the input ciphertexts
- *      (d_share: device [C][H][W] residues in [0, t), or NULL to skip);
+ *      (d_share: device [C][H][W] residues in [0, t) of the caller's layer --
+ *      the library applies a strided layer's phase split itself; [C] for a
+ *      fully connected layer -- or NULL to skip);
  *   2. d_ct_out = hc_conv_ct_pt of the result (full [O][2][L][N]; its c1
  *      components are what the client needs beside the slots);
- *   3. d_c0_slots[o][l][s] = c0[offset + i*Ww + j] - Delta * r[m][i0+i][j0+j]
- *      mod q_l for output ct o = m*B + b and slot s = i*(Ww-kw+1) + j, with
- *      r = d_mask (device [M][Ho][Wo] in [0, t), or NULL for r = 0), and 0 for
- *      slots of edge blocks outside the Ho x Wo output map.  S slots per
- *      ciphertext and limb, S = (Hw-kh+1)*(Ww-kw+1) of the resolved partition.
+ *   3. d_c0_slots[o][l][s] = c0[k] - Delta * r[m][row][col] mod q_l, where,
+ *      with the stride-1 layer computed (hc_weights_layout) and oh = Hw-kh+1,
+ *      ow = Ww-kw+1: output ct o = m'*B + b, slot s = (n*oh + i)*ow + j,
+ *      k = n*Cw*Hw*Ww + offset + i*Ww + j, m = m'*No + n, (row, col) =
+ *      (i0+i, j0+j); r = d_mask (device [M][Ho][Wo] in [0, t) -- [M] for a
+ *      fully connected layer -- or NULL for r = 0); 0 for slots outside the
+ *      Ho x Wo output map or with m >= M.  S = No*oh*ow slots per ciphertext
+ *      and limb (convolutions: No = 1; FC: oh = ow = 1, slot n holds y[m'*No+n]).
  * The client decrypts slot s of output o from (d_c0_slots, c1 of d_ct_out) as
- * conv(x_c + x_s) - r mod t.  Share and mask values must lie in [0, t).
+ * layer(x_c + x_s) - r mod t.  Share and mask values must lie in [0, t).
  * Device scratch of (2I)*2*L*N*8 bytes plus small counters comes from the
  * allocator.  Errors: as hc_conv_ct_pt. */
 hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in,

@@ -47,6 +47,10 @@ class hc_conv_desc(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in ("C", "H", "W", "M", "kh", "kw", "stride", "pad", "Cw", "Hw", "Ww")]
 
 
+class hc_fc_desc(C.Structure):
+    _fields_ = [(n, C.c_uint32) for n in ("C", "M", "Cw", "No")]
+
+
 class hc_work_item(C.Structure):
     _fields_ = [("kind", C.c_uint32), ("ctx", C.c_void_p), ("weights", C.c_void_p), ("d_ct_in", C.c_void_p),
                 ("d_pt_ntt", C.c_void_p), ("d_ct_out", C.c_void_p), ("n", C.c_size_t)]
@@ -89,6 +93,11 @@ _SIGS = {
                                     C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "hc_weights_preprocess": (C.c_int, [_P, C.POINTER(hc_conv_desc), _P, C.POINTER(_P), _P]),
     "hc_weights_preprocess_ex": (C.c_int, [_P, C.POINTER(hc_conv_desc), _P, C.c_uint32, C.POINTER(_P), _P]),
+    "hc_fc_partition": (C.c_int, [C.POINTER(hc_fc_desc), C.c_uint32, C.POINTER(hc_fc_desc),
+                                  C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+    "hc_weights_preprocess_fc": (C.c_int, [_P, C.POINTER(hc_fc_desc), _P, C.c_uint32, C.POINTER(_P), _P]),
+    "hc_weights_layout": (C.c_int, [_P, C.POINTER(hc_conv_desc), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                    C.POINTER(C.c_uint32)]),
     "hc_conv_geometry": (C.c_int, [_P] + [C.POINTER(C.c_uint32)] * 5),
     "hc_weights_data": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_size_t)]),
     "hc_weights_export": (C.c_int, [_P, _P, _P]),
@@ -202,9 +211,19 @@ class Ctx(_Handle):
 
 
 class Weights(_Handle):
+    """Preprocessed weights.  desc: the caller's layer with its partition;
+    computed: the stride-1 layer the library computes (hc_weights_layout);
+    kind 0 convolution / 1 fully connected; No output channels per output
+    ciphertext; n_slots server-step slots per output ciphertext and limb;
+    products: ct x pt products of one call."""
+
     def __init__(self, ptr, ctx, resolved, I, O):
         super().__init__(ptr, keep=ctx)
         self.ctx, self.desc, self.I, self.O = ctx, resolved, I, O
+        comp, kind, no, slots = hc_conv_desc(), C.c_uint32(), C.c_uint32(), C.c_uint32()
+        _check(lib().hc_weights_layout(self.ptr, C.byref(comp), C.byref(kind), C.byref(no), C.byref(slots)))
+        self.computed, self.kind, self.No, self.n_slots = comp, kind.value, no.value, slots.value
+        self.products = -(-comp.M // self.No) * I
 
 
 # ---------------------------------------------------------------- context ---
@@ -309,6 +328,32 @@ def hc_weights_preprocess_ex(ctx, desc, K, mode, stream=None):
     return Weights(out, ctx, res, i.value, o.value)
 
 
+def make_fc_desc(C_, M, Cw=0, No=0):
+    return hc_fc_desc(C_, M, Cw, No)
+
+
+def hc_fc_partition(desc, N):
+    """Host-only: (resolved fc desc, n_in_ct, n_pt, n_out_ct)."""
+    res = hc_fc_desc()
+    i, p, o = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    _check(lib().hc_fc_partition(C.byref(desc), N, C.byref(res), C.byref(i), C.byref(p), C.byref(o)))
+    return res, i.value, p.value, o.value
+
+
+def hc_weights_preprocess_fc(ctx, desc, Wm, mode=HC_WEIGHTS_NTT_OFFLINE, stream=None):
+    """Fully connected layer y = Wm x, Wm int8 [M][C]; the handle's desc is its 1x1 convolution form."""
+    Wm = np.ascontiguousarray(Wm, dtype=np.int8)
+    if Wm.size != desc.M * desc.C:
+        raise ValueError("Wm must have M*C entries")
+    out = C.c_void_p()
+    _check(lib().hc_weights_preprocess_fc(ctx.ptr, C.byref(desc), C.c_void_p(Wm.ctypes.data), mode, C.byref(out),
+                                          _stream(stream)))
+    i, o, cw, hw, ww = (C.c_uint32() for _ in range(5))
+    _check(lib().hc_conv_geometry(out, C.byref(i), C.byref(o), C.byref(cw), C.byref(hw), C.byref(ww)))
+    res = hc_conv_desc(desc.C, 1, 1, desc.M, 1, 1, 1, 0, cw.value, 1, 1)
+    return Weights(out, ctx, res, i.value, o.value)
+
+
 def hc_conv_geometry(w):
     i, o, cw, hw, ww = (C.c_uint32() for _ in range(5))
     _check(lib().hc_conv_geometry(w.ptr, C.byref(i), C.byref(o), C.byref(cw), C.byref(hw), C.byref(ww)))
@@ -333,8 +378,11 @@ def hc_weights_load(ctx, path, like_desc=None):
     i, o, cw, hw, ww = (C.c_uint32() for _ in range(5))
     _check(lib().hc_conv_geometry(out, C.byref(i), C.byref(o), C.byref(cw), C.byref(hw), C.byref(ww)))
     d = like_desc
-    res = hc_conv_desc(d.C, d.H, d.W, d.M, d.kh, d.kw, d.stride, d.pad, cw.value, hw.value, ww.value) \
-        if d is not None else hc_conv_desc(0, 0, 0, 0, 0, 0, 1, 0, cw.value, hw.value, ww.value)
+    if d is None:
+        comp = hc_conv_desc()
+        _check(lib().hc_weights_layout(out, C.byref(comp), None, None, None))
+        d = comp
+    res = hc_conv_desc(d.C, d.H, d.W, d.M, d.kh, d.kw, d.stride, d.pad, cw.value, hw.value, ww.value)
     return Weights(out, ctx, res, i.value, o.value)
 
 
@@ -363,9 +411,9 @@ def hc_conv_ct_pt_host(ctx, w, h_in, h_out, stream=None):
 
 
 def slot_count(w):
-    """Output slots per output ciphertext and limb of a layer: (Hw-kh+1)*(Ww-kw+1)."""
-    d = w.desc
-    return (d.Hw - d.kh + 1) * (d.Ww - d.kw + 1)
+    """Output slots per output ciphertext and limb of hc_conv_server_step: No*(Hw-kh+1)*(Ww-kw+1)
+    of the stride-1 layer computed."""
+    return w.n_slots
 
 
 def hc_conv_server_step(ctx, w, ct_in, share, mask, ct_out, c0_slots, stream=None):

@@ -29,11 +29,12 @@ uint32_t log2_exact(uint32_t n)
 
 // ---- partition of a stride-1 convolution --------------------------------------
 struct Geom {
-    uint32_t Cw, Hw, Ww, G, Bh, Bw, B, I, P, O;
+    uint32_t Cw, Hw, Ww, G, Bh, Bw, B, Mp, I, P, O;
     uint64_t cost;
 };
 
-Geom geom_of(const hc_conv_desc &d, uint32_t Cw, uint32_t Hw, uint32_t Ww)
+// No output channels share one output polynomial (1 for convolutions)
+Geom geom_of(const hc_conv_desc &d, uint32_t Cw, uint32_t Hw, uint32_t Ww, uint32_t No = 1)
 {
     Geom g{};
     g.Cw = Cw;
@@ -45,22 +46,81 @@ Geom geom_of(const hc_conv_desc &d, uint32_t Cw, uint32_t Hw, uint32_t Ww)
     g.Bh = (Ho + oh - 1) / oh;
     g.Bw = (Wo + ow - 1) / ow;
     g.B = g.Bh * g.Bw;
+    g.Mp = (d.M + No - 1) / No;
     g.I = g.G * g.B;
-    g.P = d.M * g.G;
-    g.O = d.M * g.B;
+    g.P = g.Mp * g.G;
+    g.O = g.Mp * g.B;
     g.cost = 2ull * g.I + g.P + 2ull * g.O;
     return g;
 }
 
-hc_status resolve_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *res, Geom *geo)
+// Phases of a strided convolution.  A stride-s convolution with zero padding p,
+// y[m][r][c] = sum x~[ch][s*r+l][s*c+l'] K[m][ch][l][l'] (x~ the padded input),
+// equals the stride-1 convolution without padding of the phase-split input
+//   x'[(a*pb + b)*C + ch][i][j] = x~[ch][s*i + a][s*j + b]     (0 past x~'s edge)
+// with the phase-split kernel
+//   K'[m][(a*pb + b)*C + ch][u][v] = K[m][ch][s*u + a][s*v + b]  (0 past kh, kw),
+// phases a < pa = min(s, kh), b < pb = min(s, kw), kernel ceil(kh/s) x ceil(kw/s)
+// and x' of (Ho + kh' - 1) x (Wo + kw' - 1) for the strided output Ho x Wo
+// (l = s*u + a gives s*r + l = s*(r + u) + a).  Phases a >= kh meet no weight
+// and are left out.
+struct Phases {
+    uint32_t s, pa, pb;
+};
+
+hc_status effective_desc(const hc_conv_desc &d, hc_conv_desc *eff, Phases *ph)
 {
-    if (!desc || !res) return set_error(HC_ERR_INVALID_ARG, "null descriptor");
-    const hc_conv_desc d = *desc;
-    if (d.stride != 1) return set_error(HC_ERR_UNSUPPORTED, "only stride 1 is supported (got %u)", d.stride);
     if (!d.C || !d.H || !d.W || !d.M || !d.kh || !d.kw)
         return set_error(HC_ERR_INVALID_ARG, "zero dimension in convolution descriptor");
-    const uint32_t Hp = d.H + 2 * d.pad, Wp = d.W + 2 * d.pad;
+    if (!d.stride) return set_error(HC_ERR_INVALID_ARG, "stride 0");
+    const uint64_t Hp = (uint64_t)d.H + 2ull * d.pad, Wp = (uint64_t)d.W + 2ull * d.pad;
+    if (Hp > 0xffffffffu || Wp > 0xffffffffu) return set_error(HC_ERR_INVALID_ARG, "padded input too large");
     if (d.kh > Hp || d.kw > Wp) return set_error(HC_ERR_INVALID_ARG, "kernel larger than padded input");
+    *eff = d;
+    *ph = Phases{1, 1, 1};
+    if (d.stride == 1) return HC_OK;
+    const uint32_t s = d.stride;
+    const uint32_t Ho = (uint32_t)((Hp - d.kh) / s + 1), Wo = (uint32_t)((Wp - d.kw) / s + 1);
+    const uint32_t kh1 = (d.kh + s - 1) / s, kw1 = (d.kw + s - 1) / s;
+    ph->s = s;
+    ph->pa = std::min(s, d.kh);
+    ph->pb = std::min(s, d.kw);
+    const uint64_t C1 = (uint64_t)ph->pa * ph->pb * d.C;
+    if (C1 > 0xffffffffu) return set_error(HC_ERR_INVALID_ARG, "too many phase-split channels");
+    eff->C = (uint32_t)C1;
+    eff->H = Ho + kh1 - 1;
+    eff->W = Wo + kw1 - 1;
+    eff->kh = kh1;
+    eff->kw = kw1;
+    eff->stride = 1;
+    eff->pad = 0;
+    return HC_OK;
+}
+
+// K (int8 [M][C][kh][kw]) -> K' ([M][pa*pb*C][kh'][kw']) as above
+void polyphase_kernel(const hc_conv_desc &d, const hc_conv_desc &eff, const Phases &ph, const int8_t *K,
+                      std::vector<int8_t> &out)
+{
+    out.assign((size_t)eff.M * eff.C * eff.kh * eff.kw, 0);
+    for (uint32_t m = 0; m < d.M; ++m)
+        for (uint32_t a = 0; a < ph.pa; ++a)
+            for (uint32_t b = 0; b < ph.pb; ++b)
+                for (uint32_t ch = 0; ch < d.C; ++ch) {
+                    const uint32_t c1 = (a * ph.pb + b) * d.C + ch;
+                    for (uint32_t u = 0; u < eff.kh; ++u)
+                        for (uint32_t v = 0; v < eff.kw; ++v) {
+                            const uint32_t l = ph.s * u + a, l2 = ph.s * v + b;
+                            if (l < d.kh && l2 < d.kw)
+                                out[(((size_t)m * eff.C + c1) * eff.kh + u) * eff.kw + v] =
+                                    K[(((size_t)m * d.C + ch) * d.kh + l) * d.kw + l2];
+                        }
+                }
+}
+
+// partition of the stride-1 layer `eff` (explicit, or the canonical search)
+hc_status partition_of(const hc_conv_desc &d, uint32_t N, hc_conv_desc *res, Geom *geo)
+{
+    const uint32_t Hp = d.H + 2 * d.pad, Wp = d.W + 2 * d.pad;
     if ((uint64_t)d.kh * d.kw > N) return set_error(HC_ERR_INVALID_ARG, "kernel does not fit in N");
     Geom best{};
     bool have = false;
@@ -106,22 +166,113 @@ hc_status resolve_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *
     return HC_OK;
 }
 
-// Pack int8 weights [M][C][kh][kw] into P = M*G polynomials of N int8 coefficients:
-// poly (m, g) coefficient O - c*Hw*Ww - l*Ww - l' = K[m][g*Cw + c][l][l'].
-void pack_weights(const hc_conv_desc &d, const Geom &g, uint32_t N, const int8_t *K, std::vector<int8_t> &out)
+// any convolution: *res is the stride-1 layer computed, with its partition
+hc_status resolve_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *res, Geom *geo, Phases *ph = nullptr)
+{
+    if (!desc || !res) return set_error(HC_ERR_INVALID_ARG, "null descriptor");
+    hc_conv_desc eff{};
+    Phases p{};
+    hc_status st = effective_desc(*desc, &eff, &p);
+    if (st != HC_OK) return st;
+    if (ph) *ph = p;
+    return partition_of(eff, N, res, geo);
+}
+
+// A fully connected layer y = W x (W: M x C) is the 1x1 convolution on a 1x1
+// image {C, 1, 1, M, 1, 1} with partition (Cw, 1, 1) and No output rows per
+// output polynomial (matrix-vector packing):
+//   input poly g : coeff [c] = x[g*Cw + c]
+//   weight poly m'*G + g : coeff [r*Cw + Cw-1 - c] = W[m'*No + r][g*Cw + c]
+//   output poly m' : coeff [r*Cw + Cw-1] holds y[m'*No + r]
+// No*Cw <= N.  A term lands at r*Cw + Cw-1 + (c_in - c), |c_in - c| < Cw, so no
+// other row's term reaches an extracted coefficient, and a term past X^N wraps
+// below Cw - 1.  Canonical: minimal 2I + P + 2O, then fewer P, larger Cw,
+// smaller No.
+hc_conv_desc fc_conv(uint32_t C, uint32_t M, uint32_t Cw)
+{
+    hc_conv_desc d{};
+    d.C = C;
+    d.H = d.W = 1;
+    d.M = M;
+    d.kh = d.kw = 1;
+    d.stride = 1;
+    d.pad = 0;
+    d.Cw = Cw;
+    d.Hw = d.Ww = 1;
+    return d;
+}
+
+hc_status resolve_fc(const hc_fc_desc *desc, uint32_t N, hc_fc_desc *res, hc_conv_desc *eff, Geom *geo)
+{
+    if (!desc) return set_error(HC_ERR_INVALID_ARG, "null descriptor");
+    const hc_fc_desc d = *desc;
+    if (!d.C || !d.M) return set_error(HC_ERR_INVALID_ARG, "zero dimension in fully connected descriptor");
+    Geom best{};
+    uint32_t best_no = 0;
+    if (d.Cw || d.No) {
+        if (!d.Cw || !d.No || d.Cw > d.C || d.No > d.M || (uint64_t)d.Cw * d.No > N)
+            return set_error(HC_ERR_INVALID_ARG, "invalid explicit partition Cw=%u No=%u", d.Cw, d.No);
+        best = geom_of(fc_conv(d.C, d.M, d.Cw), d.Cw, 1, 1, d.No);
+        best_no = d.No;
+    } else {
+        const uint32_t cmax = std::min(d.C, N);
+        for (uint32_t Cw = 1; Cw <= cmax; ++Cw) {
+            const hc_conv_desc c = fc_conv(d.C, d.M, Cw);
+            const uint32_t nmax = std::min(d.M, N / Cw);
+            for (uint32_t No = 1; No <= nmax; ++No) {
+                const Geom g = geom_of(c, Cw, 1, 1, No);
+                bool better;
+                if (!best_no) {
+                    better = true;
+                } else if (g.cost != best.cost) {
+                    better = g.cost < best.cost;
+                } else if (g.P != best.P) {
+                    better = g.P < best.P;
+                } else if (g.Cw != best.Cw) {
+                    better = g.Cw > best.Cw;
+                } else {
+                    better = No < best_no;
+                }
+                if (better) {
+                    best = g;
+                    best_no = No;
+                }
+            }
+        }
+    }
+    if (res) {
+        *res = d;
+        res->Cw = best.Cw;
+        res->No = best_no;
+    }
+    if (eff) *eff = fc_conv(d.C, d.M, best.Cw);
+    if (geo) *geo = best;
+    return HC_OK;
+}
+
+// Pack int8 weights [M][C][kh][kw] of the stride-1 layer d into P = Mp*G
+// polynomials of N int8 coefficients: poly (m', g) coefficient
+// r*S + O - c*Hw*Ww - l*Ww - l' = K[m'*No + r][g*Cw + c][l][l'], S = Cw*Hw*Ww.
+void pack_weights(const hc_conv_desc &d, const Geom &g, uint32_t No, uint32_t N, const int8_t *K,
+                  std::vector<int8_t> &out)
 {
     out.assign((size_t)g.P * N, 0);
-    const uint32_t HW = g.Hw * g.Ww;
+    const uint32_t HW = g.Hw * g.Ww, S = g.Cw * HW;
     const uint32_t off = (g.Cw - 1) * HW + (d.kh - 1) * g.Ww + (d.kw - 1);
-    for (uint32_t m = 0; m < d.M; ++m)
+    for (uint32_t mp = 0; mp < g.Mp; ++mp)
         for (uint32_t gi = 0; gi < g.G; ++gi) {
-            int8_t *poly = out.data() + ((size_t)m * g.G + gi) * N;
-            for (uint32_t c = 0; c < g.Cw; ++c) {
-                const uint32_t ch = gi * g.Cw + c;
-                if (ch >= d.C) break;
-                for (uint32_t l = 0; l < d.kh; ++l)
-                    for (uint32_t l2 = 0; l2 < d.kw; ++l2)
-                        poly[off - c * HW - l * g.Ww - l2] = K[(((size_t)m * d.C + ch) * d.kh + l) * d.kw + l2];
+            int8_t *poly = out.data() + ((size_t)mp * g.G + gi) * N;
+            for (uint32_t r = 0; r < No; ++r) {
+                const uint32_t m = mp * No + r;
+                if (m >= d.M) break;
+                for (uint32_t c = 0; c < g.Cw; ++c) {
+                    const uint32_t ch = gi * g.Cw + c;
+                    if (ch >= d.C) break;
+                    for (uint32_t l = 0; l < d.kh; ++l)
+                        for (uint32_t l2 = 0; l2 < d.kw; ++l2)
+                            poly[r * S + off - c * HW - l * g.Ww - l2] =
+                                K[(((size_t)m * d.C + ch) * d.kh + l) * d.kw + l2];
+                }
             }
         }
 }
@@ -144,7 +295,7 @@ size_t conv_scratch_words(const hc_ctx *ctx, const hc_weights *w)
 
 size_t conv_counter_bound(const hc_ctx *ctx, const hc_weights *w)
 {
-    return 1 + (size_t)ctx->L * (1 + w->desc.M);
+    return 1 + (size_t)ctx->L * (1 + w->Mp);
 }
 
 hc_status conv_layer(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_in, uint64_t *d_out,
@@ -187,6 +338,158 @@ hc_status check_inputs(const hc_ctx *ctx, const uint64_t *p, size_t n_polys, cud
     HC_CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     HC_CUDA_TRY(cudaStreamSynchronize(s));
     if (h) return set_error(HC_ERR_RANGE, "input residue out of range [0, q_i)");
+    return HC_OK;
+}
+}  // namespace hc
+
+namespace {
+// Weights of the stride-1 layer `eff` (resolved partition, geometry g, No output
+// rows per output polynomial) from its int8 kernel K [M][C][kh][kw].
+hc_status build_weights(const hc_ctx *ctx, const hc_conv_desc &eff, const Geom &g, uint32_t No, uint32_t kind,
+                        const hc_conv_desc &user, uint32_t pa, uint32_t pb, const int8_t *K, uint32_t mode,
+                        hc_weights **out, cudaStream_t s)
+{
+    DeviceGuard guard(ctx->device);
+    const uint32_t N = ctx->N, L = ctx->L;
+
+    std::vector<int8_t> packed;
+    // CSR of output terms: output o = m'*B + b sums g < G of (ct g*B + b, pt m'*G + g)
+    std::vector<uint32_t> term_ptr((size_t)g.O + 1), terms((size_t)2 * g.O * g.G);
+    for (uint32_t m = 0; m < g.Mp; ++m)
+        for (uint32_t b = 0; b < g.B; ++b) {
+            const uint32_t o = m * g.B + b;
+            term_ptr[o] = o * g.G;
+            for (uint32_t gi = 0; gi < g.G; ++gi) {
+                terms[2 * ((size_t)o * g.G + gi)] = gi * g.B + b;
+                terms[2 * ((size_t)o * g.G + gi) + 1] = m * g.G + gi;
+            }
+        }
+    term_ptr[g.O] = g.O * g.G;
+
+    hc_weights *w = new (std::nothrow) hc_weights();
+    if (!w) return set_error(HC_ERR_OOM, "host allocation failed");
+    w->magic = kMagicWeights;
+    w->ctx = ctx;
+    w->device = ctx->device;
+    w->desc = eff;
+    w->user = user;
+    w->user.Cw = eff.Cw;
+    w->user.Hw = eff.Hw;
+    w->user.Ww = eff.Ww;
+    w->kind = kind;
+    w->No = No;
+    w->Mp = g.Mp;
+    w->pa = pa;
+    w->pb = pb;
+    w->G = g.G;
+    w->B = g.B;
+    w->I = g.I;
+    w->P = g.P;
+    w->O = g.O;
+    w->mode = mode;
+    if (mode == HC_WEIGHTS_NO_NTT) {
+        // keep the small signed weights of the stride-1 layer; nothing is packed, lifted or transformed
+        const size_t kbytes = (size_t)eff.M * eff.C * eff.kh * eff.kw;
+        w->d_k = (int8_t *)dev_alloc_persistent(kbytes);
+        cudaError_t e = w->d_k ? cudaMemcpy(w->d_k, K, kbytes, cudaMemcpyHostToDevice) : cudaErrorMemoryAllocation;
+        if (e != cudaSuccess) {
+            hc_free(w);
+            return e == cudaErrorMemoryAllocation ? set_error(HC_ERR_OOM, "device allocation of weights failed")
+                                                  : cuda_error(e, "uploading weights");
+        }
+        *out = w;
+        return HC_OK;
+    }
+    pack_weights(eff, g, No, N, K, packed);
+    w->d_pt = (uint64_t *)dev_alloc_persistent((size_t)g.P * L * N * sizeof(uint64_t));
+    w->d_term_ptr = (uint32_t *)dev_alloc_persistent(term_ptr.size() * sizeof(uint32_t));
+    w->d_terms = (uint32_t *)dev_alloc_persistent(terms.size() * sizeof(uint32_t));
+    int8_t *d_packed = (int8_t *)dev_alloc(packed.size(), s);
+    auto fail = [&](hc_status e) {
+        dev_free(d_packed, s);
+        cudaStreamSynchronize(s);
+        hc_free(w);
+        return e;
+    };
+    if (!w->d_pt || !w->d_term_ptr || !w->d_terms || !d_packed)
+        return fail(set_error(HC_ERR_OOM, "device allocation of weights failed"));
+    cudaError_t e = cudaMemcpyAsync(d_packed, packed.data(), packed.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->d_term_ptr, term_ptr.data(), term_ptr.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_terms, terms.data(), terms.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(cuda_error(e, "uploading weights"));
+    hc_status st = launch_lift_int8(ctx, d_packed, w->d_pt, g.P, s);
+    if (st == HC_OK && mode == HC_WEIGHTS_NTT_OFFLINE) st = launch_ntt_fwd(ctx, w->d_pt, w->d_pt, g.P, s);
+    if (st != HC_OK) return fail(st);
+    // the host copy must outlive the asynchronous upload
+    e = cudaStreamSynchronize(s);
+    dev_free(d_packed, s);
+    d_packed = nullptr;
+    if (e != cudaSuccess) return fail(cuda_error(e, "weights preprocessing"));
+    *out = w;
+    return HC_OK;
+}
+
+// weights of a convolution (any stride) or of a fully connected layer, from the
+// caller's descriptor and int8 kernel
+hc_status make_conv_weights(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K, uint32_t mode,
+                            hc_weights **out, cudaStream_t s)
+{
+    hc_conv_desc res{};
+    Geom g{};
+    Phases ph{};
+    hc_status st = resolve_partition(desc, ctx->N, &res, &g, &ph);
+    if (st != HC_OK) return st;
+    if (ph.s == 1) return build_weights(ctx, res, g, 1, LAYER_CONV, *desc, 1, 1, h_K, mode, out, s);
+    std::vector<int8_t> k1;
+    polyphase_kernel(*desc, res, ph, h_K, k1);
+    return build_weights(ctx, res, g, 1, LAYER_CONV, *desc, ph.pa, ph.pb, k1.data(), mode, out, s);
+}
+
+hc_status make_fc_weights(const hc_ctx *ctx, const hc_fc_desc *desc, const int8_t *h_W, uint32_t mode,
+                          hc_weights **out, cudaStream_t s)
+{
+    hc_fc_desc res{};
+    hc_conv_desc eff{};
+    Geom g{};
+    hc_status st = resolve_fc(desc, ctx->N, &res, &eff, &g);
+    if (st != HC_OK) return st;
+    // W [M][C] is the kernel [M][C][1][1] of the 1x1 convolution
+    return build_weights(ctx, eff, g, res.No, LAYER_FC, eff, 1, 1, h_W, mode, out, s);
+}
+}  // namespace
+
+namespace hc {
+hc_status layer_geometry(const hc_conv_desc &user, uint32_t kind, uint32_t No, uint32_t N, LayerGeom *out)
+{
+    Geom g{};
+    LayerGeom lg{};
+    if (kind == LAYER_FC) {
+        if (user.H != 1 || user.W != 1 || user.kh != 1 || user.kw != 1 || user.stride != 1 || user.pad != 0)
+            return set_error(HC_ERR_INVALID_ARG, "not a fully connected layer");
+        const hc_fc_desc d{user.C, user.M, user.Cw, No};
+        hc_status st = resolve_fc(&d, N, nullptr, &lg.eff, &g);
+        if (st != HC_OK) return st;
+        lg.No = No;
+        lg.pa = lg.pb = 1;
+    } else if (kind == LAYER_CONV) {
+        if (No != 1) return set_error(HC_ERR_INVALID_ARG, "convolutions have one output channel per ciphertext");
+        Phases ph{};
+        hc_status st = resolve_partition(&user, N, &lg.eff, &g, &ph);
+        if (st != HC_OK) return st;
+        lg.No = 1;
+        lg.pa = ph.pa;
+        lg.pb = ph.pb;
+    } else {
+        return set_error(HC_ERR_INVALID_ARG, "unknown layer kind %u", kind);
+    }
+    lg.Mp = g.Mp;
+    lg.G = g.G;
+    lg.B = g.B;
+    lg.I = g.I;
+    lg.P = g.P;
+    lg.O = g.O;
+    *out = lg;
     return HC_OK;
 }
 }  // namespace hc
@@ -428,11 +731,25 @@ hc_status hc_conv_partition(const hc_conv_desc *desc, uint32_t N, hc_conv_desc *
     return HC_OK;
 }
 
+hc_status hc_fc_partition(const hc_fc_desc *desc, uint32_t N, hc_fc_desc *resolved, uint32_t *n_in_ct,
+                          uint32_t *n_pt, uint32_t *n_out_ct)
+{
+    if (!resolved) return set_error(HC_ERR_INVALID_ARG, "resolved is NULL");
+    Geom g{};
+    hc_status st = resolve_fc(desc, N, resolved, nullptr, &g);
+    if (st != HC_OK) return st;
+    if (n_in_ct) *n_in_ct = g.I;
+    if (n_pt) *n_pt = g.P;
+    if (n_out_ct) *n_out_ct = g.O;
+    return HC_OK;
+}
+
 hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K, hc_weights **out,
                                 void *cuda_stream)
 {
     return hc_weights_preprocess_ex(ctx, desc, h_K, HC_WEIGHTS_NTT_OFFLINE, out, cuda_stream);
 }
+
 
 hc_status hc_weights_preprocess_ex(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K, uint32_t mode,
                                    hc_weights **out, void *cuda_stream)
@@ -442,79 +759,28 @@ hc_status hc_weights_preprocess_ex(const hc_ctx *ctx, const hc_conv_desc *desc, 
     if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
     if (!h_K) return set_error(HC_ERR_INVALID_ARG, "h_K is NULL");
     if (mode > HC_WEIGHTS_NO_NTT) return set_error(HC_ERR_INVALID_ARG, "unknown weights mode %u", mode);
-    hc_conv_desc res{};
-    Geom g{};
-    hc_status st = resolve_partition(desc, ctx->N, &res, &g);
-    if (st != HC_OK) return st;
-    DeviceGuard guard(ctx->device);
-    cudaStream_t s = as_stream(cuda_stream);
-    const uint32_t N = ctx->N, L = ctx->L;
+    return make_conv_weights(ctx, desc, h_K, mode, out, as_stream(cuda_stream));
+}
 
-    std::vector<int8_t> packed;
-    pack_weights(res, g, N, h_K, packed);
-    // CSR of output terms: output o = m*B + b sums g < G of (ct g*B + b, pt m*G + g)
-    std::vector<uint32_t> term_ptr((size_t)g.O + 1), terms((size_t)2 * g.O * g.G);
-    for (uint32_t m = 0; m < res.M; ++m)
-        for (uint32_t b = 0; b < g.B; ++b) {
-            const uint32_t o = m * g.B + b;
-            term_ptr[o] = o * g.G;
-            for (uint32_t gi = 0; gi < g.G; ++gi) {
-                terms[2 * ((size_t)o * g.G + gi)] = gi * g.B + b;
-                terms[2 * ((size_t)o * g.G + gi) + 1] = m * g.G + gi;
-            }
-        }
-    term_ptr[g.O] = g.O * g.G;
+hc_status hc_weights_preprocess_fc(const hc_ctx *ctx, const hc_fc_desc *desc, const int8_t *h_W, uint32_t mode,
+                                   hc_weights **out, void *cuda_stream)
+{
+    if (!out) return set_error(HC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (!h_W) return set_error(HC_ERR_INVALID_ARG, "h_W is NULL");
+    if (mode > HC_WEIGHTS_NO_NTT) return set_error(HC_ERR_INVALID_ARG, "unknown weights mode %u", mode);
+    return make_fc_weights(ctx, desc, h_W, mode, out, as_stream(cuda_stream));
+}
 
-    hc_weights *w = new (std::nothrow) hc_weights();
-    if (!w) return set_error(HC_ERR_OOM, "host allocation failed");
-    w->magic = kMagicWeights;
-    w->ctx = ctx;
-    w->device = ctx->device;
-    w->desc = res;
-    w->G = g.G;
-    w->B = g.B;
-    w->I = g.I;
-    w->P = g.P;
-    w->O = g.O;
-    w->mode = mode;
-    if (mode == HC_WEIGHTS_NO_NTT) {
-        // keep the small signed weights as given; nothing is packed, lifted or transformed
-        const size_t kbytes = (size_t)res.M * res.C * res.kh * res.kw;
-        w->d_k = (int8_t *)dev_alloc_persistent(kbytes);
-        cudaError_t e = w->d_k ? cudaMemcpy(w->d_k, h_K, kbytes, cudaMemcpyHostToDevice) : cudaErrorMemoryAllocation;
-        if (e != cudaSuccess) {
-            hc_free(w);
-            return e == cudaErrorMemoryAllocation ? set_error(HC_ERR_OOM, "device allocation of weights failed")
-                                                  : cuda_error(e, "uploading weights");
-        }
-        *out = w;
-        return HC_OK;
-    }
-    w->d_pt = (uint64_t *)dev_alloc_persistent((size_t)g.P * L * N * sizeof(uint64_t));
-    w->d_term_ptr = (uint32_t *)dev_alloc_persistent(term_ptr.size() * sizeof(uint32_t));
-    w->d_terms = (uint32_t *)dev_alloc_persistent(terms.size() * sizeof(uint32_t));
-    int8_t *d_packed = (int8_t *)dev_alloc(packed.size(), s);
-    auto fail = [&](hc_status e) {
-        dev_free(d_packed, s);
-        cudaStreamSynchronize(s);
-        hc_free(w);
-        return e;
-    };
-    if (!w->d_pt || !w->d_term_ptr || !w->d_terms || !d_packed)
-        return fail(set_error(HC_ERR_OOM, "device allocation of weights failed"));
-    cudaError_t e = cudaMemcpyAsync(d_packed, packed.data(), packed.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(w->d_term_ptr, term_ptr.data(), term_ptr.size() * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_terms, terms.data(), terms.size() * 4, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return fail(cuda_error(e, "uploading weights"));
-    st = launch_lift_int8(ctx, d_packed, w->d_pt, g.P, s);
-    if (st == HC_OK && mode == HC_WEIGHTS_NTT_OFFLINE) st = launch_ntt_fwd(ctx, w->d_pt, w->d_pt, g.P, s);
-    if (st != HC_OK) return fail(st);
-    dev_free(d_packed, s);
-    d_packed = nullptr;
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(cuda_error(e, "weights preprocessing"));
-    *out = w;
+hc_status hc_weights_layout(const hc_weights *w, hc_conv_desc *computed, uint32_t *kind, uint32_t *No,
+                            uint32_t *n_slots)
+{
+    if (!weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid weights handle");
+    if (computed) *computed = w->desc;
+    if (kind) *kind = w->kind;
+    if (No) *No = w->No;
+    if (n_slots) *n_slots = w->No * (w->desc.Hw - w->desc.kh + 1) * (w->desc.Ww - w->desc.kw + 1);
     return HC_OK;
 }
 
@@ -577,7 +843,7 @@ hc_status hc_conv_ct_pt_plain(const hc_ctx *ctx, const hc_weights *w, const uint
     if (st != HC_OK) return st;
     const size_t ct_words = (size_t)2 * ctx->L * ctx->N, pt_words = (size_t)ctx->L * ctx->N;
     HC_CUDA_TRY(cudaMemsetAsync(d_ct_out, 0, (size_t)w->O * ct_words * sizeof(uint64_t), s));
-    const uint32_t M = w->desc.M;
+    const uint32_t M = w->Mp;
     for (uint32_t m = 0; m < M; ++m)
         for (uint32_t gi = 0; gi < w->G; ++gi)
             for (uint32_t b = 0; b < w->B; ++b) {

@@ -203,7 +203,7 @@ hc_status fused_for_ns(const ConvJob *jobs, size_t n, uint32_t *ctr, cudaStream_
         idx[P.n] = &jobs[i];
         FusedLayer &ly = P.s[P.n++];
         const ConvJob &j = jobs[i];
-        ly.mac = make_mac_seg(j.ctx, j.ntt, job_weights(j), j.out, j.w->G, j.w->B, j.w->desc.M, kMacKC);
+        ly.mac = make_mac_seg(j.ctx, j.ntt, job_weights(j), j.out, j.w->G, j.w->B, j.w->Mp, kMacKC);
         ly.in = j.in;
         ly.I = j.w->I;
         ly.O = j.w->O;
@@ -257,7 +257,7 @@ size_t fused_counter_words(const ConvJob *jobs, size_t n, uint32_t logN)
     for (size_t i = 0; i < n; ++i) {
         if (jobs[i].ctx->logN != logN || !jobs[i].blocked) continue;
         const MacSeg sg = make_mac_seg(jobs[i].ctx, jobs[i].ntt, job_weights(jobs[i]), jobs[i].out, jobs[i].w->G,
-                                       jobs[i].w->B, jobs[i].w->desc.M, kMacKC);
+                                       jobs[i].w->B, jobs[i].w->Mp, kMacKC);
         words += jobs[i].ctx->L * (1 + sg.groups);
     }
     return words ? words + 1 : 0;

@@ -61,12 +61,30 @@ struct hc_ctx {
     uint8_t variant[hc::KK_COUNT];  // launch-shape variant per kernel family
 };
 
+// A linear layer is held as a stride-1 convolution without output packing
+// restrictions: `desc` is that convolution (for a strided layer the layer of
+// the phase-split input, for a fully connected layer a 1x1 convolution on a
+// 1x1 image) with its resolved partition; `No` output channels share one
+// output polynomial at coefficient shifts of Cw*Hw*Ww, so Mp = ceil(M/No)
+// output polynomials per spatial block.  Convolutions have No = 1, Mp = M.
+enum LayerKind : uint32_t { LAYER_CONV = 0, LAYER_FC = 1 };
+
+// The stride-1 layer computed for a caller's layer, and its geometry.
+struct LayerGeom {
+    hc_conv_desc eff;
+    uint32_t No, Mp, pa, pb, G, B, I, P, O;
+};
+
 struct hc_weights {
     uint32_t magic;
     const hc_ctx *ctx;
     int device;
-    hc_conv_desc desc;        // resolved partition
-    uint32_t G, B, I, P, O;
+    hc_conv_desc desc;        // the stride-1 layer computed, resolved partition
+    hc_conv_desc user;        // the layer as described by the caller (stride, pad, C/H/W/kh/kw of its tensors)
+    uint32_t kind;            // LayerKind
+    uint32_t No, Mp;          // output channels per output polynomial, output polynomials per block
+    uint32_t pa, pb;          // row and column phases of a strided layer (1, 1 for stride 1)
+    uint32_t G, B, I, P, O;   // P = Mp*G, O = Mp*B
     uint32_t mode;            // hc_weights_mode
     uint64_t *d_pt;           // [P][L][N] NTT domain (offline mode) or coefficient domain (online mode), owned
     int8_t *d_k;              // [M][C][kh][kw] (no-NTT mode), owned
@@ -75,6 +93,11 @@ struct hc_weights {
 };
 
 namespace hc {
+
+// Geometry of a layer from the caller's descriptor (kind LAYER_CONV: any stride;
+// LAYER_FC: the 1x1 convolution {C,1,1,M,1,1,1,0,Cw,1,1} with No rows per output)
+// with an explicit partition, as saved weights store it.
+hc_status layer_geometry(const hc_conv_desc &user, uint32_t kind, uint32_t No, uint32_t N, LayerGeom *out);
 
 // ---- error reporting ------------------------------------------------------
 hc_status set_error(hc_status s, const char *fmt, ...);

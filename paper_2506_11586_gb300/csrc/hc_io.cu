@@ -3,11 +3,14 @@
 // (Sec. 8.1); saving the NTT-domain plaintexts lets a restarted server resume
 // without repacking and re-transforming them.
 //
-// File layout (little-endian): the 8-byte tag "HCWTS001"; a header of u32 N,
-// L, mode, G, B, I, P, O, the 11 u32 of the resolved hc_conv_desc, u64 t and
-// the L moduli; u64 sizes of the four payloads (NTT-domain plaintexts, int8
-// kernel, term pointers, terms); the payloads; a u64 FNV-1a hash of every
-// byte before it.
+// File layout (little-endian): the 8-byte tag "HCWTS002"; a header of u32 N,
+// L, mode, kind, No, G, B, I, P, O; the 11 u32 of the caller's hc_conv_desc
+// (any stride; a fully connected layer as its 1x1 convolution) with the
+// resolved partition; u64 t and the L moduli; u64 sizes of the four payloads
+// (NTT-domain plaintexts, int8 kernel of the stride-1 layer, term pointers,
+// terms); the payloads; a u64 FNV-1a hash of every byte before it.  Loading
+// derives the layer's geometry from the descriptor again and refuses a file
+// whose counts disagree with it.
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -18,7 +21,7 @@ using namespace hc;
 
 namespace {
 
-constexpr char kTag[8] = {'H', 'C', 'W', 'T', 'S', '0', '0', '1'};
+constexpr char kTag[8] = {'H', 'C', 'W', 'T', 'S', '0', '0', '2'};
 
 struct Fnv {
     uint64_t h = 1469598103934665603ull;
@@ -86,9 +89,9 @@ hc_status hc_weights_save(const hc_weights *w, const char *path)
     if (!f) return set_error(HC_ERR_INVALID_ARG, "cannot open %s for writing", path);
     Writer wr{f};
     wr.put(kTag, sizeof kTag);
-    const uint32_t hdr[8] = {c->N, c->L, w->mode, w->G, w->B, w->I, w->P, w->O};
+    const uint32_t hdr[10] = {c->N, c->L, w->mode, w->kind, w->No, w->G, w->B, w->I, w->P, w->O};
     wr.put(hdr, sizeof hdr);
-    wr.put(&w->desc, sizeof(hc_conv_desc));
+    wr.put(&w->user, sizeof(hc_conv_desc));
     wr.put(&c->t, sizeof c->t);
     wr.put(c->q, sizeof(uint64_t) * c->L);
     const uint64_t sizes[4] = {pt_words, kb, n_tp, n_t};
@@ -113,12 +116,12 @@ hc_status hc_weights_load(const hc_ctx *ctx, const char *path, hc_weights **out)
     if (!f) return set_error(HC_ERR_INVALID_ARG, "cannot open %s", path);
     Reader rd{f};
     char tag[8];
-    uint32_t hdr[8];
-    hc_conv_desc desc;
+    uint32_t hdr[10];
+    hc_conv_desc user;
     uint64_t t = 0, q[kMaxLimbs] = {}, sizes[4] = {};
     rd.get(tag, sizeof tag);
     rd.get(hdr, sizeof hdr);
-    rd.get(&desc, sizeof desc);
+    rd.get(&user, sizeof user);
     rd.get(&t, sizeof t);
     const uint32_t L = hdr[1];
     bool ok = rd.ok && memcmp(tag, kTag, sizeof tag) == 0 && L >= 1 && L <= kMaxLimbs;
@@ -133,12 +136,18 @@ hc_status hc_weights_load(const hc_ctx *ctx, const char *path, hc_weights **out)
         fclose(f);
         return set_error(HC_ERR_INVALID_ARG, "%s was saved for other ring parameters", path);
     }
-    const uint32_t mode = hdr[2], G = hdr[3], B = hdr[4], I = hdr[5], P = hdr[6], O = hdr[7];
-    const size_t want_pt = mode == HC_WEIGHTS_NO_NTT ? 0 : (size_t)P * ctx->L * ctx->N;
+    const uint32_t mode = hdr[2], kind = hdr[3], No = hdr[4];
+    LayerGeom lg{};
+    if (mode > HC_WEIGHTS_NO_NTT || layer_geometry(user, kind, No, ctx->N, &lg) != HC_OK) {
+        fclose(f);
+        return set_error(HC_ERR_INVALID_ARG, "%s describes no valid layer", path);
+    }
+    const hc_conv_desc &desc = lg.eff;
+    const size_t want_pt = mode == HC_WEIGHTS_NO_NTT ? 0 : (size_t)lg.P * ctx->L * ctx->N;
     const size_t want_k = mode == HC_WEIGHTS_NO_NTT ? (size_t)desc.M * desc.C * desc.kh * desc.kw : 0;
-    if (mode > HC_WEIGHTS_NO_NTT || sizes[0] != want_pt || sizes[1] != want_k ||
-        (mode != HC_WEIGHTS_NO_NTT && (sizes[2] != (size_t)O + 1 || sizes[3] != (size_t)2 * O * G)) ||
-        I != G * B || O != desc.M * B || P != desc.M * G) {
+    if (sizes[0] != want_pt || sizes[1] != want_k ||
+        (mode != HC_WEIGHTS_NO_NTT && (sizes[2] != (size_t)lg.O + 1 || sizes[3] != (size_t)2 * lg.O * lg.G)) ||
+        hdr[5] != lg.G || hdr[6] != lg.B || hdr[7] != lg.I || hdr[8] != lg.P || hdr[9] != lg.O) {
         fclose(f);
         return set_error(HC_ERR_INVALID_ARG, "%s has inconsistent sizes", path);
     }
@@ -162,11 +171,17 @@ hc_status hc_weights_load(const hc_ctx *ctx, const char *path, hc_weights **out)
     w->ctx = ctx;
     w->device = ctx->device;
     w->desc = desc;
-    w->G = G;
-    w->B = B;
-    w->I = I;
-    w->P = P;
-    w->O = O;
+    w->user = user;
+    w->kind = kind;
+    w->No = lg.No;
+    w->Mp = lg.Mp;
+    w->pa = lg.pa;
+    w->pb = lg.pb;
+    w->G = lg.G;
+    w->B = lg.B;
+    w->I = lg.I;
+    w->P = lg.P;
+    w->O = lg.O;
     w->mode = mode;
     auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
         if (!bytes) return true;

@@ -222,7 +222,7 @@ uint64_t plan_signature(const hc_plan *p)
         mix(c.ctx->L);
         mix(c.w->G);
         mix(c.w->B);
-        mix(c.w->desc.M);
+        mix(c.w->Mp);
         mix(c.w->I);
         mix(c.w->O);
     }
@@ -349,7 +349,7 @@ hc_status launch_limb_chains(const ConvJob *jobs, size_t n, uint32_t logN, cudaS
                 v.Lc = 1;
                 v.limb0 = l;
                 inv.s[inv.n++] = v;
-                MacLayer ly{c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->desc.M};
+                MacLayer ly{c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->Mp};
                 ly.Lc = 1;
                 ly.limb0 = l;
                 mctx.push_back(c.ctx);
@@ -413,7 +413,7 @@ hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s, uint32
         if (!c.blocked)
             return launch_mac_intt(c.ctx, c.ntt, job_weights(c), MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out, c.w->O,
                                    s);
-        st = launch_mac_conv(c.ctx, c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->desc.M, s);
+        st = launch_mac_conv(c.ctx, c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->Mp, s);
         if (st != HC_OK) return st;
         return launch_ntt_inv_ct(c.ctx, c.out, c.out, c.w->O, s);
     }
@@ -445,7 +445,7 @@ hc_status launch_conv_jobs(const ConvJob *jobs, size_t n, cudaStream_t s, uint32
         if (done(c)) continue;
         if (c.blocked) {
             mctx.push_back(c.ctx);
-            layers.push_back(MacLayer{c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->desc.M});
+            layers.push_back(MacLayer{c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->Mp});
         } else {
             hc_status st = launch_mac_intt(c.ctx, c.ntt, job_weights(c), MacTerms{c.w->d_term_ptr, c.w->d_terms}, c.out,
                                            c.w->O, s);
@@ -535,7 +535,7 @@ hc_status hc_plan_create(const hc_work_item *items, size_t n, hc_plan **out)
             const hc_weights *w = it.weights;
             p->convs.push_back(PlanConv{c, w, it.d_ct_in, it.d_ct_out, nullptr, conv_job_blocked(c, w)});
             scratch_words += (size_t)w->I * ct_words(c);
-            p->n_products += (uint64_t)w->desc.M * w->G * w->B;
+            p->n_products += (uint64_t)w->Mp * w->G * w->B;
             p->alg_bytes += nl * (2ull * w->I + w->P + 2ull * w->O);
         } else {
             p->prods.push_back(PlanProd{c, it.d_ct_in, it.d_pt_ntt, it.d_ct_out, it.n});

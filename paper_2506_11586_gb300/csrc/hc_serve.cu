@@ -407,7 +407,7 @@ hc_status hc_server_add_layer(hc_server *s, const hc_ctx *ctx, const hc_weights 
     ly.w = w;
     ly.in_words = (size_t)w->I * 2 * ctx->L * ctx->N;
     ly.out_words = (size_t)w->O * 2 * ctx->L * ctx->N;
-    ly.products = (uint64_t)w->desc.M * w->G * w->B;
+    ly.products = (uint64_t)w->Mp * w->G * w->B;
     ly.blocked = conv_job_blocked(ctx, w);
     std::lock_guard<std::mutex> lk(s->mu);
     *layer_id = (uint32_t)s->layers.size();

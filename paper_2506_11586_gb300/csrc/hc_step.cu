@@ -1,4 +1,4 @@
-// hc_step.cu -- the server's step around the convolution (Sec. 7): add the
+// hc_step.cu -- the server's step around a linear layer (Sec. 7): add the
 // server's activation share to the client's ciphertexts, run the convolution
 // with the NTT-preprocessed weights, subtract the server's random output mask,
 // and extract only the output coefficients of c0 (Sec. 6.2: the results are
@@ -14,34 +14,47 @@
 namespace hc {
 namespace {
 
+// Geometry of the step: the stride-1 layer computed (desc of the weights), its
+// output packing, and the caller's input tensor with the phase split of a
+// strided layer (s = 1, pb = 1, C1 = C0 for stride 1).
 struct StepGeom {
-    uint32_t C, H, W, pad, Cw, Hw, Ww, B, Bw, oh, ow, Ho, Wo, M, offset, S;
+    uint32_t Cw, Hw, Ww, Hpe, Wpe, B, Bw, oh, ow, Ho, Wo, offset, span, No, M;
+    uint32_t C1, C0, H0, W0, pad0, s, pb;
 };
 
 StepGeom geom_of(const hc_weights *w)
 {
     const hc_conv_desc &d = w->desc;
     StepGeom g;
-    g.C = d.C;
-    g.H = d.H;
-    g.W = d.W;
-    g.pad = d.pad;
     g.Cw = d.Cw;
     g.Hw = d.Hw;
     g.Ww = d.Ww;
+    g.Hpe = d.H + 2 * d.pad;
+    g.Wpe = d.W + 2 * d.pad;
     g.B = w->B;
     g.oh = d.Hw - d.kh + 1;
     g.ow = d.Ww - d.kw + 1;
-    g.Ho = d.H + 2 * d.pad - d.kh + 1;
-    g.Wo = d.W + 2 * d.pad - d.kw + 1;
+    g.Ho = g.Hpe - d.kh + 1;
+    g.Wo = g.Wpe - d.kw + 1;
     g.Bw = (g.Wo + g.ow - 1) / g.ow;
-    g.M = d.M;
     g.offset = (d.Cw - 1) * d.Hw * d.Ww + (d.kh - 1) * d.Ww + (d.kw - 1);
-    g.S = g.oh * g.ow;
+    g.span = d.Cw * d.Hw * d.Ww;
+    g.No = w->No;
+    g.M = d.M;
+    g.C1 = d.C;
+    g.C0 = w->user.C;
+    g.H0 = w->user.H;
+    g.W0 = w->user.W;
+    g.pad0 = w->user.pad;
+    g.s = w->user.stride;
+    g.pb = w->pb;
     return g;
 }
 
-// out = in with c0 += Delta * (server share packed like the input), c1 copied
+// out = in with c0 += Delta * (server share packed like the input), c1 copied.
+// Input coefficient (channel c1, padded position (r, q)) of the stride-1 layer
+// holds x~[c1 % C0][s*r + a - pad0][s*q + b - pad0] of the caller's tensor,
+// (a, b) = phase c1 / C0 split by pb (Sec. 8.1 networks; the polyphase split).
 __global__ void k_share_add(const uint64_t *__restrict__ in, const uint64_t *__restrict__ share,
                             uint64_t *__restrict__ out, const LimbConst *__restrict__ limbs, uint32_t L, uint32_t N,
                             StepGeom g, size_t total)
@@ -56,35 +69,44 @@ __global__ void k_share_add(const uint64_t *__restrict__ in, const uint64_t *__r
         if (comp == 0 && k < g.Cw * area) {
             const uint32_t c = k / area, rem = k % area, ii = rem / g.Ww, jj = rem % g.Ww;
             const uint32_t grp = item / g.B, b = item % g.B;
-            const uint32_t ch = grp * g.Cw + c;
-            const uint32_t r = (b / g.Bw) * g.oh + ii, s = (b % g.Bw) * g.ow + jj;  // padded coordinates
-            if (ch < g.C && r >= g.pad && r < g.H + g.pad && s >= g.pad && s < g.W + g.pad) {
-                const uint64_t x = share[((size_t)ch * g.H + (r - g.pad)) * g.W + (s - g.pad)];
-                const LimbConst &lc = limbs[limb];
-                const uint64_t q = lc.q;
-                const uint64_t dx = canon4(shoup_lazy(x, lc.delta, lc.delta_s, 0ull - q), q);
-                v = csub(v + dx, q);
+            const uint32_t ch1 = grp * g.Cw + c;
+            const uint32_t r = (b / g.Bw) * g.oh + ii, q = (b % g.Bw) * g.ow + jj;  // padded coordinates
+            if (ch1 < g.C1 && r < g.Hpe && q < g.Wpe) {
+                const uint32_t phase = ch1 / g.C0, ch = ch1 % g.C0;
+                const int64_t R = (int64_t)g.s * r + phase / g.pb - g.pad0;
+                const int64_t Q = (int64_t)g.s * q + phase % g.pb - g.pad0;
+                if (R >= 0 && R < g.H0 && Q >= 0 && Q < g.W0) {
+                    const uint64_t x = share[((size_t)ch * g.H0 + R) * g.W0 + Q];
+                    const LimbConst &lc = limbs[limb];
+                    const uint64_t qm = lc.q;
+                    const uint64_t dx = canon4(shoup_lazy(x, lc.delta, lc.delta_s, 0ull - qm), qm);
+                    v = csub(v + dx, qm);
+                }
             }
         }
         out[i] = v;
     }
 }
 
-// slots[o][l][s] = c0[offset + i*Ww + j] - Delta * r[m][row][col] (or 0 outside the output map)
+// slots[o][l][s] = c0[n*span + offset + i*Ww + j] - Delta * r[m][row][col] for
+// s = (n*oh + i)*ow + j, m = (o / B)*No + n (or 0 outside the output map / past M)
 __global__ void k_extract_mask(const uint64_t *__restrict__ ct_out, const uint64_t *__restrict__ mask,
                                uint64_t *__restrict__ slots, const LimbConst *__restrict__ limbs, uint32_t L,
                                uint32_t N, StepGeom g, size_t total)
 {
+    const uint32_t per = g.oh * g.ow, S = g.No * per;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const uint32_t s = (uint32_t)(i % g.S);
-        const size_t rest = i / g.S;
+        const uint32_t sl = (uint32_t)(i % S);
+        const size_t rest = i / S;
         const uint32_t limb = (uint32_t)(rest % L), o = (uint32_t)(rest / L);
-        const uint32_t m = o / g.B, b = o % g.B;
-        const uint32_t ii = s / g.ow, jj = s % g.ow;
+        const uint32_t mp = o / g.B, b = o % g.B;
+        const uint32_t n = sl / per, rem = sl % per;
+        const uint32_t ii = rem / g.ow, jj = rem % g.ow;
+        const uint32_t m = mp * g.No + n;
         const uint32_t row = (b / g.Bw) * g.oh + ii, col = (b % g.Bw) * g.ow + jj;
         uint64_t v = 0;
-        if (row < g.Ho && col < g.Wo) {
-            const uint32_t k = g.offset + ii * g.Ww + jj;
+        if (m < g.M && row < g.Ho && col < g.Wo) {
+            const uint32_t k = n * g.span + g.offset + ii * g.Ww + jj;
             v = ct_out[(((size_t)o * 2) * L + limb) * N + k];
             if (mask) {
                 const LimbConst &lc = limbs[limb];
@@ -144,7 +166,7 @@ extern "C" hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w,
     }
     st = conv_any(ctx, w, src, d_ct_out, s);  // any preprocessing mode
     if (st != HC_OK) return st;
-    const size_t slot_words = (size_t)w->O * ctx->L * g.S;
+    const size_t slot_words = (size_t)w->O * ctx->L * g.No * g.oh * g.ow;
     ProfileScope ps("k_extract_mask", s);
     k_extract_mask<<<grid_for(slot_words), 256, 0, s>>>(d_ct_out, d_mask, d_c0_slots, ctx->d_limbs, ctx->L, ctx->N, g,
                                                         slot_words);

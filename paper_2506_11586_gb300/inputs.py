@@ -162,6 +162,40 @@ RESNET50_STRIDE1 = (
     ConvShape("res5.conv1", 2048, 7, 7, 512, 1, 1, 0),
 )
 
+@dataclass(frozen=True)
+class StridedShape:
+    """Convolution with stride: C input channels of H x W, M output channels,
+    kh x kw kernel, zero padding pad on every side."""
+    name: str
+    C: int
+    H: int
+    W: int
+    M: int
+    kh: int
+    kw: int
+    stride: int
+    pad: int
+
+
+# SqueezeNet-1.1's first convolution (3x3, stride 2, no padding, 224 -> 111).
+SQUEEZENET_CONV1 = StridedShape("conv1", 3, 224, 224, 64, 3, 3, 2, 0)
+
+# The strided convolutions of ResNet-50 (v1.5 layout: the stride sits on the
+# 3x3 convolution of each stage's first block, and the projection shortcut of
+# stages 3-5 is a 1x1 stride-2 convolution), at a 224x224 input.
+RESNET50_STRIDED = (
+    StridedShape("conv1", 3, 224, 224, 64, 7, 7, 2, 3),
+    StridedShape("res3.conv2_s2", 128, 56, 56, 128, 3, 3, 2, 1),
+    StridedShape("res3.proj", 256, 56, 56, 512, 1, 1, 2, 0),
+    StridedShape("res4.conv2_s2", 256, 28, 28, 256, 3, 3, 2, 1),
+    StridedShape("res4.proj", 512, 28, 28, 1024, 1, 1, 2, 0),
+    StridedShape("res5.conv2_s2", 512, 14, 14, 512, 3, 3, 2, 1),
+    StridedShape("res5.proj", 1024, 14, 14, 2048, 1, 1, 2, 0),
+)
+
+# ResNet-50's fully connected classifier: 2048 inputs, 1000 outputs.
+RESNET50_FC = (2048, 1000)
+
 # The single-layer benchmark workload: 56x56x64 activations, 3x3 weights,
 # 64 output channels, stride 1, pad 1, N = 8192 with three 50-bit primes.
 CONV_56x56x64 = ConvShape("conv3x3_56x56x64_to64", 64, 56, 56, 64, 3, 3, 1)

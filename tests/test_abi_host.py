@@ -116,10 +116,10 @@ def test_partition_parity_random_shapes():
 
 
 def test_partition_errors():
-    d = L.make_desc(8, 8, 8, 4, 3, 3, pad=1, stride=2)
+    d = L.make_desc(8, 8, 8, 4, 3, 3, pad=1, stride=0)
     with pytest.raises(L.HcError) as e:
         L.hc_conv_partition(d, 4096)
-    assert e.value.status == L.HC_ERR_UNSUPPORTED
+    assert e.value.status == L.HC_ERR_INVALID_ARG
     d = L.make_desc(8, 8, 8, 4, 3, 3, pad=1, Cw=8, Hw=30, Ww=30)   # 8*30*30 > 4096
     with pytest.raises(L.HcError) as e:
         L.hc_conv_partition(d, 4096)
@@ -131,3 +131,49 @@ def test_partition_errors():
     res, i, p, o = L.hc_conv_partition(d, 4096)
     op = conv.Partition(8, 8, 8, 4, 3, 3, 1, 4096, 4, 6, 6)
     assert (res.Cw, res.Hw, res.Ww, i, p, o) == (4, 6, 6, op.I, op.P, op.O)
+
+
+STRIDED = [  # (C, H, W, M, kh, kw, stride, pad, N): the networks' strided layers and odd cases
+    (3, 224, 224, 64, 3, 3, 2, 0, 8192),      # SqueezeNet-1.1 conv1
+    (3, 224, 224, 64, 7, 7, 2, 3, 16384),     # ResNet-50 conv1
+    (128, 56, 56, 128, 3, 3, 2, 1, 16384),    # ResNet-50 layer2 downsampling 3x3
+    (256, 56, 56, 512, 1, 1, 2, 0, 16384),    # ResNet-50 layer2 projection 1x1
+    (5, 13, 11, 3, 4, 2, 3, 1, 4096),
+    (2, 9, 9, 2, 2, 3, 2, 2, 4096),
+]
+
+
+def test_strided_partition_parity():
+    from oracle import layers
+    for C_, H, W, M, kh, kw, st, pad, N in STRIDED:
+        res, i, p, o = L.hc_conv_partition(L.make_desc(C_, H, W, M, kh, kw, pad=pad, stride=st), N)
+        ph, op = layers.strided_partition(C_, H, W, M, kh, kw, st, pad, N)
+        assert (res.C, res.H, res.W, res.M, res.kh, res.kw, res.stride, res.pad) == \
+            (ph.C1, ph.H1, ph.W1, M, ph.kh1, ph.kw1, 1, 0)
+        assert (res.Cw, res.Hw, res.Ww, i, p, o) == (op.Cw, op.Hw, op.Ww, op.I, op.P, op.O)
+    # stride 1 is left as given
+    res, *_ = L.hc_conv_partition(L.make_desc(4, 9, 9, 2, 3, 3, pad=1), 4096)
+    assert (res.C, res.H, res.pad, res.stride) == (4, 9, 1, 1)
+
+
+def test_fc_partition_parity():
+    from oracle import layers
+    s = Stream(18, 0)
+    cases = [(2048, 1000, 16384), (2048, 1000, 8192), (512, 10, 4096), (4096, 4096, 8192)]
+    for _ in range(12):
+        cases.append((int(s.below(3000, 1)[0]) + 1, int(s.below(300, 1)[0]) + 1, (1024, 4096)[int(s.below(2, 1)[0])]))
+    for C_, M, N in cases:
+        res, i, p, o = L.hc_fc_partition(L.make_fc_desc(C_, M), N)
+        fp = layers.canonical_fc_partition(C_, M, N)
+        assert (res.Cw, res.No, i, p, o) == (fp.Cw, fp.No, fp.I, fp.P, fp.O), (C_, M, N)
+    res, i, p, o = L.hc_fc_partition(L.make_fc_desc(45, 23, Cw=20, No=9), 256)
+    assert (res.Cw, res.No, i, p, o) == (20, 9, 3, 9, 3)
+
+
+def test_fc_partition_errors():
+    for d, N in ((L.make_fc_desc(0, 5), 4096), (L.make_fc_desc(10, 5, Cw=11, No=1), 4096),
+                 (L.make_fc_desc(10, 5, Cw=10, No=6), 4096), (L.make_fc_desc(100, 50, Cw=100, No=50), 4096),
+                 (L.make_fc_desc(10, 5, Cw=10, No=0), 4096)):
+        with pytest.raises(L.HcError) as e:
+            L.hc_fc_partition(d, N)
+        assert e.value.status == L.HC_ERR_INVALID_ARG

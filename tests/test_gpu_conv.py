@@ -158,8 +158,11 @@ def test_conv_argument_errors(L):
         L.hc_conv_ct_pt(other, w, buf, out)           # weights of another context
     assert e.value.status == L.HC_ERR_INVALID_ARG
     with pytest.raises(L.HcError) as e:
-        L.hc_weights_preprocess(ctx, L.make_desc(3, 5, 5, 2, 3, 3, pad=1, stride=2), K)
-    assert e.value.status == L.HC_ERR_UNSUPPORTED
+        L.hc_weights_preprocess(ctx, L.make_desc(3, 5, 5, 2, 3, 3, pad=1, stride=0), K)
+    assert e.value.status == L.HC_ERR_INVALID_ARG
+    with pytest.raises(L.HcError) as e:
+        L.hc_weights_preprocess(ctx, L.make_desc(3, 1, 1, 2, 3, 3, pad=0, stride=2), K)
+    assert e.value.status == L.HC_ERR_INVALID_ARG      # kernel larger than the input
     L.hc_conv_ct_pt(ctx, w, buf, out)                 # all-zero input -> all-zero output
     torch.cuda.synchronize()
     assert int(out.abs().sum()) == 0
