@@ -659,6 +659,18 @@ def run_gb300(args):
         step_full = {"ms_per_layer": statistics.median(sms), "value": geo["products"] / (statistics.median(sms) / 1e3),
                      "unit": UNIT, "slots_per_output": n_slots,
                      "returned_bytes": int(d_slots.numel() * 8 + geo["O"] * nl * N * 8)}
+        # the same step with the extraction fused into the inverse NTT: c0 is never stored in full
+        d_c1 = torch.empty(geo["O"] * nl * N, dtype=torch.int64, device="cuda")
+        d_slots2 = torch.empty_like(d_slots)
+        fs = lambda: L.hc_conv_server_step_sparse(ctx, w, d_in, s_share, s_mask, d_c1, d_slots2, stream)
+        for _ in range(3):
+            fs()
+        sps = _events_ms(fs, 50, stream, flush)
+        step_full["sparse"] = {
+            "ms_per_layer": statistics.median(sps), "value": geo["products"] / (statistics.median(sps) / 1e3),
+            "unit": UNIT, "bit_exact_vs_full_step": bool(torch.equal(d_slots2, d_slots)) and bool(
+                torch.equal(d_c1.view(geo["O"], -1), d_full.view(geo["O"], 2, -1)[:, 1])),
+            "kernels": _kernel_trace(L, fs, "server_step_sparse")}
 
     # the same layer with online NTT preprocessing and with none (Sec. 9's preprocessing modes)
     modes = None

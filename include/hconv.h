@@ -338,6 +338,19 @@ hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w, const uint
                               const uint64_t *d_share, const uint64_t *d_mask, uint64_t *d_ct_out,
                               uint64_t *d_c0_slots, void *cuda_stream);
 
+/* The same step returning only what the client needs (Sec. 6.2: the results
+ * are sparse and only the output coefficients go back; Sec. 7): d_c1_out
+ * [O][L][N] gets the full c1 of every output ciphertext and d_c0_slots
+ * [O][L][S] the masked output slots of c0, bit for bit what
+ * hc_conv_server_step returns.  c0 is never stored in full: the inverse NTT
+ * of the outputs writes the slots directly, so the layer's output writes drop
+ * from O*2*L*N to O*L*(N + S) words.  Device scratch of (I + 2*O)*L*N*8*2
+ * bytes (plus P*L*N*8 for online weights) comes from the allocator.
+ * Errors: as hc_conv_server_step. */
+hc_status hc_conv_server_step_sparse(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in,
+                                     const uint64_t *d_share, const uint64_t *d_mask, uint64_t *d_c1_out,
+                                     uint64_t *d_c0_slots, void *cuda_stream);
+
 /* Checkpoint / resume of preprocessed weights (the paper's server keeps its
  * NTT-preprocessed weights until the model changes, Sec. 8.1).  hc_weights_save
  * writes w (any preprocessing mode) with its ring parameters and an integrity

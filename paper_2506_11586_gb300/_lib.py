@@ -109,6 +109,7 @@ _SIGS = {
     "hc_conv_ct_pt_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_ctpt_mac": (C.c_int, [_P, _P, _P, _P, C.c_size_t, _P, C.c_size_t, _P]),
     "hc_conv_server_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "hc_conv_server_step_sparse": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "hc_plan_create": (C.c_int, [_P, C.c_size_t, C.POINTER(_P)]),
     "hc_plan_run": (C.c_int, [_P, _P]),
     "hc_plan_run_plain": (C.c_int, [_P, _P]),
@@ -421,6 +422,14 @@ def hc_conv_server_step(ctx, w, ct_in, share, mask, ct_out, c0_slots, stream=Non
     _check(lib().hc_conv_server_step(ctx.ptr, w.ptr, _dptr(ct_in), _dptr(share) if share is not None else None,
                                      _dptr(mask) if mask is not None else None, _dptr(ct_out), _dptr(c0_slots),
                                      _stream(stream)))
+
+
+def hc_conv_server_step_sparse(ctx, w, ct_in, share, mask, c1_out, c0_slots, stream=None):
+    """share: device [C][H][W] or None; mask: device [M][Ho][Wo] or None; c1_out: [O][L][N]; c0_slots: [O][L][S]."""
+    _check(lib().hc_conv_server_step_sparse(ctx.ptr, w.ptr, _dptr(ct_in),
+                                            _dptr(share) if share is not None else None,
+                                            _dptr(mask) if mask is not None else None, _dptr(c1_out),
+                                            _dptr(c0_slots), _stream(stream)))
 
 
 def hc_ctpt_mac(ctx, ct, pt_ntt, slots, out, stream=None):

@@ -351,6 +351,7 @@ hc_status build_weights(const hc_ctx *ctx, const hc_conv_desc &eff, const Geom &
 {
     DeviceGuard guard(ctx->device);
     const uint32_t N = ctx->N, L = ctx->L;
+    hc_status st = HC_OK;
 
     std::vector<int8_t> packed;
     // CSR of output terms: output o = m'*B + b sums g < G of (ct g*B + b, pt m'*G + g)
@@ -387,6 +388,11 @@ hc_status build_weights(const hc_ctx *ctx, const hc_conv_desc &eff, const Geom &
     w->P = g.P;
     w->O = g.O;
     w->mode = mode;
+    st = build_slot_table(w);
+    if (st != HC_OK) {
+        hc_free(w);
+        return st;
+    }
     if (mode == HC_WEIGHTS_NO_NTT) {
         // keep the small signed weights of the stride-1 layer; nothing is packed, lifted or transformed
         const size_t kbytes = (size_t)eff.M * eff.C * eff.kh * eff.kw;
@@ -418,7 +424,7 @@ hc_status build_weights(const hc_ctx *ctx, const hc_conv_desc &eff, const Geom &
         e = cudaMemcpyAsync(w->d_term_ptr, term_ptr.data(), term_ptr.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_terms, terms.data(), terms.size() * 4, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(cuda_error(e, "uploading weights"));
-    hc_status st = launch_lift_int8(ctx, d_packed, w->d_pt, g.P, s);
+    st = launch_lift_int8(ctx, d_packed, w->d_pt, g.P, s);
     if (st == HC_OK && mode == HC_WEIGHTS_NTT_OFFLINE) st = launch_ntt_fwd(ctx, w->d_pt, w->d_pt, g.P, s);
     if (st != HC_OK) return fail(st);
     // the host copy must outlive the asynchronous upload
@@ -950,6 +956,7 @@ void hc_free(void *handle)
         dev_free_persistent(w->d_k);
         dev_free_persistent(w->d_term_ptr);
         dev_free_persistent(w->d_terms);
+        dev_free_persistent(w->d_slot_table);
         w->magic = kMagicDead;
         delete w;
     }

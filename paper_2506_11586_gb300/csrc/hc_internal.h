@@ -44,6 +44,25 @@ enum KernelKind {
 };
 constexpr int kNumVariants = 3;
 
+// One output slot of a layer's output ciphertext: coefficient k holds output
+// row n of the ciphertext's No packed rows at block-local position (i, j).
+struct SlotEntry {
+    uint16_t k, n, i, j;
+};
+
+// The inverse transform of a layer's NTT-domain outputs y [O][2][L][N] with the
+// server step's epilogue: c1 stored in full to c1 [O][L][N]; c0 reduced to its
+// S output slots minus Delta * mask into slots [O][L][S] (0 outside the output
+// map or past M).  Output ct o = m'*B + b, block b = bh*Bw + bw.
+struct ExtractArgs {
+    const uint64_t *y;
+    uint64_t *c1;
+    uint64_t *slots;
+    const uint64_t *mask;     // [M][Ho][Wo] residues in [0, t), or null
+    const SlotEntry *table;   // [S]
+    uint32_t O, S, B, Bw, oh, ow, Ho, Wo, No, M;
+};
+
 }  // namespace hc
 
 struct hc_ctx {
@@ -88,11 +107,17 @@ struct hc_weights {
     uint32_t mode;            // hc_weights_mode
     uint64_t *d_pt;           // [P][L][N] NTT domain (offline mode) or coefficient domain (online mode), owned
     int8_t *d_k;              // [M][C][kh][kw] (no-NTT mode), owned
+    hc::SlotEntry *d_slot_table;  // [No*oh*ow] output slots of one output ciphertext (owned)
     uint32_t *d_terms;        // CSR of output terms (owned): see mac kernels
     uint32_t *d_term_ptr;     // [O+1]
 };
 
 namespace hc {
+
+// inverse transform with the server step's output epilogue (ExtractArgs)
+hc_status launch_inv_extract(const hc_ctx *ctx, const ExtractArgs &ex, cudaStream_t s);
+// the output slot table of w (built once per weights handle)
+hc_status build_slot_table(hc_weights *w);
 
 // Geometry of a layer from the caller's descriptor (kind LAYER_CONV: any stride;
 // LAYER_FC: the 1x1 convolution {C,1,1,M,1,1,1,0,Cw,1,1} with No rows per output)
@@ -269,8 +294,10 @@ constexpr uint32_t mix_comps_per_unit(uint32_t logN) { return logN >= 14 ? 1 : 2
 hc_status launch_product_mixed(const MixItem *items, const uint32_t *units, uint32_t n_units, uint32_t *next,
                                cudaStream_t s);
 
-// transform kinds that take a segment table (pseudo-kinds, variant of FWDCT / INVCT)
-constexpr int KK_FWDCT_SEGS = 100, KK_INVCT_SEGS = 101;
+// transform kinds that take a segment table (pseudo-kinds, variant of FWDCT / INVCT),
+// and the inverse transform with the server step's output epilogue (variant of INV)
+constexpr int KK_FWDCT_SEGS = 100, KK_INVCT_SEGS = 101, KK_INV_EXTRACT = 102;
+
 
 // arguments of one launch of a kernel family (unused fields ignored)
 struct LaunchArgs {
@@ -282,6 +309,7 @@ struct LaunchArgs {
     const uint32_t *out_index;
     size_t n;
     bool accumulate;
+    const ExtractArgs *ex;
 };
 template <int LOGN>
 hc_status launch_n(const hc_ctx *ctx, int kind, int variant, const LaunchArgs &a, cudaStream_t s);

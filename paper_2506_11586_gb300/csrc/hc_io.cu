@@ -194,6 +194,11 @@ hc_status hc_weights_load(const hc_ctx *ctx, const char *path, hc_weights **out)
         hc_free(w);
         return set_error(HC_ERR_OOM, "uploading loaded weights failed");
     }
+    const hc_status st = build_slot_table(w);
+    if (st != HC_OK) {
+        hc_free(w);
+        return st;
+    }
     *out = w;
     return HC_OK;
 }

@@ -124,8 +124,8 @@ __device__ __forceinline__ void fwd_task(uint64_t *sm, const uint64_t *src, uint
 // COHERENT loads bypass the non-coherent read-only path, for inputs written
 // earlier by other CTAs of the same launch.  One CTA task.
 template <class Cfg, bool COHERENT = false>
-__device__ __forceinline__ void inv_task(uint64_t *sm, const uint64_t *src, uint64_t *dst, size_t pstride,
-                                         const LimbConst &lc, int tid)
+__device__ __forceinline__ void inv_core(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm, const uint64_t *src,
+                                         size_t pstride, const LimbConst &lc, int tid)
 {
     constexpr int NP = Cfg::NP, C = Cfg::C, N = Cfg::N;
     // coalesced 16-byte loads into shared memory, then the round-0 layout
@@ -141,9 +141,17 @@ __device__ __forceinline__ void inv_task(uint64_t *sm, const uint64_t *src, uint
             sm[p * N + spos<Cfg>(e + 1)] = v.y;
         }
     }
-    uint64_t x[NP][C];
     load_round0<Cfg>(x, sm, tid);
     inv_transform<Cfg>(x, sm, lc, lc.tw_i, tid);
+}
+
+template <class Cfg, bool COHERENT = false>
+__device__ __forceinline__ void inv_task(uint64_t *sm, const uint64_t *src, uint64_t *dst, size_t pstride,
+                                         const LimbConst &lc, int tid)
+{
+    constexpr int NP = Cfg::NP, C = Cfg::C;
+    uint64_t x[NP][C];
+    inv_core<Cfg, COHERENT>(x, sm, src, pstride, lc, tid);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         uint64_t *d = dst + p * pstride;
@@ -174,6 +182,53 @@ k_ntt_inv(const __grid_constant__ NttSegsT<NS> segs)
     const uint32_t limb = sg.limb0 + local / sg.n_groups, grp = local % sg.n_groups;
     const size_t off = ((size_t)grp * Cfg::NP * sg.L + limb) * Cfg::N;
     inv_task<Cfg>(sm, sg.in + off, sg.out + off, (size_t)sg.L * Cfg::N, sg.limbs[limb], threadIdx.x);
+}
+
+// Inverse NTT of a layer's outputs with the server step's epilogue (Sec. 7, Sec.
+// 6.2: only the output coefficients of c0 go back, masked): one CTA per output
+// polynomial (limb-major).  c1 is stored in full; c0 goes through shared memory
+// and only its S output slots are written, each minus Delta * mask.
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
+k_ntt_inv_extract(const __grid_constant__ ExtractArgs ex, const LimbConst *__restrict__ limbs, uint32_t L)
+{
+    static_assert(Cfg::NP == 1, "one polynomial per CTA");
+    extern __shared__ uint64_t sm[];
+    const int tid = threadIdx.x;
+    const uint32_t per_limb = ex.O * 2;
+    const uint32_t limb = blockIdx.x / per_limb, pi = blockIdx.x % per_limb;
+    const uint32_t o = pi >> 1, comp = pi & 1;
+    const LimbConst &lc = limbs[limb];
+    uint64_t x[1][Cfg::C];
+    inv_core<Cfg>(x, sm, ex.y + ((size_t)pi * L + limb) * Cfg::N, 0, lc, tid);
+    if (comp) {
+        uint64_t *d = ex.c1 + ((size_t)o * L + limb) * Cfg::N;
+#pragma unroll
+        for (int r = 0; r < Cfg::C; ++r) d[inv_out_elem<Cfg>(tid, r)] = x[0][r];
+        return;
+    }
+    __syncthreads();  // the transform's last reads of shared memory are done
+#pragma unroll
+    for (int r = 0; r < Cfg::C; ++r) sm[spos<Cfg>(inv_out_elem<Cfg>(tid, r))] = x[0][r];
+    __syncthreads();
+    const uint32_t mp = o / ex.B, b = o % ex.B;
+    const uint32_t row0 = (b / ex.Bw) * ex.oh, col0 = (b % ex.Bw) * ex.ow;
+    const uint64_t q = lc.q;
+    uint64_t *out = ex.slots + ((size_t)o * L + limb) * ex.S;
+    for (uint32_t s = tid; s < ex.S; s += Cfg::T) {
+        const SlotEntry e = ex.table[s];
+        const uint32_t m = mp * ex.No + e.n, row = row0 + e.i, col = col0 + e.j;
+        uint64_t v = 0;
+        if (m < ex.M && row < ex.Ho && col < ex.Wo) {
+            v = sm[spos<Cfg>(e.k)];
+            if (ex.mask) {
+                const uint64_t r = ex.mask[((size_t)m * ex.Ho + row) * ex.Wo + col];
+                const uint64_t dr = canon4(shoup_lazy(r, lc.delta, lc.delta_s, 0ull - q), q);
+                v = v >= dr ? v - dr : v + q - dr;
+            }
+        }
+        out[s] = v;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -563,6 +618,20 @@ hc_status run_mac_intt(const hc_ctx *ctx, const uint64_t *ct_ntt, const uint64_t
 }
 
 template <class Cfg>
+hc_status run_inv_extract(const hc_ctx *ctx, const ExtractArgs &ex, cudaStream_t s)
+{
+    if (ex.O == 0) return HC_OK;
+    auto kern = k_ntt_inv_extract<Cfg>;
+    hc_status st = prepare<Cfg, KK_INV_EXTRACT>(kern, Cfg::SMEM_BYTES);
+    if (st != HC_OK) return st;
+    const size_t items = (size_t)ex.O * 2 * ctx->L;
+    if (items > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "layer too large");
+    ProfileScope ps("k_ntt_inv_extract", s);
+    kern<<<(unsigned)items, Cfg::T, Cfg::SMEM_BYTES, s>>>(ex, ctx->d_limbs, ctx->L);
+    return after_launch("k_ntt_inv_extract");
+}
+
+template <class Cfg>
 hc_status run_product(const hc_ctx *ctx, const uint64_t *ct, const uint64_t *pt_ntt, const uint32_t *out_index,
                       uint64_t *out, size_t n, bool accumulate, cudaStream_t s)
 {
@@ -625,6 +694,7 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
     }
     case KK_MAC: return detail::run_mac_intt<Fused>(ctx, a.in, a.pt, a.terms, a.out, a.n, s);
     case KK_PROD: return detail::run_product<Fused>(ctx, a.in, a.pt, a.out_index, a.out, a.n, a.accumulate, s);
+    case KK_INV_EXTRACT: return detail::run_inv_extract<Single>(ctx, *a.ex, s);
     default: return set_error(HC_ERR_INVALID_ARG, "unknown kernel kind %d", kind);
     }
 }

@@ -238,8 +238,10 @@ hc_status after(const char *what)
 
 hc_status dispatch(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaStream_t s)
 {
-    const int v = kind == KK_FWDCT_SEGS ? ctx->variant[KK_FWDCT]
-                  : kind == KK_INVCT_SEGS ? ctx->variant[KK_INVCT] : ctx->variant[kind];
+    const int v = kind == KK_FWDCT_SEGS    ? ctx->variant[KK_FWDCT]
+                  : kind == KK_INVCT_SEGS  ? ctx->variant[KK_INVCT]
+                  : kind == KK_INV_EXTRACT ? ctx->variant[KK_INV]
+                                           : ctx->variant[kind];
     switch (ctx->logN) {
     case 12: return launch_n<12>(ctx, kind, v, a, s);
     case 13: return launch_n<13>(ctx, kind, v, a, s);
@@ -266,6 +268,13 @@ hc_status launch_ntt_inv(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, s
     a.out = out;
     a.n = n_polys;
     return dispatch(ctx, KK_INV, a, s);
+}
+
+hc_status launch_inv_extract(const hc_ctx *ctx, const ExtractArgs &ex, cudaStream_t s)
+{
+    LaunchArgs a{};
+    a.ex = &ex;
+    return dispatch(ctx, KK_INV_EXTRACT, a, s);
 }
 
 hc_status launch_ntt_fwd_ct(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_ct, cudaStream_t s)

@@ -173,3 +173,91 @@ extern "C" hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w,
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HC_OK : cuda_error(e, "launch k_extract_mask");
 }
+
+namespace hc {
+hc_status build_slot_table(hc_weights *w)
+{
+    const hc_conv_desc &d = w->desc;
+    const uint32_t oh = d.Hw - d.kh + 1, ow = d.Ww - d.kw + 1, span = d.Cw * d.Hw * d.Ww;
+    const uint32_t offset = (d.Cw - 1) * d.Hw * d.Ww + (d.kh - 1) * d.Ww + (d.kw - 1);
+    const size_t S = (size_t)w->No * oh * ow;
+    if (S == 0 || (size_t)w->No * span > w->ctx->N) return set_error(HC_ERR_INVALID_ARG, "invalid layer geometry");
+    std::vector<SlotEntry> t(S);
+    for (uint32_t n = 0; n < w->No; ++n)
+        for (uint32_t i = 0; i < oh; ++i)
+            for (uint32_t j = 0; j < ow; ++j) {
+                SlotEntry &e = t[((size_t)n * oh + i) * ow + j];
+                e.k = (uint16_t)(n * span + offset + i * d.Ww + j);  // < N <= 16384
+                e.n = (uint16_t)n;
+                e.i = (uint16_t)i;
+                e.j = (uint16_t)j;
+            }
+    w->d_slot_table = (SlotEntry *)dev_alloc_persistent(S * sizeof(SlotEntry));
+    if (!w->d_slot_table) return set_error(HC_ERR_OOM, "device allocation of the slot table failed");
+    const cudaError_t e = cudaMemcpy(w->d_slot_table, t.data(), S * sizeof(SlotEntry), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? HC_OK : cuda_error(e, "uploading the slot table");
+}
+}  // namespace hc
+
+// The server step returning only what the client needs (Sec. 6.2, Sec. 7): the
+// full c1 of every output ciphertext and the masked output slots of its c0.
+// The inverse transform writes them directly (k_ntt_inv_extract); c0 is never
+// stored in full.
+extern "C" hc_status hc_conv_server_step_sparse(const hc_ctx *ctx, const hc_weights *w, const uint64_t *d_ct_in,
+                                                const uint64_t *d_share, const uint64_t *d_mask, uint64_t *d_c1_out,
+                                                uint64_t *d_c0_slots, void *cuda_stream)
+{
+    using namespace hc;
+    if (!ctx || ctx->magic != kMagicCtx || !w || w->magic != kMagicWeights)
+        return set_error(HC_ERR_INVALID_ARG, "invalid context or weights");
+    if (w->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "weights were preprocessed for another context");
+    if (!d_ct_in || !d_c1_out || !d_c0_slots) return set_error(HC_ERR_INVALID_ARG, "null buffer");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const StepGeom g = geom_of(w);
+    const size_t LN = (size_t)ctx->L * ctx->N;
+    const size_t in_words = (size_t)w->I * 2 * LN, y_words = (size_t)w->O * 2 * LN;
+    if (w->mode == HC_WEIGHTS_NO_NTT || !conv_job_blocked(ctx, w)) {
+        // no inverse transform to fuse into: the full step into scratch, then c1 out of it
+        Scratch full(s);
+        full.p = dev_alloc(y_words * sizeof(uint64_t), s);
+        if (!full.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+        uint64_t *y = (uint64_t *)full.p;
+        hc_status st = hc_conv_server_step(ctx, w, d_ct_in, d_share, d_mask, y, d_c0_slots, cuda_stream);
+        if (st != HC_OK) return st;
+        HC_CUDA_TRY(cudaMemcpy2DAsync(d_c1_out, LN * sizeof(uint64_t), y + LN, 2 * LN * sizeof(uint64_t),
+                                      LN * sizeof(uint64_t), w->O, cudaMemcpyDeviceToDevice, s));
+        return HC_OK;
+    }
+    hc_status st = check_inputs(ctx, d_ct_in, (size_t)2 * w->I, s);
+    if (st != HC_OK) return st;
+    Scratch xs(s), ys(s), ws(s);
+    xs.p = dev_alloc(in_words * sizeof(uint64_t), s);
+    ys.p = dev_alloc(y_words * sizeof(uint64_t), s);
+    if (!xs.p || !ys.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+    uint64_t *x = (uint64_t *)xs.p, *y = (uint64_t *)ys.p;
+    const uint64_t *src = d_ct_in;
+    if (d_share) {
+        ProfileScope ps("k_share_add", s);
+        k_share_add<<<grid_for(in_words), 256, 0, s>>>(d_ct_in, d_share, x, ctx->d_limbs, ctx->L, ctx->N, g,
+                                                       in_words);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "launch k_share_add");
+        src = x;
+    }
+    st = launch_ntt_fwd_ct(ctx, src, x, w->I, s);  // in place after the share add
+    if (st != HC_OK) return st;
+    const uint64_t *wpt = w->d_pt;
+    if (w->mode == HC_WEIGHTS_NTT_ONLINE) {
+        ws.p = dev_alloc((size_t)w->P * LN * sizeof(uint64_t), s);
+        if (!ws.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+        st = launch_ntt_fwd(ctx, w->d_pt, (uint64_t *)ws.p, w->P, s);
+        if (st != HC_OK) return st;
+        wpt = (const uint64_t *)ws.p;
+    }
+    st = launch_mac_conv(ctx, x, wpt, y, w->G, w->B, w->Mp, s);
+    if (st != HC_OK) return st;
+    ExtractArgs ex{y, d_c1_out, d_c0_slots, d_mask, w->d_slot_table, w->O, g.No * g.oh * g.ow, g.B, g.Bw,
+                   g.oh, g.ow, g.Ho, g.Wo, g.No, g.M};
+    return launch_inv_extract(ctx, ex, s);
+}

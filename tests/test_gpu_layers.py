@@ -74,6 +74,17 @@ def test_strided_full_size_sampled(L, shape):
     assert np.array_equal(got[outs][..., ks], want)
 
 
+def _sparse_matches(L, ctx, w, ct, share, mask, full_out, full_slots):
+    """hc_conv_server_step_sparse returns c1 of the full step's outputs and the same slots."""
+    c1 = torch.full((w.O * ctx.L * ctx.N,), -1, dtype=torch.int64, device="cuda")
+    slots = torch.full((w.O * ctx.L * L.slot_count(w),), -1, dtype=torch.int64, device="cuda")
+    L.hc_conv_server_step_sparse(ctx, w, to_dev(ct), to_dev(share.astype(np.uint64)), to_dev(mask.astype(np.uint64)),
+                                 c1, slots)
+    L.hc_ctx_device_status(ctx)
+    assert np.array_equal(to_host(c1).reshape(w.O, ctx.L, ctx.N), full_out[:, 1])
+    assert np.array_equal(to_host(slots).reshape(full_slots.shape), full_slots)
+
+
 SMALL_STRIDED = [
     (4, 9, 9, 3, 3, 3, 2, 1, 4096, 2),
     (3, 11, 10, 4, 7, 7, 2, 3, 4096, 2),
@@ -127,6 +138,7 @@ def test_strided_server_step_full_parity_modes_and_decryption(L, shape):
         got_out = to_host(out).reshape(p.O, 2, nl, N)
         got_slots = to_host(slots).reshape(p.O, nl, S)
         assert np.array_equal(got_out, want_out) and np.array_equal(got_slots, want_slots)
+        _sparse_matches(L, ctx, w, ct, x_s, r, got_out, got_slots)
     # the client decrypts layer(x_c + x_s) - r at every output
     n = 0
     for m in range(M):
@@ -189,6 +201,7 @@ def test_fc_server_step_full_parity_modes_and_decryption(L, C_, M, N, nl, Cw, No
         L.hc_ctx_device_status(ctx)
         got_out, got_slots = to_host(out).reshape(fp.O, 2, nl, N), to_host(slots).reshape(fp.O, nl, fp.No)
         assert np.array_equal(got_out, want_out) and np.array_equal(got_slots, want_slots)
+        _sparse_matches(L, ctx, w, ct, x_s, r, got_out, got_slots)
     y = layers.fc_mod_t((x_c + x_s) % T_PLAIN, Wm, T_PLAIN)
     for m in range(M):
         mp, k = layers.fc_output_coeff(fp, m)

@@ -95,3 +95,56 @@ def test_server_step_56x56x64_sampled(L):
     y = conv.conv2d_mod_t((x_c + x_s) % T_PLAIN, K, p.pad, T_PLAIN)
     for o in outs:                                   # every slot of these outputs decrypts to y - r
         _check_output(p, params, sk, got_out, got_slots, y, r, o)
+
+
+def _sparse_vs_full(L, ctx, w, ct, share, mask):
+    """hc_conv_server_step_sparse against hc_conv_server_step on the same inputs:
+    c1 of every output and every slot, bit for bit."""
+    nl, N = ctx.L, ctx.N
+    S = L.slot_count(w)
+    out = torch.empty(w.O * 2 * nl * N, dtype=torch.int64, device="cuda")
+    slots = torch.empty(w.O * nl * S, dtype=torch.int64, device="cuda")
+    c1 = torch.full((w.O * nl * N,), -1, dtype=torch.int64, device="cuda")
+    slots2 = torch.full_like(slots, -1)
+    d_in = to_dev(ct)
+    d_share = to_dev(share.astype(np.uint64)) if share is not None else None
+    d_mask = to_dev(mask.astype(np.uint64)) if mask is not None else None
+    L.hc_conv_server_step(ctx, w, d_in, d_share, d_mask, out, slots)
+    L.hc_conv_server_step_sparse(ctx, w, d_in, d_share, d_mask, c1, slots2)
+    L.hc_ctx_device_status(ctx)
+    torch.cuda.synchronize()
+    assert torch.equal(slots2, slots)
+    assert torch.equal(c1.view(w.O, nl * N), out.view(w.O, 2, nl * N)[:, 1])
+    return to_host(c1).reshape(w.O, nl, N), to_host(slots2).reshape(w.O, nl, S)
+
+
+def test_sparse_server_step_matches_full_step_and_oracle(L):
+    p, params, sk, x_c, x_s, K, r, ct = _case(5, 7, 6, 3, 3, 3, 1, 4096, 2, 3, part=(3, 6, 5))
+    ctx = L.hc_ctx_create(p.N, params.moduli, T_PLAIN)
+    d = L.make_desc(p.C, p.H, p.W, p.M, p.kh, p.kw, pad=p.pad, Cw=p.Cw, Hw=p.Hw, Ww=p.Ww)
+    ct1 = conv.share_add(ct, x_s, p, params.moduli, T_PLAIN)
+    want_out = conv.conv_ct_pt(ct1, conv.pack_weights(K, p), p, params.moduli)
+    want_slots = conv.extract_masked(want_out, r, p, params.moduli, T_PLAIN)
+    for mode in range(3):
+        w = L.hc_weights_preprocess_ex(ctx, d, K.astype(np.int8), mode)
+        c1, slots = _sparse_vs_full(L, ctx, w, ct, x_s, r)
+        assert np.array_equal(c1, want_out[:, 1]) and np.array_equal(slots, want_slots), mode
+        _sparse_vs_full(L, ctx, w, ct, None, None)          # no share, no mask
+        w.close()
+    # the client decrypts every returned slot from (slot, c1) alone
+    y = conv.conv2d_mod_t((x_c + x_s) % T_PLAIN, K, p.pad, T_PLAIN)
+    for o in range(p.O):
+        c = np.zeros((2, len(params.moduli), p.N), dtype=np.uint64)
+        c[1] = c1[o]
+        _check_output(p, params, sk, np.stack([c] * p.O), slots, y, r, o)
+
+
+def test_sparse_server_step_56x56x64(L):
+    sh = CONV_56x56x64
+    x_c, K = conv_tensors(sh, seed=2)
+    p, params, sk, x_c, x_s, K, r, ct = _case(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, sh.pad, 8192, 3, 4, x_c=x_c, K=K)
+    ctx = L.hc_ctx_create(8192, params.moduli, T_PLAIN)
+    w = L.hc_weights_preprocess(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), K.astype(np.int8))
+    for v in range(3):                                      # every launch shape of the inverse transform
+        L.hc_ctx_set_variant(ctx, L.KIND_NTT_INV, v)
+        _sparse_vs_full(L, ctx, w, ct, x_s, r)
