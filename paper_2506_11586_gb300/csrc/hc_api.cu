@@ -1,5 +1,6 @@
 // hc_api.cu -- the C ABI of libhconv (include/hconv.h).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -287,6 +288,30 @@ struct ScratchGuard {
 }  // namespace
 
 namespace hc {
+// Per-call scratch comes from the device's default stream-ordered pool.  With
+// the pool's default release threshold (0) every synchronisation hands freed
+// scratch back to the driver and the next call maps it again, which costs
+// more than a small layer's kernels; keep freed scratch cached instead (once
+// per device, and only if nobody has set a threshold).  cudaMemPoolTrimTo
+// releases it.
+void keep_scratch_cached(int device)
+{
+    static std::atomic<uint32_t> done{0};
+    const uint32_t bit = 1u << (device & 31);
+    if (done.fetch_or(bit) & bit) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    uint64_t cur = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur == 0) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+}
+
 size_t conv_scratch_words(const hc_ctx *ctx, const hc_weights *w)
 {
     // NTT-domain inputs, then dependency counters of the fused form (two per 64-bit word)
@@ -566,6 +591,7 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
         cudaGetLastError();
         return set_error(HC_ERR_CUDA, "no CUDA device");
     }
+    keep_scratch_cached(c->device);
 
     // host tables: per limb, forward and inverse twiddles with Shoup companions
     std::vector<ulonglong2> tw((size_t)2 * L * N);

@@ -61,6 +61,7 @@ struct ExtractArgs {
     const uint64_t *mask;     // [M][Ho][Wo] residues in [0, t), or null
     const SlotEntry *table;   // [S]
     uint32_t O, S, B, Bw, oh, ow, Ho, Wo, No, M;
+    uint32_t limb0 = 0, Lc = 0;  // limbs [limb0, limb0 + Lc) only (Lc = 0: all L)
 };
 
 }  // namespace hc
@@ -118,6 +119,9 @@ namespace hc {
 hc_status launch_inv_extract(const hc_ctx *ctx, const ExtractArgs &ex, cudaStream_t s);
 // the output slot table of w (built once per weights handle)
 hc_status build_slot_table(hc_weights *w);
+
+// keep freed per-call scratch cached in the device's default memory pool
+void keep_scratch_cached(int device);
 
 // Geometry of a layer from the caller's descriptor (kind LAYER_CONV: any stride;
 // LAYER_FC: the 1x1 convolution {C,1,1,M,1,1,1,0,Cw,1,1} with No rows per output)
@@ -244,9 +248,14 @@ struct ConvJob {
     uint64_t *ntt;        // scratch: NTT-domain inputs [I][2][L][N]
     bool blocked;         // blocked MAC fits (else fused MAC + inverse NTT)
     const uint64_t *wpt = nullptr;  // NTT-domain weights [P][L][N]; nullptr: the resident ones
+    const ExtractArgs *ex = nullptr;  // set: out is the NTT-domain MAC result and the inverse
+                                      // transform is the server step's epilogue (limb chains only)
 };
 inline const uint64_t *job_weights(const ConvJob &c) { return c.wpt ? c.wpt : c.w->d_pt; }
 bool conv_job_blocked(const hc_ctx *c, const hc_weights *w);
+// launch form 2 for the blocked jobs of one degree: one forward -> MAC -> inverse
+// chain per limb on parallel streams, joined back into s
+hc_status launch_limb_chains(const ConvJob *jobs, size_t n, uint32_t logN, cudaStream_t s);
 // The batched launch sequence of n conv jobs in stream order on s.  Per ring
 // degree, when the first job's context selects the fused form (KK_CONV) and
 // ctr holds enough words (conv_jobs_counter_words): one persistent fused

@@ -196,7 +196,7 @@ k_ntt_inv_extract(const __grid_constant__ ExtractArgs ex, const LimbConst *__res
     extern __shared__ uint64_t sm[];
     const int tid = threadIdx.x;
     const uint32_t per_limb = ex.O * 2;
-    const uint32_t limb = blockIdx.x / per_limb, pi = blockIdx.x % per_limb;
+    const uint32_t limb = ex.limb0 + blockIdx.x / per_limb, pi = blockIdx.x % per_limb;
     const uint32_t o = pi >> 1, comp = pi & 1;
     const LimbConst &lc = limbs[limb];
     uint64_t x[1][Cfg::C];
@@ -624,7 +624,9 @@ hc_status run_inv_extract(const hc_ctx *ctx, const ExtractArgs &ex, cudaStream_t
     auto kern = k_ntt_inv_extract<Cfg>;
     hc_status st = prepare<Cfg, KK_INV_EXTRACT>(kern, Cfg::SMEM_BYTES);
     if (st != HC_OK) return st;
-    const size_t items = (size_t)ex.O * 2 * ctx->L;
+    const uint32_t Lc = ex.Lc ? ex.Lc : ctx->L;
+    if (ex.limb0 + Lc > ctx->L) return set_error(HC_ERR_INVALID_ARG, "limb range out of bounds");
+    const size_t items = (size_t)ex.O * 2 * Lc;
     if (items > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "layer too large");
     ProfileScope ps("k_ntt_inv_extract", s);
     kern<<<(unsigned)items, Cfg::T, Cfg::SMEM_BYTES, s>>>(ex, ctx->d_limbs, ctx->L);

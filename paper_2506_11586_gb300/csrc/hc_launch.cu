@@ -240,7 +240,7 @@ hc_status dispatch(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaStream_
 {
     const int v = kind == KK_FWDCT_SEGS    ? ctx->variant[KK_FWDCT]
                   : kind == KK_INVCT_SEGS  ? ctx->variant[KK_INVCT]
-                  : kind == KK_INV_EXTRACT ? ctx->variant[KK_INV]
+                  : kind == KK_INV_EXTRACT ? ctx->variant[KK_INVCT]
                                            : ctx->variant[kind];
     switch (ctx->logN) {
     case 12: return launch_n<12>(ctx, kind, v, a, s);

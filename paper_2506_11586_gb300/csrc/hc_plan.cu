@@ -332,6 +332,7 @@ hc_status launch_limb_chains(const ConvJob *jobs, size_t n, uint32_t logN, cudaS
     for (uint32_t l = 0; l < maxl; ++l) {
         cudaStream_t sl = l == 0 ? s : pool->st[l - 1];
         for (size_t i0 = 0; i0 < n;) {  // at most kMaxSegs jobs per launch
+            const size_t i0_begin = i0;
             NttSegs fwd{}, inv{};
             std::vector<const hc_ctx *> mctx;
             std::vector<MacLayer> layers;
@@ -345,10 +346,12 @@ hc_status launch_limb_chains(const ConvJob *jobs, size_t n, uint32_t logN, cudaS
                 f.Lc = 1;
                 f.limb0 = l;
                 fwd.s[fwd.n++] = f;
-                NttSeg v{c.out, c.out, c.ctx->d_limbs, c.ctx->L, c.w->O, 0};
-                v.Lc = 1;
-                v.limb0 = l;
-                inv.s[inv.n++] = v;
+                if (!c.ex) {
+                    NttSeg v{c.out, c.out, c.ctx->d_limbs, c.ctx->L, c.w->O, 0};
+                    v.Lc = 1;
+                    v.limb0 = l;
+                    inv.s[inv.n++] = v;
+                }
                 MacLayer ly{c.ntt, job_weights(c), c.out, c.w->G, c.w->B, c.w->Mp};
                 ly.Lc = 1;
                 ly.limb0 = l;
@@ -359,7 +362,15 @@ hc_status launch_limb_chains(const ConvJob *jobs, size_t n, uint32_t logN, cudaS
             if (!first) continue;
             st = launch_ntt_ct_segs(first, fwd, false, sl);
             if (st == HC_OK) st = launch_mac_conv_layers(mctx.data(), layers.data(), layers.size(), sl);
-            if (st == HC_OK) st = launch_ntt_ct_segs(first, inv, true, sl);
+            if (st == HC_OK && inv.n) st = launch_ntt_ct_segs(first, inv, true, sl);
+            for (size_t j = i0_begin; st == HC_OK && j < i; ++j) {  // the server step's epilogue, per job
+                const ConvJob &c = jobs[j];
+                if (!c.ex || c.ctx->logN != logN || !c.blocked || c.ctx->L <= l) continue;
+                ExtractArgs ex = *c.ex;
+                ex.limb0 = l;
+                ex.Lc = 1;
+                st = launch_inv_extract(c.ctx, ex, sl);
+            }
             if (st != HC_OK) return st;
         }
         if (l > 0) HC_CUDA_TRY(cudaEventRecord(pool->ev[l], sl));

@@ -57,35 +57,45 @@ StepGeom geom_of(const hc_weights *w)
 // (a, b) = phase c1 / C0 split by pb (Sec. 8.1 networks; the polyphase split).
 __global__ void k_share_add(const uint64_t *__restrict__ in, const uint64_t *__restrict__ share,
                             uint64_t *__restrict__ out, const LimbConst *__restrict__ limbs, uint32_t L, uint32_t N,
-                            StepGeom g, size_t total)
+                            StepGeom g, uint32_t n_polys)
 {
-    const uint32_t area = g.Hw * g.Ww;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        uint64_t v = in[i];
-        const uint32_t k = (uint32_t)(i % N);
-        const size_t rest = i / N;
-        const uint32_t limb = (uint32_t)(rest % L), comp = (uint32_t)((rest / L) % 2);
-        const uint32_t item = (uint32_t)(rest / ((size_t)2 * L));
-        if (comp == 0 && k < g.Cw * area) {
-            const uint32_t c = k / area, rem = k % area, ii = rem / g.Ww, jj = rem % g.Ww;
-            const uint32_t grp = item / g.B, b = item % g.B;
-            const uint32_t ch1 = grp * g.Cw + c;
-            const uint32_t r = (b / g.Bw) * g.oh + ii, q = (b % g.Bw) * g.ow + jj;  // padded coordinates
-            if (ch1 < g.C1 && r < g.Hpe && q < g.Wpe) {
-                const uint32_t phase = ch1 / g.C0, ch = ch1 % g.C0;
-                const int64_t R = (int64_t)g.s * r + phase / g.pb - g.pad0;
-                const int64_t Q = (int64_t)g.s * q + phase % g.pb - g.pad0;
-                if (R >= 0 && R < g.H0 && Q >= 0 && Q < g.W0) {
-                    const uint64_t x = share[((size_t)ch * g.H0 + R) * g.W0 + Q];
-                    const LimbConst &lc = limbs[limb];
-                    const uint64_t qm = lc.q;
-                    const uint64_t dx = canon4(shoup_lazy(x, lc.delta, lc.delta_s, 0ull - qm), qm);
-                    v = csub(v + dx, qm);
+    const uint32_t area = g.Hw * g.Ww, span = g.Cw * area;
+    for (uint32_t pi = blockIdx.y; pi < n_polys; pi += gridDim.y) {  // poly (item, component, limb)
+        const uint32_t limb = pi % L, comp = (pi / L) & 1, item = pi / (2 * L);
+        const uint64_t *src = in + (size_t)pi * N;
+        uint64_t *dst = out + (size_t)pi * N;
+        const uint32_t grp = item / g.B, b = item % g.B;
+        const uint32_t r0 = (b / g.Bw) * g.oh, q0 = (b % g.Bw) * g.ow;  // block origin, padded coordinates
+        const LimbConst &lc = limbs[limb];
+        const uint64_t qm = lc.q;
+        for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+            uint64_t v = src[k];
+            if (comp == 0 && k < span) {
+                const uint32_t c = k / area, rem = k - c * area, ii = rem / g.Ww, jj = rem - ii * g.Ww;
+                const uint32_t ch1 = grp * g.Cw + c, r = r0 + ii, q = q0 + jj;
+                if (ch1 < g.C1 && r < g.Hpe && q < g.Wpe) {
+                    const uint32_t phase = ch1 / g.C0, ch = ch1 - phase * g.C0;
+                    const int64_t R = (int64_t)g.s * r + phase / g.pb - g.pad0;
+                    const int64_t Q = (int64_t)g.s * q + phase % g.pb - g.pad0;
+                    if (R >= 0 && R < g.H0 && Q >= 0 && Q < g.W0) {
+                        const uint64_t x = share[((size_t)ch * g.H0 + R) * g.W0 + Q];
+                        const uint64_t dx = canon4(shoup_lazy(x, lc.delta, lc.delta_s, 0ull - qm), qm);
+                        v = csub(v + dx, qm);
+                    }
                 }
             }
+            dst[k] = v;
         }
-        out[i] = v;
     }
+}
+
+// launch k_share_add over the n_polys polynomials of [I][2][L][N]
+cudaError_t share_add(const hc_ctx *ctx, const uint64_t *in, const uint64_t *share, uint64_t *out, const StepGeom &g,
+                      uint32_t n_polys, cudaStream_t s)
+{
+    const dim3 grid((ctx->N + 1023) / 1024, n_polys < 65535 ? n_polys : 65535);
+    k_share_add<<<grid, 256, 0, s>>>(in, share, out, ctx->d_limbs, ctx->L, ctx->N, g, n_polys);
+    return cudaGetLastError();
 }
 
 // slots[o][l][s] = c0[n*span + offset + i*Ww + j] - Delta * r[m][row][col] for
@@ -158,9 +168,7 @@ extern "C" hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w,
         if (!scratch.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
         uint64_t *shared_in = (uint64_t *)scratch.p;
         ProfileScope ps("k_share_add", s);
-        k_share_add<<<grid_for(in_words), 256, 0, s>>>(d_ct_in, d_share, shared_in, ctx->d_limbs, ctx->L, ctx->N, g,
-                                                       in_words);
-        cudaError_t e = cudaGetLastError();
+        const cudaError_t e = share_add(ctx, d_ct_in, d_share, shared_in, g, 2 * w->I * ctx->L, s);
         if (e != cudaSuccess) return cuda_error(e, "launch k_share_add");
         src = shared_in;
     }
@@ -239,14 +247,10 @@ extern "C" hc_status hc_conv_server_step_sparse(const hc_ctx *ctx, const hc_weig
     const uint64_t *src = d_ct_in;
     if (d_share) {
         ProfileScope ps("k_share_add", s);
-        k_share_add<<<grid_for(in_words), 256, 0, s>>>(d_ct_in, d_share, x, ctx->d_limbs, ctx->L, ctx->N, g,
-                                                       in_words);
-        cudaError_t e = cudaGetLastError();
+        const cudaError_t e = share_add(ctx, d_ct_in, d_share, x, g, 2 * w->I * ctx->L, s);
         if (e != cudaSuccess) return cuda_error(e, "launch k_share_add");
         src = x;
     }
-    st = launch_ntt_fwd_ct(ctx, src, x, w->I, s);  // in place after the share add
-    if (st != HC_OK) return st;
     const uint64_t *wpt = w->d_pt;
     if (w->mode == HC_WEIGHTS_NTT_ONLINE) {
         ws.p = dev_alloc((size_t)w->P * LN * sizeof(uint64_t), s);
@@ -255,9 +259,15 @@ extern "C" hc_status hc_conv_server_step_sparse(const hc_ctx *ctx, const hc_weig
         if (st != HC_OK) return st;
         wpt = (const uint64_t *)ws.p;
     }
-    st = launch_mac_conv(ctx, x, wpt, y, w->G, w->B, w->Mp, s);
-    if (st != HC_OK) return st;
     ExtractArgs ex{y, d_c1_out, d_c0_slots, d_mask, w->d_slot_table, w->O, g.No * g.oh * g.ow, g.B, g.Bw,
                    g.oh, g.ow, g.Ho, g.Wo, g.No, g.M};
+    if (ctx->variant[KK_CONV] == 2) {
+        // launch form 2: one forward -> MAC -> epilogue chain per limb on parallel streams
+        ConvJob job{ctx, w, src, y, x, true, wpt, &ex};
+        return launch_limb_chains(&job, 1, ctx->logN, s);
+    }
+    st = launch_ntt_fwd_ct(ctx, src, x, w->I, s);  // in place after the share add
+    if (st == HC_OK) st = launch_mac_conv(ctx, x, wpt, y, w->G, w->B, w->Mp, s);
+    if (st != HC_OK) return st;
     return launch_inv_extract(ctx, ex, s);
 }

@@ -145,6 +145,9 @@ def test_sparse_server_step_56x56x64(L):
     p, params, sk, x_c, x_s, K, r, ct = _case(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, sh.pad, 8192, 3, 4, x_c=x_c, K=K)
     ctx = L.hc_ctx_create(8192, params.moduli, T_PLAIN)
     w = L.hc_weights_preprocess(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), K.astype(np.int8))
-    for v in range(3):                                      # every launch shape of the inverse transform
-        L.hc_ctx_set_variant(ctx, L.KIND_NTT_INV, v)
-        _sparse_vs_full(L, ctx, w, ct, x_s, r)
+    for form in (0, 2):                                     # three launches; per-limb chains on side streams
+        L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, form)
+        for v in range(3):                                  # every launch shape of the inverse transform
+            L.hc_ctx_set_variant(ctx, L.KIND_NTT_INV_CT, v)
+            _sparse_vs_full(L, ctx, w, ct, x_s, r)
+            _sparse_vs_full(L, ctx, w, ct, None, None)
