@@ -594,7 +594,10 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
     keep_scratch_cached(c->device);
 
     // host tables: per limb, forward and inverse twiddles with Shoup companions
-    std::vector<ulonglong2> tw((size_t)2 * L * N);
+    // per limb: forward, inverse, then the rearranged tables (inverse first round,
+    // forward last round) for LOGC = 3, 4, 5
+    constexpr uint32_t kTablesPerLimb = 8;
+    std::vector<ulonglong2> tw((size_t)kTablesPerLimb * L * N);
     std::vector<LimbConst> lcs(L);
     std::vector<uint64_t> delta(L);
     delta_residues(moduli, L, t, delta.data());
@@ -608,8 +611,8 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
         const uint64_t psi_inv = powmod_u64(psi, q - 2, q);
         c->q[i] = q;
         c->psi[i] = psi;
-        ulonglong2 *f = tw.data() + (size_t)(2 * i) * N;
-        ulonglong2 *b = tw.data() + (size_t)(2 * i + 1) * N;
+        ulonglong2 *f = tw.data() + (size_t)(kTablesPerLimb * i) * N;
+        ulonglong2 *b = tw.data() + (size_t)(kTablesPerLimb * i + 1) * N;
         // powers psi^j and psi^-j in natural order, then scattered to bit-reversed slots
         uint64_t pf = 1, pb = 1;
         for (uint32_t j = 0; j < N; ++j) {
@@ -620,6 +623,30 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
             b[k].y = shoup_companion(pb, q);
             pf = mulmod_u64(pf, psi, q);
             pb = mulmod_u64(pb, psi_inv, q);
+        }
+        // first inverse register round with 2^lc residues per thread (thread t, stage s,
+        // group g uses b[(N >> (s+1)) + t*2^(lc-1-s) + g]), rearranged for coalesced reads
+        for (uint32_t lcg = 3; lcg <= 5 && lcg < c->logN; ++lcg) {
+            ulonglong2 *r0 = tw.data() + (size_t)(kTablesPerLimb * i + 2 + (lcg - 3)) * N;
+            const uint32_t T = N >> lcg;
+            for (uint32_t st = 0; st < lcg; ++st) {
+                const uint32_t ngrp = 1u << (lcg - 1 - st), off = N - (N >> st);
+                for (uint32_t g = 0; g < ngrp; ++g)
+                    for (uint32_t tt = 0; tt < T; ++tt) r0[off + g * T + tt] = b[(N >> (st + 1)) + tt * ngrp + g];
+            }
+            // last forward register round (stages S0 .. log2 N - 1, SUBS sub-transforms per
+            // thread): thread t, sub-transform v, stage S0 + sig, group lam uses
+            // f[2^(S0+sig) + (t*SUBS + v)*2^sig + lam]
+            ulonglong2 *rl = tw.data() + (size_t)(kTablesPerLimb * i + 5 + (lcg - 3)) * N;
+            const uint32_t nr = (c->logN + lcg - 1) / lcg, S0 = (nr - 1) * lcg, K = c->logN - S0;
+            const uint32_t subs = 1u << (lcg - K);
+            for (uint32_t sig = 0; sig < K; ++sig) {
+                const uint32_t st = S0 + sig, off = (1u << st) - (1u << S0);
+                for (uint32_t v = 0; v < subs; ++v)
+                    for (uint32_t lam = 0; lam < (1u << sig); ++lam)
+                        for (uint32_t tt = 0; tt < T; ++tt)
+                            rl[off + ((v << sig) + lam) * T + tt] = f[(1u << st) + ((tt * subs + v) << sig) + lam];
+            }
         }
         LimbConst &lc = lcs[i];
         memset(&lc, 0, sizeof(lc));
@@ -649,8 +676,9 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
         return set_error(HC_ERR_OOM, "device allocation of context tables failed");
     }
     for (uint32_t i = 0; i < L; ++i) {
-        lcs[i].tw_f = (const ulonglong2 *)c->d_tables + (size_t)(2 * i) * N;
-        lcs[i].tw_i = (const ulonglong2 *)c->d_tables + (size_t)(2 * i + 1) * N;
+        lcs[i].tw_f = (const ulonglong2 *)c->d_tables + (size_t)(kTablesPerLimb * i) * N;
+        lcs[i].tw_i = (const ulonglong2 *)c->d_tables + (size_t)(kTablesPerLimb * i + 1) * N;
+        lcs[i].tw_r = (const ulonglong2 *)c->d_tables + (size_t)(kTablesPerLimb * i + 2) * N;
     }
     cudaError_t e = cudaMemcpy(c->d_tables, tw.data(), c->table_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_limbs, lcs.data(), sizeof(LimbConst) * L, cudaMemcpyHostToDevice);

@@ -31,7 +31,13 @@ struct LimbConst {
     const ulonglong2 *tw_i;   // [N] {psi^-rev(k), companion}
     uint64_t delta, delta_s;  // BFV scale floor(Q/t) mod q (Q = product of all limbs), companion
     uint64_t special_c;       // c when q = 2^50 - c with 0 < c < 2^22 (cheaper MAC reduction), else 0
-    uint64_t pad_[3];         // 128-byte stride
+    // Twiddles of the register rounds in which every thread needs its own ones,
+    // rearranged so that the threads of a warp read consecutive entries, for
+    // transforms with 2^LOGC residues per thread (T = N >> LOGC threads): table
+    // tw_r + (3*d + LOGC - 3)*N, d = 0 inverse (first round), d = 1 forward (last
+    // round); layouts in hc_ntt.cuh.  Tables with LOGC >= log2 N stay unset.
+    const ulonglong2 *tw_r;
+    uint64_t pad_[2];         // 128-byte stride
 };
 static_assert(sizeof(LimbConst) == 128, "LimbConst is 128 bytes");
 

@@ -95,7 +95,7 @@ __device__ __forceinline__ void fwd_task(uint64_t *sm, const uint64_t *src, uint
 #pragma unroll
         for (int r = 0; r < C; ++r) x[p][r] = __ldg(src + p * pstride + tid + r * T);
     }
-    fwd_transform<Cfg>(x, sm, lc.tw_f, q, tid);
+    fwd_transform<Cfg>(x, sm, lc.tw_f, lc.tw_r, q, tid);
 
     const uint32_t ones = (uint32_t)lc.one_s;
     const uint64_t nq = 0ull - q;
@@ -423,7 +423,7 @@ __device__ __forceinline__ void product_task(uint64_t *sm, const uint64_t *__res
 #pragma unroll
         for (int r = 0; r < C; ++r) x[p][r] = __ldg(src + tid + r * T);
     }
-    fwd_transform<Cfg>(x, sm, lc.tw_f, q, tid);  // lazy values < 57 q, contiguous layout
+    fwd_transform<Cfg>(x, sm, lc.tw_f, lc.tw_r, q, tid);  // lazy values < 57 q, contiguous layout
 
     const uint64_t nq = 0ull - q, r64 = lc.r64, r64_s = lc.r64_s;
     const uint32_t ones = (uint32_t)lc.one_s;

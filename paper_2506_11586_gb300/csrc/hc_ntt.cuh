@@ -20,6 +20,12 @@
 //            inputs are < 2^s q and X - Y + 2^s q < 2^(s+1) q <= 2^64; the last
 //            stage's Shoup steps (N^-1 merged) and two corrections give
 //            canonical output.
+// Twiddle loads: in the inverse's first round and the forward's last round
+// every thread needs its own twiddles (N/2 distinct ones in the inverse's
+// first stage); read from the natural tables a warp's 32 loads would hit 32
+// lines, so those rounds read context tables rearranged so that a warp's
+// loads are consecutive (LimbConst::tw_r); the other rounds share each
+// twiddle among neighbouring threads and read the natural tables.
 // Shared-memory layout: element e of polynomial p lives at word
 // p * N + (e ^ ((e >> LOGC) & 15)); the XOR swizzle makes every 8-byte
 // access pattern below conflict-free (the 16 threads of each half-warp touch
@@ -100,14 +106,21 @@ __device__ __forceinline__ void static_for(F &&f)
 // ---- one forward round: K Cooley-Tukey stages in registers ---------------------
 template <class Cfg, int R, int SIG>
 __device__ __forceinline__ void fwd_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const ulonglong2 *__restrict__ tw,
-                                          uint64_t q, int v, int g0)
+                                          const ulonglong2 *__restrict__ twr, uint64_t q, int v, int g0, int tid)
 {
     using RS = RoundShape<Cfg, R>;
+    static_assert(Cfg::LOGC >= 3 && Cfg::LOGC <= 5, "last-round tables exist for LOGC = 3, 4, 5");
     constexpr int half = RS::KK >> (SIG + 1);
+    constexpr bool last = R == Cfg::NROUNDS - 1;  // every thread has its own twiddles (g0 = tid*SUBS + v)
     const uint64_t nq = 0ull - q, q4 = 4 * q;
 #pragma unroll
     for (int lam = 0; lam < (1 << SIG); ++lam) {
-        const ulonglong2 w = __ldg(tw + (1 << (RS::S0 + SIG)) + (g0 << SIG) + lam);
+        // last round: the rearranged table, stage S0 + SIG at [2^(S0+SIG) - 2^S0],
+        // entry ((v << SIG) + lam)*T + tid, so that a warp reads consecutive entries
+        const ulonglong2 w =
+            last ? __ldg(twr + (size_t)(3 + Cfg::LOGC - 3) * Cfg::N + ((1 << (RS::S0 + SIG)) - (1 << RS::S0)) +
+                         ((v << SIG) + lam) * Cfg::T + tid)
+                 : __ldg(tw + (1 << (RS::S0 + SIG)) + (g0 << SIG) + lam);
 #pragma unroll
         for (int jj = 0; jj < half; ++jj) {
             const int j = v * RS::KK + lam * 2 * half + jj;
@@ -123,15 +136,15 @@ __device__ __forceinline__ void fwd_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
 }
 
 template <class Cfg, int R>
-__device__ __forceinline__ void fwd_round(uint64_t (&x)[Cfg::NP][Cfg::C],
-                                          const ulonglong2 *__restrict__ tw, uint64_t q, int tid)
+__device__ __forceinline__ void fwd_round(uint64_t (&x)[Cfg::NP][Cfg::C], const ulonglong2 *__restrict__ tw,
+                                          const ulonglong2 *__restrict__ twr, uint64_t q, int tid)
 {
     using RS = RoundShape<Cfg, R>;
     constexpr int S = Cfg::N >> (RS::S0 + RS::K);
     static_for<0, RS::SUBS>([&](auto vc) {
         constexpr int v = decltype(vc)::value;
         const int g0 = (tid * RS::SUBS + v) / S;
-        static_for<0, RS::K>([&](auto sc) { fwd_stage<Cfg, R, decltype(sc)::value>(x, tw, q, v, g0); });
+        static_for<0, RS::K>([&](auto sc) { fwd_stage<Cfg, R, decltype(sc)::value>(x, tw, twr, q, v, g0, tid); });
     });
 }
 
@@ -141,6 +154,7 @@ __device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
                                           const ulonglong2 *__restrict__ tw, int v, int blk)
 {
     using RS = RoundShape<Cfg, R>;
+    static_assert(Cfg::LOGC >= 3 && Cfg::LOGC <= 5, "first-round tables exist for LOGC = 3, 4, 5");
     constexpr int s = RS::S0 + SIG;  // global stage
     constexpr int dist = 1 << SIG;
     constexpr int ngrp = RS::KK >> (SIG + 1);
@@ -164,7 +178,11 @@ __device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
     } else {
 #pragma unroll
         for (int grp = 0; grp < ngrp; ++grp) {
-            const ulonglong2 w = __ldg(tw + (Cfg::N >> (s + 1)) + blk * ngrp + grp);
+            // first round: blk is the thread index, and the rearranged table gives the
+            // warp consecutive entries; later rounds share each twiddle across threads
+            const ulonglong2 w =
+                R == 0 ? __ldg(lc.tw_r + (size_t)(Cfg::LOGC - 3) * Cfg::N + (Cfg::N - (Cfg::N >> s)) + grp * Cfg::T + blk)
+                       : __ldg(tw + (Cfg::N >> (s + 1)) + blk * ngrp + grp);
 #pragma unroll
             for (int jj = 0; jj < dist; ++jj) {
                 const int j = v * RS::KK + grp * 2 * dist + jj;
@@ -237,12 +255,13 @@ __device__ __forceinline__ void inv_exchange(uint64_t (&x)[Cfg::NP][Cfg::C], uin
 // last-round layout (element tid*C + r, contiguous) on exit.
 template <class Cfg, int R = 0>
 __device__ __forceinline__ void fwd_transform(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm,
-                                              const ulonglong2 *__restrict__ tw, uint64_t q, int tid)
+                                              const ulonglong2 *__restrict__ tw, const ulonglong2 *__restrict__ twr,
+                                              uint64_t q, int tid)
 {
-    fwd_round<Cfg, R>(x, tw, q, tid);
+    fwd_round<Cfg, R>(x, tw, twr, q, tid);
     if constexpr (R + 1 < Cfg::NROUNDS) {
         fwd_exchange<Cfg, R>(x, sm, tid);
-        fwd_transform<Cfg, R + 1>(x, sm, tw, q, tid);
+        fwd_transform<Cfg, R + 1>(x, sm, tw, twr, q, tid);
     }
 }
 
