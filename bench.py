@@ -1,9 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the homomorphic-convolution hot path (SecONNds, arXiv 2506.11586, Sec. 6.2).
 
-One step = one online HE convolution layer through the C ABI (hc_conv_ct_pt):
-forward NTT of every input ciphertext, NTT-domain multiply-accumulate against
-the resident NTT-preprocessed weights, inverse NTT of the outputs.  Workload:
+One step = one online HE convolution layer through the C ABI: forward NTT of
+every input ciphertext, NTT-domain multiply-accumulate against the resident
+NTT-preprocessed weights, inverse NTT of the outputs -- by default the layer as
+a one-item plan (hc_plan_run) replayed from the CUDA graph the plan captures,
+with --step-api direct one hc_conv_ct_pt call; the line carries the other entry
+point's time too.  Workload:
 56x56x64 activations -> 64 output channels, 3x3, stride 1, pad 1, packed into
 N = 8192 polynomials over three 50-bit primes (I = 32 input ciphertexts,
 P = 512 weight plaintexts, O = 256 output ciphertexts, 2048 ct x pt products).
@@ -66,6 +69,8 @@ def parse():
     ap.add_argument("--conv-form", type=int, default=None, choices=[0, 1, 2],
                     help="force the layer's launch form instead of the autotuned one")
     ap.add_argument("--batched-reps", type=int, default=20)
+    ap.add_argument("--step-api", default="direct", choices=["direct", "plan"],
+                    help="timed step: a one-layer plan replayed from a CUDA graph, or one hc_conv_ct_pt call")
     ap.add_argument("--no-networks", action="store_true",
                     help="skip the whole-network plans (SqueezeNet-1.1 and ResNet-50, every linear layer)")
     ap.add_argument("--no-batched-plain", action="store_true", help="skip the one-launch-per-product comparisons")
@@ -518,13 +523,34 @@ def run_gb300(args):
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
+    def direct_step():
         L.hc_conv_ct_pt(ctx, w, d_in, d_out, stream)
+
+    # the timed step: the layer as a one-item plan, replayed from the CUDA graph the
+    # plan captures on its second run (--step-api direct: one hc_conv_ct_pt call)
+    plan_step = None
+    if args.step_api == "plan":
+        plan_step = L.hc_plan_create([L.work_conv(ctx, w, d_in, d_out)])
+
+        def step():
+            L.hc_plan_run(plan_step, stream)
+    else:
+        step = direct_step
 
     for _ in range(max(3, args.warmup)):
         flush.zero_()
         step()
     torch.cuda.synchronize()
+    # the library's kernels per step, counted by its trace on one untimed step (the trace
+    # records CUDA events around every launch, so it stays off in the timed region)
+    L.hc_profile_collect()
+    L.hc_profile_enable(True)
+    direct_step()
+    torch.cuda.synchronize()
+    L.hc_profile_enable(False)
+    launches_per_step = sum(v[0] for v in L.hc_profile_collect().values())
+    if plan_step is not None:
+        launches_per_step = L.hc_plan_info(plan_step)[2]
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sampler = ClockSampler(local)
@@ -532,18 +558,14 @@ def run_gb300(args):
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)                        # let the sampler attach before the timed region
-    L.hc_profile_collect()
-    L.hc_profile_enable(True)
     for k in range(args.steps):
         flush.zero_()                      # L2 flush between steps, outside the timed events
         ev[k][0].record(stream)
         step()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
-    L.hc_profile_enable(False)
     replicas.barrier()
     clocks = sampler.stop()
-    prof = L.hc_profile_collect()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     max_total_ms = replicas.reduce_max(total_ms)
@@ -554,22 +576,26 @@ def run_gb300(args):
     # overlap and a launch's duration no longer isolates its own work; the per-kernel
     # figures are then taken from a second traced pass of the same layer with the form
     # of one launch per phase (same stream, same L2 flush), and the line says so.
-    launches = sum(v[0] for v in prof.values())
+    # Per-kernel figures come from a second, traced pass of the same layer (same stream,
+    # same L2 flush) in the form of one launch per phase: the timed region is not traced,
+    # and the tuned form runs each limb's chain on its own stream, where kernels overlap
+    # and a launch's duration no longer isolates its own work.
+    launches = launches_per_step * args.steps
     form = L.hc_ctx_get_variant(ctx, L.KIND_CONV_FORM)
-    rprof, rsteps, measured_with = prof, args.steps, "the timed region"
-    if form != 0:
-        L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, 0)
-        rsteps = min(args.steps, 300)
-        step()
-        torch.cuda.synchronize()
-        L.hc_profile_collect()
-        L.hc_profile_enable(True)
-        rms = _events_ms(step, rsteps, stream, flush)
-        L.hc_profile_enable(False)
-        rprof = L.hc_profile_collect()
-        L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, form)
-        measured_with = ("a second traced pass of %d steps with one launch per phase (%.4f ms per layer); "
-                         "the timed region ran launch form %d" % (rsteps, statistics.median(rms), form))
+    L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, 0)
+    rsteps = min(args.steps, 300)
+    direct_step()
+    torch.cuda.synchronize()
+    L.hc_profile_collect()
+    L.hc_profile_enable(True)
+    rms = _events_ms(direct_step, rsteps, stream, flush)
+    L.hc_profile_enable(False)
+    rprof = L.hc_profile_collect()
+    L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, form)
+    measured_with = ("a traced pass of %d direct calls with one launch per phase (%.4f ms per layer); "
+                     "the timed region ran %s with launch form %d, untraced"
+                     % (rsteps, statistics.median(rms),
+                        "graph replays of a one-layer plan" if plan_step is not None else "direct calls", form))
     kname = max(rprof, key=lambda k: rprof[k][1])
     kl, kms = rprof[kname]
     k_avg_ms = kms / kl
@@ -594,17 +620,24 @@ def run_gb300(args):
                      "measured_with": measured_with})
     layer_gbs = bytes_layer * args.steps / (total_ms / 1000.0) / 1e9
 
-    # the same layer as a one-item plan replayed from a CUDA graph (same stream, same L2 flush)
-    graph = None
+    # the other entry point on the same layer (same stream, same L2 flush): direct
+    # hc_conv_ct_pt calls when the timed region replayed the plan, and vice versa
+    alt = None
     if args.plain_steps > 0:
-        plan1 = L.hc_plan_create([L.work_conv(ctx, w, d_in, d_out)])
-        for _ in range(3):
-            L.hc_plan_run(plan1, stream)
-        gms = _events_ms(lambda: L.hc_plan_run(plan1, stream), 200, stream, flush)
-        graph = {"ms_per_step": statistics.median(gms), "p99_ms": sorted(gms)[int(0.99 * (len(gms) - 1))],
-                 "value": geo["products"] / (statistics.median(gms) / 1e3), "unit": UNIT,
-                 "launches_per_step": L.hc_plan_info(plan1)[2]}
-        plan1.close()
+        if plan_step is not None:
+            for _ in range(3):
+                direct_step()
+            gms = _events_ms(direct_step, 200, stream, flush)
+            alt = {"api": "hc_conv_ct_pt (direct call)"}
+        else:
+            plan1 = L.hc_plan_create([L.work_conv(ctx, w, d_in, d_out)])
+            for _ in range(3):
+                L.hc_plan_run(plan1, stream)
+            gms = _events_ms(lambda: L.hc_plan_run(plan1, stream), 200, stream, flush)
+            plan1.close()
+            alt = {"api": "hc_plan_run (one-layer plan, graph replay)"}
+        alt.update({"ms_per_step": statistics.median(gms), "p99_ms": sorted(gms)[int(0.99 * (len(gms) - 1))],
+                    "value": geo["products"] / (statistics.median(gms) / 1e3), "unit": UNIT})
 
     # plain one-launch-per-product path on the same inputs (comparison)
     plain = None
@@ -718,16 +751,22 @@ def run_gb300(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "L": nl, "I": geo["I"], "P": geo["P"], "O": geo["O"],
                    "products_per_layer": geo["products"], "partition": [geo["Cw"], geo["Hw"], geo["Ww"]],
-                   "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps"},
+                   "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps",
+                   "step_api": ("hc_plan_run: one-layer plan replayed from a CUDA graph" if plan_step is not None
+                                else "hc_conv_ct_pt: direct call")},
         "p50_ms": statistics.median(step_ms), "p99_ms": p99, "layer_gbs": layer_gbs,
-        "roofline": roofline, "graph": graph, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
+        "roofline": roofline, "other_entry_point": alt, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
         "server_step": step_full, "preprocessing_modes": modes, "batched": batched, "networks": networks,
-        "serving": serving, "gpu_launches": launches, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+        "serving": serving, "gpu_launches": launches,
+        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in rprof.items()},
+        "kernels_from": measured_with.split(";")[0],
         "launch_form": form,
         "offline_weights_s": offline_s, "launch_variants": tuned, "clocks": clocks, "device": torch.cuda.get_device_name(local),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if plan_step is not None:
+        plan_step.close()
     w.close()
     ctx.close()
     replicas.shutdown()
