@@ -671,10 +671,25 @@ def run_gb300(args):
             L.hc_conv_ct_pt_host(ctx, w, h_in, h_out, stream)   # H2D, layer, D2H, synchronise
             ts.append(time.perf_counter() - t0)
         e2e_s = replicas.reduce_max(sum(ts))
+        e2e_exact = bool(torch.equal(h_out, d_out.cpu()))
+        # the copies alone, for the bound: pinned host <-> device, same byte counts
+        d_tmp = torch.empty_like(d_out)
+
+        def copy_gbs(dst, src, nbytes):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(5):
+                dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            return 5 * nbytes / (time.perf_counter() - t0) / 1e9
+        h2d_gbs = copy_gbs(d_in.new_empty(d_in.shape), h_in, ct_host.nbytes)
+        d2h_gbs = copy_gbs(h_out, d_tmp, h_out.numel() * 8)
         e2e = {"value": replicas.whole_job_throughput(geo["products"] * args.e2e_steps, world, e2e_s),
+               "copy_h2d_gbs": h2d_gbs, "copy_d2h_gbs": d2h_gbs,
                "unit": UNIT, "h2d_bytes_per_step": int(ct_host.nbytes),
                "d2h_bytes_per_step": int(h_out.numel() * 8), "ms_per_step": 1000 * statistics.mean(ts),
-               "bit_exact_vs_device": bool(torch.equal(h_out, d_out.cpu()))}
+               "bit_exact_vs_device": e2e_exact}
 
     # the server's whole step on the same layer: share add, convolution, output mask, slot extraction
     step_full = None

@@ -278,6 +278,29 @@ void pack_weights(const hc_conv_desc &d, const Geom &g, uint32_t No, uint32_t N,
         }
 }
 
+// output-channel blocks of the pipelined host-buffer convolution
+constexpr uint32_t kHostChunks = 4;
+
+// per host thread and device: a copy stream and its events (made once, kept)
+struct CopyLane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev[kHostChunks + 1] = {};
+};
+
+hc_status copy_lane(CopyLane **out)
+{
+    static thread_local CopyLane lanes[32];
+    int dev = 0;
+    HC_CUDA_TRY(cudaGetDevice(&dev));
+    CopyLane &l = lanes[dev & 31];
+    if (!l.st) {
+        HC_CUDA_TRY(cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking));
+        for (auto &e : l.ev) HC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    *out = &l;
+    return HC_OK;
+}
+
 struct ScratchGuard {
     void *p = nullptr;
     cudaStream_t s;
@@ -919,18 +942,53 @@ hc_status hc_conv_ct_pt_host(const hc_ctx *ctx, const hc_weights *w, const uint6
                              void *cuda_stream)
 {
     if (!ctx_ok(ctx) || !weights_ok(w)) return set_error(HC_ERR_INVALID_ARG, "invalid context or weights");
+    if (w->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "weights were preprocessed for another context");
     if (!h_ct_in || !h_ct_out) return set_error(HC_ERR_INVALID_ARG, "null ciphertext buffer");
     DeviceGuard g(ctx->device);
     cudaStream_t s = as_stream(cuda_stream);
-    const size_t ct_bytes = (size_t)2 * ctx->L * ctx->N * sizeof(uint64_t);
-    ScratchGuard din(s), dout(s);
+    const size_t ct_words = (size_t)2 * ctx->L * ctx->N, ct_bytes = ct_words * sizeof(uint64_t);
+    ScratchGuard din(s), dout(s), dntt(s);
     din.p = dev_alloc(w->I * ct_bytes, s);
     dout.p = dev_alloc(w->O * ct_bytes, s);
     if (!din.p || !dout.p) return set_error(HC_ERR_OOM, "device buffer allocation failed");
     HC_CUDA_TRY(cudaMemcpyAsync(din.p, h_ct_in, w->I * ct_bytes, cudaMemcpyHostToDevice, s));
-    hc_status st = hc_conv_ct_pt(ctx, w, (const uint64_t *)din.p, (uint64_t *)dout.p, cuda_stream);
+    const uint32_t K = std::min<uint32_t>(kHostChunks, w->Mp);
+    if (w->mode != HC_WEIGHTS_NTT_OFFLINE || !conv_job_blocked(ctx, w) || K < 2) {
+        hc_status st = hc_conv_ct_pt(ctx, w, (const uint64_t *)din.p, (uint64_t *)dout.p, cuda_stream);
+        if (st != HC_OK) return st;
+        HC_CUDA_TRY(cudaMemcpyAsync(h_ct_out, dout.p, w->O * ct_bytes, cudaMemcpyDeviceToHost, s));
+        return hc_ctx_device_status(ctx, cuda_stream);
+    }
+    // Pipelined: the outputs of a block of output channels (contiguous in the output
+    // and in the weights) go back to the host while the next block is computed.
+    hc_status st = check_inputs(ctx, (const uint64_t *)din.p, (size_t)2 * w->I, s);
     if (st != HC_OK) return st;
-    HC_CUDA_TRY(cudaMemcpyAsync(h_ct_out, dout.p, w->O * ct_bytes, cudaMemcpyDeviceToHost, s));
+    CopyLane *lane = nullptr;
+    st = copy_lane(&lane);
+    if (st != HC_OK) return st;
+    dntt.p = dev_alloc(w->I * ct_bytes, s);
+    if (!dntt.p) return set_error(HC_ERR_OOM, "device buffer allocation failed");
+    uint64_t *x = (uint64_t *)dntt.p, *y = (uint64_t *)dout.p;
+    st = launch_ntt_fwd_ct(ctx, (const uint64_t *)din.p, x, w->I, s);
+    if (st != HC_OK) return st;
+    const size_t LN = (size_t)ctx->L * ctx->N;
+    const uint32_t per = (w->Mp + K - 1) / K;
+    uint32_t used = 0;
+    for (uint32_t j = 0; j < K; ++j) {
+        const uint32_t m0 = j * per, m1 = std::min(w->Mp, m0 + per);
+        if (m0 >= m1) break;
+        const size_t o0 = (size_t)m0 * w->B, no = (size_t)(m1 - m0) * w->B;
+        st = launch_mac_conv(ctx, x, w->d_pt + (size_t)m0 * w->G * LN, y + o0 * ct_words, w->G, w->B, m1 - m0, s);
+        if (st == HC_OK) st = launch_ntt_inv_ct(ctx, y + o0 * ct_words, y + o0 * ct_words, no, s);
+        if (st != HC_OK) return st;
+        HC_CUDA_TRY(cudaEventRecord(lane->ev[j], s));
+        HC_CUDA_TRY(cudaStreamWaitEvent(lane->st, lane->ev[j], 0));
+        HC_CUDA_TRY(cudaMemcpyAsync(h_ct_out + o0 * ct_words, y + o0 * ct_words, no * ct_bytes,
+                                    cudaMemcpyDeviceToHost, lane->st));
+        used = j + 1;
+    }
+    HC_CUDA_TRY(cudaEventRecord(lane->ev[used], lane->st));
+    HC_CUDA_TRY(cudaStreamWaitEvent(s, lane->ev[used], 0));  // scratch is freed after the copies
     return hc_ctx_device_status(ctx, cuda_stream);
 }
 

@@ -201,3 +201,31 @@ def test_generic_reduction_paths(L, moduli_kind):
     ks = sample_indices(N, 24, 9)
     want = conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, moduli, ks)
     assert np.array_equal(to_host(out).reshape(p.O, 2, len(moduli), N)[..., ks], want)
+
+
+@pytest.mark.parametrize("M", [1, 2, 7, 64])
+def test_host_entry_point_blocks_of_output_channels(L, M):
+    """hc_conv_ct_pt_host runs offline-weight layers in up to four blocks of output
+    channels, copying each block back while the next is computed: pinned and
+    pageable host buffers, block counts that do not divide M, every bit equal to
+    the device entry point."""
+    N, nl = 8192, 3
+    ctx = L.hc_ctx_create(N, CANONICAL_PRIMES[:nl], T_PLAIN)
+    s = Stream(48, M)
+    C_, H, W = 12, 20, 20
+    K = s.int8(M * C_ * 9).reshape(M, C_, 3, 3)
+    w = L.hc_weights_preprocess(ctx, L.make_desc(C_, H, W, M, 3, 3, pad=1), K)
+    ct = uniform_residues(s, CANONICAL_PRIMES[:nl], (w.I, 2), N)
+    d_out = torch.empty(w.O * 2 * nl * N, dtype=torch.int64, device="cuda")
+    L.hc_conv_ct_pt(ctx, w, to_dev(ct), d_out)
+    torch.cuda.synchronize()
+    want = to_host(d_out)
+    h_in = torch.from_numpy(ct.reshape(-1).view(np.int64)).pin_memory()
+    h_out = torch.full((w.O * 2 * nl * N,), -1, dtype=torch.int64).pin_memory()
+    for _ in range(2):
+        L.hc_conv_ct_pt_host(ctx, w, h_in, h_out)
+        assert np.array_equal(h_out.numpy().view(np.uint64), want)
+        h_out.fill_(-1)
+    pageable = np.zeros(w.O * 2 * nl * N, dtype=np.uint64)
+    L.hc_conv_ct_pt_host(ctx, w, np.ascontiguousarray(ct), pageable)
+    assert np.array_equal(pageable, want)
