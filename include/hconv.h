@@ -287,7 +287,7 @@ hc_status hc_conv_ct_pt_plain(const hc_ctx *ctx, const hc_weights *w, const uint
 /* hc_conv_ct_pt on HOST buffers: copies h_ct_in ([I][2][L][N]) to the
  * device, runs the layer, copies the result to h_ct_out ([O][2][L][N]) and
  * synchronises the stream before returning.  With offline weights the layer
- * runs in up to four blocks of output channels and each block's outputs are
+ * runs in up to eight blocks of output channels and each block's outputs are
  * copied back on a second stream while the next block is computed.  Pinned
  * host memory gives the fastest copies (and the overlap); pageable memory
  * works.  Device buffers come from the allocator.  Errors as hc_conv_ct_pt. */

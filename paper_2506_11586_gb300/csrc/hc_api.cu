@@ -279,7 +279,7 @@ void pack_weights(const hc_conv_desc &d, const Geom &g, uint32_t No, uint32_t N,
 }
 
 // output-channel blocks of the pipelined host-buffer convolution
-constexpr uint32_t kHostChunks = 4;
+constexpr uint32_t kHostChunks = 8;
 
 // per host thread and device: a copy stream and its events (made once, kept)
 struct CopyLane {

@@ -203,9 +203,9 @@ def test_generic_reduction_paths(L, moduli_kind):
     assert np.array_equal(to_host(out).reshape(p.O, 2, len(moduli), N)[..., ks], want)
 
 
-@pytest.mark.parametrize("M", [1, 2, 7, 64])
+@pytest.mark.parametrize("M", [1, 2, 7, 13, 64])
 def test_host_entry_point_blocks_of_output_channels(L, M):
-    """hc_conv_ct_pt_host runs offline-weight layers in up to four blocks of output
+    """hc_conv_ct_pt_host runs offline-weight layers in up to eight blocks of output
     channels, copying each block back while the next is computed: pinned and
     pageable host buffers, block counts that do not divide M, every bit equal to
     the device entry point."""
