@@ -17,6 +17,10 @@ Contents
   layers -- strided convolutions as stride-1 layers of the phase-split input
             (polyphase reading) and fully connected layers by matrix-vector
             packing, with their server steps (Sec. 6.1, Sec. 8.1 networks).
+  zp     -- BFV over Z_P with SIMD slots: encoding, Galois automorphisms,
+            key-switched slot rotations (one special prime) and the
+            multiply-accumulate-rotate iteration of HELiKs-style linear layers
+            (SecONNds-P, Sec. 6.1, Sec. 2.3).
   bfv    -- BFV secret-key encryption / decryption (App. C), client-side
             test harness only (Sec. 6.3: the server never holds the key).
 

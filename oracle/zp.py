@@ -1,0 +1,252 @@
+"""BFV over Z_P with SIMD slots, slot rotations by key switching, and the
+iterated multiply-accumulate-rotate of HELiKs-style linear layers.
+TEST INFRASTRUCTURE ONLY.
+
+SecONNds-P runs its linear layers with HELiKs' kernels over the plaintext space
+Z_P^N, P a prime (Sec. 6.1; Sec. 2.3): an iterative algorithm in which each
+iteration multiplies the input ciphertext by an NTT-preprocessed weight
+plaintext, accumulates the product into the previous iteration's result, and
+rotates the accumulator by one slot (Sec. 6.1; the 1-step rotations and NTT
+preprocessing of Sec. 2.3).  Rotations are Galois automorphisms followed by
+key switching (Sec. 2.1: rotations need a key-switching step with public
+evaluation keys; App. C).  The paper prints none of the formulas; this module
+holds the textbook reading the build uses:
+
+SIMD slots.  P = 1 mod 2N; zeta the minimal primitive 2N-th root mod P.  Slot
+(r, c), r in {0, 1}, c < N/2, holds p(zeta^e) with e = 5^c mod 2N for r = 0
+and e = -5^c mod 2N for r = 1.  With core.ntt's order (slot k holds
+p(psi^(2 rev(k) + 1))) slot (r, c) is NTT index rev((e - 1) / 2).
+
+Galois automorphism.  sigma_g(p)(X) = p(X^g) for odd g: coefficient i moves
+to i*g mod 2N, negated when that lands in [N, 2N).  sigma_5 rotates both slot
+rows left by one: slot (r, c) of sigma_5(p) holds slot (r, c + 1) of p.
+
+Key switching (one special prime p_sp, one digit per ciphertext limb).  The
+Galois key for g is, for every digit j < L, an RLWE pair over Q*p_sp
+    k_j = (b_j, a_j),  b_j = -a_j s + e_j + p_sp * Qh_j * [Qh_j^-1]_{q_j} * sigma_g(s),
+with Qh_j = Q / q_j.  A ciphertext (c0, c1) under s rotates to
+    d = sigma_g(c1);  D_j = d mod q_j (integers in [0, q_j));
+    (u0, u1) = sum_j D_j * k_j  over Q*p_sp;
+    v = (u - [u]_{p_sp}) / p_sp over Q, [.] the centered residue (rounding);
+    out = (sigma_g(c0) + v0, v1),
+which decrypts to sigma_g(m) up to small noise: u0 + u1 s = sum_j D_j e_j +
+p_sp * (d + Q k) * sigma_g(s) for an integer polynomial k, and p_sp Q = 0 mod
+Q p_sp.
+
+Multiply-accumulate-rotate.  For ciphertext x and NTT-preprocessed weights
+w_0 .. w_{n-1}: acc = x * w_{n-1}; for i = n-2 .. 0: acc = rot(acc) + x * w_i.
+The result decrypts to sum_i rot^i(m * w_i) slot-wise mod P.
+
+Parity: pinned by SIMD encode/decode round trips and slot-wise products, the
+automorphism's closed form on monomials and its action on slots, decryption of
+rotated ciphertexts to rotated slot vectors, the key-switching noise bound,
+and the iteration against the plain slot-wise formula
+(tests/test_oracle_zp.py).
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import bfv, core
+
+
+# ---- plaintext prime and SIMD slots ------------------------------------------------
+
+def plaintext_prime(N, bits=37):
+    """The largest prime below 2^bits that is 1 mod 2N."""
+    return core.ntt_primes(bits, (2 * N).bit_length() - 1, 1)[0]
+
+
+def slot_exponents(N):
+    """[2][N/2] odd exponents e: slot (r, c) is the evaluation at zeta^e."""
+    half = N // 2
+    e = np.zeros((2, half), dtype=np.int64)
+    g = 1
+    for c in range(half):
+        e[0, c] = g
+        e[1, c] = (2 * N - g) % (2 * N)
+        g = g * 5 % (2 * N)
+    return e
+
+
+def slot_index(N):
+    """[2][N/2] NTT indices (core.ntt order) of the slots."""
+    logn = N.bit_length() - 1
+    e = slot_exponents(N)
+    return np.vectorize(lambda x: core.bitrev((int(x) - 1) // 2, logn))(e).astype(np.int64)
+
+
+def encode(m, N, P):
+    """Slot values m [2][N/2] in [0, P) -> plaintext polynomial [N] with those slots."""
+    zeta = core.min_psi(P, N)
+    A = np.zeros(N, dtype=np.uint64)
+    A[slot_index(N).reshape(-1)] = np.asarray(m, dtype=np.uint64).reshape(-1)
+    return core.intt(A, P, zeta)
+
+
+def decode(p, N, P):
+    """Plaintext polynomial [N] in [0, P) -> slot values [2][N/2]."""
+    zeta = core.min_psi(P, N)
+    A = core.ntt(np.asarray(p, dtype=np.uint64), P, zeta)
+    return A[slot_index(N)]
+
+
+# ---- automorphism -------------------------------------------------------------------
+
+def automorphism(a, g, q):
+    """sigma_g(a)(X) = a(X^g) mod (X^N + 1, q), a [N] residues in [0, q)."""
+    a = np.asarray(a, dtype=np.uint64)
+    N = a.size
+    out = np.zeros(N, dtype=np.uint64)
+    for i in range(N):
+        j = i * g % (2 * N)
+        v = int(a[i])
+        if j < N:
+            out[j] = v
+        else:
+            out[j - N] = (q - v) % q
+    return out
+
+
+def automorphism_small(s, g):
+    """sigma_g of a polynomial with small signed integer coefficients."""
+    s = np.asarray(s, dtype=np.int64)
+    N = s.size
+    out = np.zeros(N, dtype=np.int64)
+    for i in range(N):
+        j = i * g % (2 * N)
+        if j < N:
+            out[j] = s[i]
+        else:
+            out[j - N] = -s[i]
+    return out
+
+
+# ---- Galois keys and key switching ------------------------------------------------------
+
+@dataclass
+class KsParams:
+    N: int
+    moduli: tuple      # q_0 .. q_{L-1}
+    special: int       # p_sp
+
+    @property
+    def L(self):
+        return len(self.moduli)
+
+    @property
+    def qp(self):
+        return tuple(self.moduli) + (self.special,)
+
+    @property
+    def Q(self):
+        r = 1
+        for q in self.moduli:
+            r *= q
+        return r
+
+
+def galois_key(kp: KsParams, sk, g, a, e):
+    """[L][2][L+1][N] uint64: digit j's pair (b_j, a_j) over Q*p_sp.
+    a: [L][L+1][N] uniform residues; e: [L][N] small noise."""
+    N, L = kp.N, kp.L
+    tern = core.ternary_of(sk)
+    s_g = automorphism_small(sk, g)
+    Q = kp.Q
+    out = np.zeros((L, 2, L + 1, N), dtype=np.uint64)
+    for j in range(L):
+        qj = kp.moduli[j]
+        Qh = Q // qj
+        scal = kp.special * Qh * pow(Qh % qj, -1, qj)
+        for i, q in enumerate(kp.qp):
+            a_ji = np.ascontiguousarray(a[j][i], dtype=np.uint64)
+            as_ = core.negacyclic_ternary(a_ji, tern, N, q).astype(object)
+            sg = core.lift_small(s_g, q).astype(object)
+            ej = core.lift_small(e[j], q).astype(object)
+            b = (-as_ + ej + (scal % q) * sg) % q
+            out[j, 0, i] = b.astype(np.uint64)
+            out[j, 1, i] = a_ji
+    return out
+
+
+def mod_down(u, kp: KsParams):
+    """[L+1][N] residues over Q*p_sp -> [L][N]: (u - [u]_{p_sp}) / p_sp mod q_i with the
+    centered residue [u]_{p_sp} in (-p_sp/2, p_sp/2]."""
+    p = kp.special
+    usp = u[kp.L].astype(object)
+    cen = np.where(usp > (p - 1) // 2, usp - p, usp)
+    out = np.zeros((kp.L, kp.N), dtype=np.uint64)
+    for i, q in enumerate(kp.moduli):
+        pinv = pow(p % q, -1, q)
+        out[i] = (((u[i].astype(object) - cen) % q) * pinv % q).astype(np.uint64)
+    return out
+
+
+def rotate(ct, gk, g, kp: KsParams):
+    """Ciphertext [2][L][N] (coefficient domain) -> sigma_g applied and switched back to s."""
+    N, L = kp.N, kp.L
+    r0 = np.stack([automorphism(ct[0, i], g, q) for i, q in enumerate(kp.moduli)])
+    d = np.stack([automorphism(ct[1, i], g, q) for i, q in enumerate(kp.moduli)])
+    u = np.zeros((2, L + 1, N), dtype=object)
+    for j in range(L):
+        Dj = d[j].astype(object)                   # integers in [0, q_j)
+        for i, q in enumerate(kp.qp):
+            Dji = (Dj % q).astype(np.uint64)
+            for comp in range(2):
+                u[comp, i] += core.negacyclic(Dji, gk[j, comp, i], q).astype(object)
+    for i, q in enumerate(kp.qp):
+        u[:, i] %= q
+    v0, v1 = mod_down(u[0], kp), mod_down(u[1], kp)
+    out = np.zeros((2, L, N), dtype=np.uint64)
+    for i, q in enumerate(kp.moduli):
+        out[0, i] = ((r0[i].astype(object) + v0[i].astype(object)) % q).astype(np.uint64)
+        out[1, i] = v1[i]
+    return out
+
+
+# ---- plaintext multiply and the multiply-accumulate-rotate iteration ---------------------
+
+def lift_plain(p, P, moduli):
+    """Plaintext polynomial [N] in [0, P) -> [L][N] centered lift mod every q_i."""
+    p = np.asarray(p, dtype=np.int64)
+    cen = np.where(p > (P - 1) // 2, p - P, p)
+    return np.stack([core.lift_small(cen, q) for q in moduli])
+
+
+def mul_plain(ct, w_lift, moduli):
+    """(c0 * w, c1 * w) over R_Q for a lifted plaintext w [L][N]."""
+    out = np.zeros_like(ct)
+    for comp in range(2):
+        for i, q in enumerate(moduli):
+            out[comp, i] = core.negacyclic(ct[comp, i], w_lift[i], q)
+    return out
+
+
+def add(a, b, moduli):
+    out = np.zeros_like(a)
+    for i, q in enumerate(moduli):
+        out[:, i] = ((a[:, i].astype(object) + b[:, i].astype(object)) % q).astype(np.uint64)
+    return out
+
+
+def mac_rotate(ct, w_lifts, gk, g, kp: KsParams):
+    """acc = ct * w_{n-1}; for i = n-2 .. 0: acc = rot(acc) + ct * w_i."""
+    n = len(w_lifts)
+    acc = mul_plain(ct, w_lifts[n - 1], kp.moduli)
+    for i in range(n - 2, -1, -1):
+        acc = add(rotate(acc, gk, g, kp), mul_plain(ct, w_lifts[i], kp.moduli), kp.moduli)
+    return acc
+
+
+def slot_mac_rotate(m, ws, P):
+    """The plain counterpart on slot vectors [2][N/2]: sum_i rot^i(m * w_i) mod P, rot =
+    left rotation of both rows by one."""
+    m = np.asarray(m, dtype=object)
+    acc = np.zeros_like(m)
+    for i, w in enumerate(ws):
+        acc = (acc + np.roll((m * np.asarray(w, dtype=object)) % P, -i, axis=1)) % P
+    return acc.astype(np.int64)
+
+
+def bfv_params(N, moduli, P):
+    return bfv.Params(N, tuple(moduli), P)
