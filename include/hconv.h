@@ -379,6 +379,53 @@ hc_status hc_ctpt_mac(const hc_ctx *ctx, const uint64_t *d_ct, const uint64_t *d
                       const uint32_t *h_slot, size_t n, uint64_t *d_out, size_t n_out,
                       void *cuda_stream);
 
+/* ------------------------------------------- Z_P layers: slot rotations --
+ * SecONNds-P runs its linear layers with HELiKs' kernels over Z_P^N (Sec. 6.1):
+ * each iteration multiplies the input ciphertext by an NTT-preprocessed weight
+ * plaintext, accumulates, and rotates the accumulator by one SIMD slot;
+ * rotations need key switching with public evaluation keys (Sec. 2.1).
+ *
+ * A rotation applies the Galois automorphism sigma_g (X -> X^g, g odd < 2N;
+ * g = 5 rotates both slot rows of a BFV-SIMD plaintext left by one) and
+ * switches the key back with one special prime p_sp and one digit per limb:
+ *   d = sigma_g(c1), D_j = d mod q_j;  u = sum_j D_j * k_j over Q*p_sp;
+ *   v = (u - [u]_{p_sp}) / p_sp over Q ([.] centered);  out = (sigma_g(c0) + v0, v1).
+ * The Galois key k_j = (b_j, a_j), j < L, is made by the secret-key holder:
+ *   b_j = -a_j s + e_j + p_sp * (Q/q_j) * [(Q/q_j)^-1]_{q_j} * sigma_g(s)  over Q*p_sp.
+ *
+ * hc_galois_key_create: h_key is host [L][2][L+1][N] coefficient-domain
+ * residues (digit j: b_j then a_j, limbs q_0 .. q_{L-1}, p_sp), copied and
+ * kept in the NTT domain.  special_prime must be a prime < 2^50, = 1 mod 2N,
+ * distinct from the context's moduli (it gets a context of its own, L + 1 <=
+ * 8).  Errors: HC_ERR_INVALID_ARG, HC_ERR_BAD_MODULUS, HC_ERR_OOM, HC_ERR_CUDA.
+ * Freed by hc_free. */
+typedef struct hc_galois_key hc_galois_key;
+hc_status hc_galois_key_create(const hc_ctx *ctx, uint64_t special_prime, uint32_t galois_elt,
+                               const uint64_t *h_key, hc_galois_key **out, void *cuda_stream);
+
+/* Rotate n_ct ciphertexts d_ct_in [n][2][L][N] (coefficient domain, residues
+ * < q_i) into d_ct_out (same layout, must not overlap the input).  Scratch of
+ * n*(L+1)*(L+2)*N*8 bytes comes from the allocator.  Errors: HC_ERR_INVALID_ARG,
+ * HC_ERR_RANGE (checked mode), HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_ct_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct_in,
+                       uint64_t *d_ct_out, size_t n_ct, void *cuda_stream);
+
+/* The multiply-accumulate-rotate iteration: for the ciphertext d_ct [2][L][N]
+ * and n NTT-domain plaintexts d_w_ntt [n][L][N] (hc_zp_plain_preprocess),
+ *   acc = d_ct * w_{n-1};  for i = n-2 .. 0: acc = rotate(acc) + d_ct * w_i;
+ * d_out [2][L][N] = acc (coefficient domain; must not overlap d_ct).  Decrypts
+ * to sum_i rot^i(m * w_i) slot-wise mod P.  Errors as hc_ct_rotate. */
+hc_status hc_mac_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct,
+                        const uint64_t *d_w_ntt, uint32_t n, uint64_t *d_out, void *cuda_stream);
+
+/* Weight preprocessing for the iteration: n plaintext polynomials h_plain
+ * [n][N] with coefficients in [0, P) (BFV-SIMD encoded by the caller), lifted
+ * centered ((P-1)/2 < v -> v - P) into every q_i and forward-NTT'd into the
+ * device buffer d_out [n][L][N]; synchronises the stream.  Errors:
+ * HC_ERR_INVALID_ARG, HC_ERR_RANGE (a coefficient >= P), HC_ERR_CUDA. */
+hc_status hc_zp_plain_preprocess(const hc_ctx *ctx, uint64_t P, const uint64_t *h_plain, size_t n,
+                                 uint64_t *d_out, void *cuda_stream);
+
 /* ------------------------------------------------------------------ plans --
  * Batching across layers, products and ring degrees (Sec. 6.2; the paper's
  * closing remarks on accelerating composite HE operations).  A plan binds a

@@ -108,6 +108,10 @@ _SIGS = {
     "hc_conv_ct_pt_host": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_conv_ct_pt_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "hc_ctpt_mac": (C.c_int, [_P, _P, _P, _P, C.c_size_t, _P, C.c_size_t, _P]),
+    "hc_galois_key_create": (C.c_int, [_P, C.c_uint64, C.c_uint32, _P, C.POINTER(_P), _P]),
+    "hc_ct_rotate": (C.c_int, [_P, _P, _P, _P, C.c_size_t, _P]),
+    "hc_mac_rotate": (C.c_int, [_P, _P, _P, _P, C.c_uint32, _P, _P]),
+    "hc_zp_plain_preprocess": (C.c_int, [_P, C.c_uint64, _P, C.c_size_t, _P, _P]),
     "hc_conv_server_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "hc_conv_server_step_sparse": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "hc_plan_create": (C.c_int, [_P, C.c_size_t, C.POINTER(_P)]),
@@ -437,6 +441,40 @@ def hc_ctpt_mac(ctx, ct, pt_ntt, slots, out, stream=None):
     n_out = _npolys(ctx, out) // 2
     _check(lib().hc_ctpt_mac(ctx.ptr, _dptr(ct), _dptr(pt_ntt), C.c_void_p(sl.ctypes.data), sl.size,
                              _dptr(out), n_out, _stream(stream)))
+
+
+class GaloisKey(_Handle):
+    def __init__(self, ptr, ctx, special, g):
+        super().__init__(ptr, keep=ctx)
+        self.ctx, self.special, self.g = ctx, special, g
+
+
+def hc_galois_key_create(ctx, special_prime, galois_elt, h_key, stream=None):
+    """h_key: host [L][2][L+1][N] coefficient-domain residues (digit j: b_j, a_j)."""
+    k = np.ascontiguousarray(h_key, dtype=np.uint64)
+    if k.size != ctx.L * 2 * (ctx.L + 1) * ctx.N:
+        raise ValueError("key must have L*2*(L+1)*N words")
+    out = C.c_void_p()
+    _check(lib().hc_galois_key_create(ctx.ptr, int(special_prime), galois_elt, C.c_void_p(k.ctypes.data),
+                                      C.byref(out), _stream(stream)))
+    return GaloisKey(out, ctx, int(special_prime), galois_elt)
+
+
+def hc_ct_rotate(ctx, key, ct_in, ct_out, stream=None):
+    n = _npolys(ctx, ct_in) // 2
+    _check(lib().hc_ct_rotate(ctx.ptr, key.ptr, _dptr(ct_in), _dptr(ct_out), n, _stream(stream)))
+
+
+def hc_mac_rotate(ctx, key, ct, w_ntt, out, stream=None):
+    n = _npolys(ctx, w_ntt)
+    _check(lib().hc_mac_rotate(ctx.ptr, key.ptr, _dptr(ct), _dptr(w_ntt), n, _dptr(out), _stream(stream)))
+
+
+def hc_zp_plain_preprocess(ctx, P, h_plain, out, stream=None):
+    """h_plain: host [n][N] coefficients in [0, P); out: device [n][L][N]."""
+    h = np.ascontiguousarray(h_plain, dtype=np.uint64)
+    n = h.size // ctx.N
+    _check(lib().hc_zp_plain_preprocess(ctx.ptr, int(P), C.c_void_p(h.ctypes.data), n, _dptr(out), _stream(stream)))
 
 
 class Plan(_Handle):

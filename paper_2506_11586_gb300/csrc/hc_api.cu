@@ -1061,6 +1061,8 @@ void hc_free(void *handle)
         plan_destroy((hc_plan *)handle);
     } else if (magic == kMagicServer) {
         server_destroy((hc_server *)handle);
+    } else if (magic == kMagicGaloisKey) {
+        galois_key_destroy((hc_galois_key *)handle);
     } else if (magic == kMagicWeights) {
         hc_weights *w = (hc_weights *)handle;
         DeviceGuard g(w->device);

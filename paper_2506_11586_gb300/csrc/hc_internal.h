@@ -17,6 +17,7 @@ constexpr uint32_t kMagicCtx = 0x48435458u;      // 'HCTX'
 constexpr uint32_t kMagicWeights = 0x48435754u;  // 'HCWT'
 constexpr uint32_t kMagicPlan = 0x4843504Cu;     // 'HCPL'
 constexpr uint32_t kMagicServer = 0x48435352u;   // 'HCSR'
+constexpr uint32_t kMagicGaloisKey = 0x4843474Bu;  // 'HCGK'
 constexpr uint32_t kMagicDead = 0xDEADDEADu;
 
 // Per-limb constants and twiddle tables, device-resident, read through the
@@ -125,6 +126,9 @@ namespace hc {
 hc_status launch_inv_extract(const hc_ctx *ctx, const ExtractArgs &ex, cudaStream_t s);
 // the output slot table of w (built once per weights handle)
 hc_status build_slot_table(hc_weights *w);
+
+// frees a Galois key handle (hc_rotate.cu)
+void galois_key_destroy(hc_galois_key *k);
 
 // keep freed per-call scratch cached in the device's default memory pool
 void keep_scratch_cached(int device);

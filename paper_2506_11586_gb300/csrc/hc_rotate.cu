@@ -1,0 +1,341 @@
+// hc_rotate.cu -- slot rotations of RLWE ciphertexts and the
+// multiply-accumulate-rotate iteration of HELiKs-style linear layers over Z_P
+// (SecONNds-P, Sec. 6.1: each iteration multiplies the input ciphertext by an
+// NTT-preprocessed weight plaintext, accumulates, and rotates the accumulator
+// by one slot; Sec. 2.1: rotations need a key-switching step with public
+// evaluation keys).
+//
+// A rotation is the Galois automorphism sigma_g (X -> X^g) followed by key
+// switching with one special prime p_sp and one digit per ciphertext limb:
+//   d = sigma_g(c1);  D_j = d mod q_j lifted to every modulus of Q*p_sp;
+//   (u0, u1) = sum_j NTT(D_j) . k_j over Q*p_sp, back to coefficients;
+//   v = (u - [u]_{p_sp}) / p_sp over Q, [.] the centered residue;
+//   out = (sigma_g(c0) + v0, v1).
+// The key k_j = (b_j, a_j), b_j = -a_j s + e_j + p_sp * Qh_j [Qh_j^-1]_{q_j} sigma_g(s)
+// (Qh_j = Q / q_j), comes from the secret-key holder; the GPU keeps it in the
+// NTT domain over Q*p_sp.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "hc_arith.cuh"
+#include "hc_internal.h"
+
+// per ciphertext limb i: p_sp mod q_i, p_sp^-1 mod q_i with its Shoup companion
+struct ModDown {
+    uint64_t p_mod_q, pinv, pinv_s;
+};
+
+struct hc_galois_key {
+    uint32_t magic;
+    const hc_ctx *ctx;     // ciphertext context: q_0 .. q_{L-1}
+    hc_ctx *qp;            // owned: q_0 .. q_{L-1}, p_sp
+    int device;
+    uint32_t g, ginv;      // Galois element and its inverse mod 2N
+    uint64_t special;
+    uint64_t *d_key;       // [L][2][L+1][N], NTT domain over Q*p_sp
+    ModDown *d_md;         // [L]
+};
+
+namespace hc {
+namespace {
+
+__device__ __forceinline__ uint64_t negmod(uint64_t v, uint64_t q) { return v ? q - v : 0; }
+
+__device__ __forceinline__ uint64_t reduce_any(uint64_t v, const LimbConst &lc)
+{
+    return canon3(reduce_lazy(v, (uint32_t)lc.one_s, 0ull - lc.q), lc.q);
+}
+
+// digits of sigma_g(c1): dig[ct][j][i][k] = sigma_g(c1)[j][k] mod m_i over the L+1
+// moduli m_i of Q*p_sp (gather: output coefficient k takes source k*ginv mod 2N)
+__global__ void k_ks_digits(const uint64_t *__restrict__ ct, uint64_t *__restrict__ dig,
+                            const LimbConst *__restrict__ lq, const LimbConst *__restrict__ lqp, uint32_t L,
+                            uint32_t N, uint32_t ginv, size_t total)
+{
+    const uint32_t n2 = 2 * N;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t k = (uint32_t)(t % N);
+        const size_t r = t / N;
+        const uint32_t j = (uint32_t)(r % L);
+        const size_t c = r / L;
+        const uint64_t qj = lq[j].q;
+        const uint32_t src = (uint32_t)(((uint64_t)k * ginv) % n2);
+        const uint64_t *c1 = ct + ((c * 2 + 1) * L + j) * N;
+        const uint64_t v = src < N ? c1[src] : negmod(c1[src - N], qj);
+        uint64_t *d = dig + ((c * L + j) * (L + 1)) * N + k;
+        for (uint32_t i = 0; i <= L; ++i) d[(size_t)i * N] = i == j ? v : reduce_any(v, lqp[i]);
+    }
+}
+
+// u[ct][comp][i][k] = sum_j dig[ct][j][i][k] * key[j][comp][i][k] mod m_i (NTT domain)
+__global__ void k_ks_mac(const uint64_t *__restrict__ dig, const uint64_t *__restrict__ key,
+                         uint64_t *__restrict__ u, const LimbConst *__restrict__ lqp, uint32_t L, uint32_t N,
+                         size_t total)
+{
+    const uint32_t L1 = L + 1;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t k = (uint32_t)(t % N);
+        const size_t r = t / N;
+        const uint32_t i = (uint32_t)(r % L1);
+        const size_t c = r / L1;
+        const LimbConst &lc = lqp[i];
+        const uint64_t q = lc.q, nq = 0ull - q;
+        MacAcc a0, a1;
+        mac_zero(a0);
+        mac_zero(a1);
+        for (uint32_t j = 0; j < L; ++j) {
+            const uint64_t x = dig[((c * L + j) * L1 + i) * N + k];
+            mac_add(a0, x, key[((size_t)(j * 2) * L1 + i) * N + k]);
+            mac_add(a1, x, key[((size_t)(j * 2 + 1) * L1 + i) * N + k]);
+        }
+        const uint32_t ones = (uint32_t)lc.one_s;
+        u[((c * 2) * L1 + i) * N + k] = mac_reduce(a0, q, nq, lc.r64, lc.r64_s, ones);
+        u[((c * 2 + 1) * L1 + i) * N + k] = mac_reduce(a1, q, nq, lc.r64, lc.r64_s, ones);
+    }
+}
+
+// out[ct][comp][i][k] = (comp == 0 ? sigma_g(c0)[i][k] : 0) + (u_i - [u_sp]) / p_sp mod q_i
+__global__ void k_ks_mod_down(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ u,
+                              uint64_t *__restrict__ out, const LimbConst *__restrict__ lq,
+                              const ModDown *__restrict__ md, uint64_t special, uint32_t L, uint32_t N,
+                              uint32_t ginv, size_t total)
+{
+    const uint32_t n2 = 2 * N, L1 = L + 1;
+    const uint64_t half = (special - 1) / 2;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t k = (uint32_t)(t % N);
+        const size_t r = t / N;
+        const uint32_t i = (uint32_t)(r % L);
+        const uint32_t comp = (uint32_t)((r / L) % 2);
+        const size_t c = r / (2 * (size_t)L);
+        const LimbConst &lc = lq[i];
+        const uint64_t q = lc.q;
+        const uint64_t ui = u[((c * 2 + comp) * L1 + i) * N + k];
+        const uint64_t usp = u[((c * 2 + comp) * L1 + L) * N + k];
+        const uint64_t rsp = reduce_any(usp, lc);  // usp mod q_i
+        // the centered residue: usp - p_sp when usp > (p_sp - 1) / 2
+        const uint64_t cen = usp > half ? (rsp >= md[i].p_mod_q ? rsp - md[i].p_mod_q : rsp + q - md[i].p_mod_q) : rsp;
+        const uint64_t diff = ui >= cen ? ui - cen : ui + q - cen;
+        uint64_t v = canon4(shoup_lazy(diff, md[i].pinv, md[i].pinv_s, 0ull - q), q);
+        if (comp == 0) {
+            const uint32_t src = (uint32_t)(((uint64_t)k * ginv) % n2);
+            const uint64_t *c0 = ct + ((c * 2) * L + i) * N;
+            const uint64_t a = src < N ? c0[src] : negmod(c0[src - N], q);
+            v = csub(v + a, q);
+        }
+        out[((c * 2 + comp) * L + i) * N + k] = v;
+    }
+}
+
+unsigned grid_of(size_t total)
+{
+    const size_t b = (total + 255) / 256;
+    return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
+}
+
+struct Buf {
+    void *p = nullptr;
+    cudaStream_t s;
+    explicit Buf(cudaStream_t st) : s(st) {}
+    ~Buf() { dev_free(p, s); }
+};
+
+bool key_ok(const hc_galois_key *k) { return k && k->magic == kMagicGaloisKey; }
+
+hc_status rotate_into(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *in, uint64_t *out, size_t n,
+                      cudaStream_t s)
+{
+    const uint32_t L = ctx->L, N = ctx->N;
+    const size_t dig_words = n * L * (L + 1) * (size_t)N, u_words = n * 2 * (L + 1) * (size_t)N;
+    Buf dig(s), u(s);
+    dig.p = dev_alloc(dig_words * 8, s);
+    u.p = dev_alloc(u_words * 8, s);
+    if (!dig.p || !u.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+    uint64_t *dd = (uint64_t *)dig.p, *uu = (uint64_t *)u.p;
+    {
+        ProfileScope ps("k_ks_digits", s);
+        const size_t total = n * L * (size_t)N;
+        k_ks_digits<<<grid_of(total), 256, 0, s>>>(in, dd, ctx->d_limbs, key->qp->d_limbs, L, N, key->ginv, total);
+        HC_CUDA_TRY(cudaGetLastError());
+    }
+    hc_status st = launch_ntt_fwd(key->qp, dd, dd, n * L, s);  // digits: n*L polys over Q*p_sp
+    if (st != HC_OK) return st;
+    {
+        ProfileScope ps("k_ks_mac", s);
+        const size_t total = n * (L + 1) * (size_t)N;
+        k_ks_mac<<<grid_of(total), 256, 0, s>>>(dd, key->d_key, uu, key->qp->d_limbs, L, N, total);
+        HC_CUDA_TRY(cudaGetLastError());
+    }
+    st = launch_ntt_inv(key->qp, uu, uu, 2 * n, s);
+    if (st != HC_OK) return st;
+    ProfileScope ps("k_ks_mod_down", s);
+    const size_t total = n * 2 * L * (size_t)N;
+    k_ks_mod_down<<<grid_of(total), 256, 0, s>>>(in, uu, out, ctx->d_limbs, key->d_md, key->special, L, N,
+                                                  key->ginv, total);
+    HC_CUDA_TRY(cudaGetLastError());
+    return HC_OK;
+}
+
+}  // namespace
+
+void galois_key_destroy(hc_galois_key *k)
+{
+    DeviceGuard g(k->device);
+    dev_free_persistent(k->d_key);
+    dev_free_persistent(k->d_md);
+    hc_free(k->qp);
+    k->magic = kMagicDead;
+    delete k;
+}
+
+}  // namespace hc
+
+using namespace hc;
+
+extern "C" {
+
+hc_status hc_galois_key_create(const hc_ctx *ctx, uint64_t special_prime, uint32_t galois_elt, const uint64_t *h_key,
+                               hc_galois_key **out, void *cuda_stream)
+{
+    if (!out) return set_error(HC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctx || ctx->magic != kMagicCtx) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (!h_key) return set_error(HC_ERR_INVALID_ARG, "h_key is NULL");
+    const uint32_t L = ctx->L, N = ctx->N;
+    if (L + 1 > kMaxLimbs) return set_error(HC_ERR_INVALID_ARG, "no room for the special prime (L = %u)", L);
+    if (!(galois_elt & 1) || galois_elt >= 2 * N)
+        return set_error(HC_ERR_INVALID_ARG, "Galois element must be odd and below 2N (got %u)", galois_elt);
+    for (uint32_t i = 0; i < L; ++i)
+        if (ctx->q[i] == special_prime) return set_error(HC_ERR_BAD_MODULUS, "special prime equals q[%u]", i);
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    uint64_t moduli[kMaxLimbs];
+    for (uint32_t i = 0; i < L; ++i) moduli[i] = ctx->q[i];
+    moduli[L] = special_prime;
+    hc_ctx *qp = nullptr;
+    hc_status st = hc_ctx_create_ex(N, moduli, L + 1, ctx->t, 0, &qp);  // validates the special prime
+    if (st != HC_OK) return st;
+    hc_galois_key *k = new (std::nothrow) hc_galois_key();
+    if (!k) {
+        hc_free(qp);
+        return set_error(HC_ERR_OOM, "host allocation failed");
+    }
+    k->magic = kMagicGaloisKey;
+    k->ctx = ctx;
+    k->qp = qp;
+    k->device = ctx->device;
+    k->g = galois_elt;
+    uint32_t ginv = 1;
+    while ((uint64_t)ginv * galois_elt % (2 * N) != 1) ginv += 2;  // odd residues form a group mod 2N
+    k->ginv = ginv;
+    k->special = special_prime;
+    std::vector<ModDown> md(L);
+    for (uint32_t i = 0; i < L; ++i) {
+        const uint64_t q = ctx->q[i];
+        md[i].p_mod_q = special_prime % q;
+        md[i].pinv = powmod_u64(md[i].p_mod_q, q - 2, q);
+        md[i].pinv_s = shoup_companion(md[i].pinv, q);
+    }
+    const size_t key_words = (size_t)L * 2 * (L + 1) * N;
+    k->d_key = (uint64_t *)dev_alloc_persistent(key_words * 8);
+    k->d_md = (ModDown *)dev_alloc_persistent(L * sizeof(ModDown));
+    if (!k->d_key || !k->d_md) {
+        galois_key_destroy(k);
+        return set_error(HC_ERR_OOM, "device allocation of the Galois key failed");
+    }
+    cudaError_t e = cudaMemcpy(k->d_key, h_key, key_words * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(k->d_md, md.data(), L * sizeof(ModDown), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        galois_key_destroy(k);
+        return cuda_error(e, "uploading the Galois key");
+    }
+    st = check_inputs(qp, k->d_key, (size_t)2 * L, s);
+    if (st == HC_OK) st = launch_ntt_fwd(qp, k->d_key, k->d_key, (size_t)2 * L, s);
+    if (st == HC_OK) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_error(e, "Galois key preprocessing");
+    }
+    if (st != HC_OK) {
+        galois_key_destroy(k);
+        return st;
+    }
+    *out = k;
+    return HC_OK;
+}
+
+hc_status hc_ct_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct_in, uint64_t *d_ct_out,
+                       size_t n_ct, void *cuda_stream)
+{
+    if (!ctx || ctx->magic != kMagicCtx || !key_ok(key)) return set_error(HC_ERR_INVALID_ARG, "invalid context or key");
+    if (key->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "key was made for another context");
+    if (n_ct == 0) return HC_OK;
+    if (!d_ct_in || !d_ct_out) return set_error(HC_ERR_INVALID_ARG, "null ciphertext buffer");
+    if (d_ct_in == d_ct_out) return set_error(HC_ERR_INVALID_ARG, "in place rotation is not supported");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    hc_status st = check_inputs(ctx, d_ct_in, 2 * n_ct, s);
+    if (st != HC_OK) return st;
+    return rotate_into(ctx, key, d_ct_in, d_ct_out, n_ct, s);
+}
+
+hc_status hc_mac_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct, const uint64_t *d_w_ntt,
+                        uint32_t n, uint64_t *d_out, void *cuda_stream)
+{
+    if (!ctx || ctx->magic != kMagicCtx || !key_ok(key)) return set_error(HC_ERR_INVALID_ARG, "invalid context or key");
+    if (key->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "key was made for another context");
+    if (!d_ct || !d_w_ntt || !d_out || n == 0) return set_error(HC_ERR_INVALID_ARG, "null buffer or n = 0");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    hc_status st = check_inputs(ctx, d_ct, 2, s);
+    if (st == HC_OK) st = check_inputs(ctx, d_w_ntt, n, s);
+    if (st != HC_OK) return st;
+    const size_t ct_words = (size_t)2 * ctx->L * ctx->N, pt_words = (size_t)ctx->L * ctx->N;
+    Buf tmp(s);
+    tmp.p = dev_alloc(2 * ct_words * 8, s);
+    if (!tmp.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+    uint64_t *bufs[2] = {(uint64_t *)tmp.p, (uint64_t *)tmp.p + ct_words};
+    // the last iteration writes d_out: pick the starting buffer by the parity of n
+    uint32_t cur = 0;
+    uint64_t *acc = n == 1 ? d_out : bufs[cur];
+    st = launch_product(ctx, d_ct, d_w_ntt + (size_t)(n - 1) * pt_words, nullptr, acc, 1, false, s);
+    for (uint32_t i = n - 1; st == HC_OK && i-- > 0;) {
+        uint64_t *next = i == 0 ? d_out : bufs[cur ^ 1];
+        st = rotate_into(ctx, key, acc, next, 1, s);
+        if (st == HC_OK) st = launch_product(ctx, d_ct, d_w_ntt + (size_t)i * pt_words, nullptr, next, 1, true, s);
+        acc = next;
+        cur ^= 1;
+    }
+    return st;
+}
+
+hc_status hc_zp_plain_preprocess(const hc_ctx *ctx, uint64_t P, const uint64_t *h_plain, size_t n, uint64_t *d_out,
+                                 void *cuda_stream)
+{
+    if (!ctx || ctx->magic != kMagicCtx) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (n == 0) return HC_OK;
+    if (!h_plain || !d_out) return set_error(HC_ERR_INVALID_ARG, "null buffer");
+    if (P < 3 || P >= (1ull << 50)) return set_error(HC_ERR_INVALID_ARG, "plaintext modulus out of range");
+    const uint32_t L = ctx->L, N = ctx->N;
+    // centered lift of every coefficient into each q_i, on the host; NTT on the device
+    std::vector<uint64_t> lifted(n * L * N);
+    for (size_t p = 0; p < n; ++p)
+        for (uint32_t k = 0; k < N; ++k) {
+            const uint64_t v = h_plain[p * N + k];
+            if (v >= P) return set_error(HC_ERR_RANGE, "plaintext coefficient %llu >= P", (unsigned long long)v);
+            const bool neg = v > (P - 1) / 2;
+            for (uint32_t i = 0; i < L; ++i) {
+                const uint64_t q = ctx->q[i];
+                lifted[(p * L + i) * N + k] = neg ? q - (P - v) % q : v % q;
+            }
+        }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    HC_CUDA_TRY(cudaMemcpyAsync(d_out, lifted.data(), lifted.size() * 8, cudaMemcpyHostToDevice, s));
+    hc_status st = launch_ntt_fwd(ctx, d_out, d_out, n, s);
+    if (st != HC_OK) return st;
+    HC_CUDA_TRY(cudaStreamSynchronize(s));  // the host copy must outlive the upload
+    return HC_OK;
+}
+
+}  // extern "C"
