@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--batched-reps", type=int, default=20)
     ap.add_argument("--step-api", default="direct", choices=["direct", "plan"],
                     help="timed step: a one-layer plan replayed from a CUDA graph, or one hc_conv_ct_pt call")
+    ap.add_argument("--no-zp", action="store_true", help="skip the Z_P rotation section")
     ap.add_argument("--no-networks", action="store_true",
                     help="skip the whole-network plans (SqueezeNet-1.1 and ResNet-50, every linear layer)")
     ap.add_argument("--no-batched-plain", action="store_true", help="skip the one-launch-per-product comparisons")
@@ -487,6 +488,40 @@ def batched_uneven(L, stream, reps=20, with_plain=True):
     return out
 
 
+def zp_rotations(L, stream, reps=20):
+    """SecONNds-P's Z_P layer operations (Sec. 6.1, Sec. 2.1): key-switched slot
+    rotations of a batch of ciphertexts and one multiply-accumulate-rotate pass,
+    N = 8192, three limbs plus one special prime. Key, ciphertexts and weight
+    plaintexts are uniform residues: the cost does not depend on the values."""
+    import numpy as np
+    import torch
+    from paper_2506_11586_gb300.inputs import CANONICAL_PRIMES, T_PLAIN, Stream, uniform_residues
+    N, nl, n_ct, n_w = 8192, 3, 64, 16
+    moduli, special = CANONICAL_PRIMES[:nl], CANONICAL_PRIMES[nl]
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    s = Stream(5, 77)
+    key_h = uniform_residues(s, moduli + (special,), (nl, 2), N)        # [L][2][L+1][N]
+    key = L.hc_galois_key_create(ctx, special, 5, key_h, stream)
+    cts = torch.from_numpy(uniform_residues(s, moduli, (n_ct, 2), N).view(np.int64)).cuda()
+    rot = torch.empty_like(cts)
+    w = torch.from_numpy(uniform_residues(s, moduli, (n_w,), N).view(np.int64)).cuda()
+    acc = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
+    fr = lambda: L.hc_ct_rotate(ctx, key, cts, rot, stream)
+    fm = lambda: L.hc_mac_rotate(ctx, key, cts[:2 * nl * N], w, acc, stream)
+    for _ in range(3):
+        fr()
+        fm()
+    tr, tm = _events_ms(fr, reps, stream), _events_ms(fm, reps, stream)
+    out = {"workload": "zp_rotations_N8192_L3_special1_batch64_mac16", "rotations_per_call": n_ct,
+           "rotate_ms": statistics.median(tr), "rotations_per_s": n_ct / (statistics.median(tr) / 1e3),
+           "mac_rotate_terms": n_w, "mac_rotate_ms": statistics.median(tm),
+           "mac_rotate_p99_ms": max(tm),
+           "kernels_rotate": _kernel_trace(L, fr, "zp_rotate"), "kernels_mac_rotate": _kernel_trace(L, fm, "zp_mac")}
+    key.close()
+    ctx.close()
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -747,6 +782,9 @@ def run_gb300(args):
         wp = not args.no_batched_plain
         batched = {"squeezenet": batched_squeezenet(L, stream, args.batched_reps, wp),
                    "uneven": batched_uneven(L, stream, args.batched_reps, wp)}
+    zp = None
+    if rank == 0 and not args.no_zp:
+        zp = zp_rotations(L, stream, max(5, args.batched_reps))
     networks = None
     if rank == 0 and not args.no_networks:
         networks = whole_networks(L, stream, max(5, args.batched_reps // 2))
@@ -771,7 +809,7 @@ def run_gb300(args):
                                 else "hc_conv_ct_pt: direct call")},
         "p50_ms": statistics.median(step_ms), "p99_ms": p99, "layer_gbs": layer_gbs,
         "roofline": roofline, "other_entry_point": alt, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
-        "server_step": step_full, "preprocessing_modes": modes, "batched": batched, "networks": networks,
+        "server_step": step_full, "preprocessing_modes": modes, "batched": batched, "networks": networks, "zp": zp,
         "serving": serving, "gpu_launches": launches,
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in rprof.items()},
         "kernels_from": measured_with.split(";")[0],

@@ -229,3 +229,38 @@ def test_host_entry_point_blocks_of_output_channels(L, M):
     pageable = np.zeros(w.O * 2 * nl * N, dtype=np.uint64)
     L.hc_conv_ct_pt_host(ctx, w, np.ascontiguousarray(ct), pageable)
     assert np.array_equal(pageable, want)
+
+
+@pytest.mark.parametrize("G, B_blocks", [(2, 1), (3, 9), (4, 9), (5, 1), (8, 4), (15, 9), (16, 1)])
+def test_mac_channel_group_sweep(L, G, B_blocks, tmp_path):
+    """The blocked MAC sums G channel groups per output row in pairs of
+    accumulator chains, with channel x row tiles when a channel has several
+    rows (several spatial blocks) and a few-rows path otherwise (one block:
+    two rows per channel), and the last of an odd number of output channels
+    alone. Every output residue must equal the oracle's schoolbook sum for even
+    and odd G up to the special-form reduction's limit of 16 terms, with
+    offline weights, online weights and weights after a save / load round trip."""
+    N, nl = 4096, 2
+    moduli = CANONICAL_PRIMES[:nl]
+    Cw = 2
+    C_, M = G * Cw, 5
+    H = W = 8 if B_blocks == 4 else 6
+    Hw = Ww = {1: 8, 4: 6, 9: 4}[B_blocks]
+    p = conv.Partition(C_, H, W, M, 3, 3, 1, N, Cw, Hw, Ww)
+    assert p.G == G and p.B == B_blocks, (p.G, p.B)
+    s = Stream(91, G)
+    K = s.int8(M * C_ * 9).astype(np.int64).reshape(M, C_, 3, 3)
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    desc = L.make_desc(C_, H, W, M, 3, 3, pad=1, Cw=Cw, Hw=Hw, Ww=Ww)
+    ct = uniform_residues(s, moduli, (p.I, 2), N)
+    want = conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, moduli)
+    d_in = to_dev(ct)
+    offline = L.hc_weights_preprocess_ex(ctx, desc, K.astype(np.int8), L.HC_WEIGHTS_NTT_OFFLINE)
+    online = L.hc_weights_preprocess_ex(ctx, desc, K.astype(np.int8), L.HC_WEIGHTS_NTT_ONLINE)
+    L.hc_weights_save(offline, tmp_path / "w.bin")
+    loaded = L.hc_weights_load(ctx, tmp_path / "w.bin")
+    for name, w in (("offline", offline), ("online", online), ("loaded", loaded)):
+        out = torch.empty(p.O * 2 * nl * N, dtype=torch.int64, device="cuda")
+        L.hc_conv_ct_pt(ctx, w, d_in, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(out).reshape(p.O, 2, nl, N), want), name
