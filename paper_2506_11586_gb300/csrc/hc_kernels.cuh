@@ -37,12 +37,17 @@ template <> struct Variant<14, 0> { static constexpr int LOGC = 5, NP = 1, MINB 
 template <> struct Variant<14, 1> { static constexpr int LOGC = 4, NP = 1, MINB = 1; };   // T 1024, 64 regs
 template <> struct Variant<14, 2> { static constexpr int LOGC = 5, NP = 1, MINB = 1; };   // (same as 0)
 
-// shapes of the persistent TMA-fed inverse NTT (inverse kinds, variant 2, N <= 8192)
+// shapes of the persistent inverse NTTs (inverse kinds, variant 2): TMA-fed
+// double buffer at N = 4096, prefetching into the exchange buffer above
 template <int LOGN> struct InvTma;
 template <> struct InvTma<12> { using Cfg = NttCfg<12, 4, 1, 2>; };  // T 256, 2 x 32 KB
-template <> struct InvTma<13> { using Cfg = NttCfg<13, 4, 1, 1>; };  // T 512, 2 x 64 KB
+template <int LOGN> struct InvPf;
+template <> struct InvPf<13> { using Cfg = NttCfg<13, 5, 1, 2>; };   // T 256, 64 KB, two CTAs per SM
+template <> struct InvPf<14> { using Cfg = NttCfg<14, 5, 1, 1>; };   // T 512, 128 KB
 template <int LOGN, int V>
-constexpr bool use_inv_tma = V == 2 && LOGN <= 13;
+constexpr bool use_inv_tma = V == 2 && LOGN == 12;
+template <int LOGN, int V>
+constexpr bool use_inv_pf = V == 2 && LOGN >= 13;
 
 template <int LOGN, int V, bool SINGLE>
 using VCfg = NttCfg<LOGN, Variant<LOGN, V>::LOGC, SINGLE ? 1 : Variant<LOGN, V>::NP, Variant<LOGN, V>::MINB>;
@@ -402,6 +407,64 @@ k_ntt_inv_tma(const __grid_constant__ NttSegsT<NS> segs, uint32_t total, int *er
     }
 }
 
+// Persistent inverse NTT that prefetches: resident CTAs walk the units
+// (polynomial limbs) round robin; a CTA's one shared-memory buffer serves the
+// transform's exchanges, and once the last exchange has been read (the
+// transform's hook, before its last register round) every thread issues the
+// next unit's cp.async copies into it (8-byte words, coalesced in global
+// memory, swizzled in shared memory), so that the next load overlaps the last
+// round and the stores.
+template <class Cfg, int NS>
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
+k_ntt_inv_pf(const __grid_constant__ NttSegsT<NS> segs, uint32_t total)
+{
+    static_assert(Cfg::NP == 1, "one polynomial per unit");
+    extern __shared__ __align__(16) uint64_t sm[];  // [N], swizzled
+    constexpr int C = Cfg::C, N = Cfg::N, T = Cfg::T;
+    const int tid = threadIdx.x;
+    const uint32_t G = gridDim.x;
+
+    auto locate = [&](uint32_t u, uint32_t &si, uint32_t &limb, uint32_t &poly) {
+        si = 0;
+        while (si + 1 < segs.n && u >= segs.s[si + 1].cta_begin) ++si;
+        const uint32_t local = u - segs.s[si].cta_begin;
+        limb = segs.s[si].limb0 + local / segs.s[si].n_groups;
+        poly = local % segs.s[si].n_groups;
+    };
+    auto prefetch = [&](uint32_t u) {
+        uint32_t si, limb, poly;
+        locate(u, si, limb, poly);
+        const uint64_t *src = segs.s[si].in + ((size_t)poly * segs.s[si].L + limb) * N;
+#pragma unroll
+        for (int r = 0; r < C; ++r) {
+            const int e = tid + r * T;
+            cp_async8(sm + spos<Cfg>(e), src + e);
+        }
+        cp_async_commit();
+    };
+    uint32_t u = blockIdx.x;
+    if (u < total) prefetch(u);
+    for (; u < total; u += G) {
+        cp_async_wait_all();
+        __syncthreads();  // every thread's copies of this unit have landed
+        uint32_t si, limb, poly;
+        locate(u, si, limb, poly);
+        const NttSeg &sg = segs.s[si];
+        const LimbConst &lc = sg.limbs[limb];
+        uint64_t x[1][C];
+#pragma unroll
+        for (int r = 0; r < C; ++r) x[0][r] = sm[spos<Cfg>(tid * C + r)];
+        const uint32_t next = u + G;
+        inv_transform<Cfg>(x, sm, lc, lc.tw_i, tid, [&] {
+            __syncthreads();  // the last exchange has been read by every thread
+            if (next < total) prefetch(next);
+        });
+        uint64_t *dst = sg.out + ((size_t)poly * sg.L + limb) * N;
+#pragma unroll
+        for (int r = 0; r < C; ++r) dst[inv_out_elem<Cfg>(tid, r)] = x[0][r];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // One task of a standalone product: NP components (comp0, comp0 + 1, ...) of
 // one limb.  ct is the product's ciphertext [2][L][N], pt its NTT-domain
@@ -575,6 +638,36 @@ hc_status run_ntt_inv_tma(const NttSegsT<NS> &segs, int *err, cudaStream_t s)
     return after_launch("k_ntt_inv_tma");
 }
 
+// persistent prefetching inverse NTT: segs' cta_begin are unit offsets
+// (n_groups polynomials x L limbs per segment); one launch of resident CTAs
+template <class Cfg, int NS>
+hc_status run_ntt_inv_pf(const NttSegsT<NS> &segs, cudaStream_t s)
+{
+    uint32_t total = 0;
+    for (uint32_t i = 0; i < segs.n; ++i) total = segs.s[i].cta_begin + segs.s[i].n_groups * seg_limbs(segs.s[i]);
+    if (total == 0) return HC_OK;
+    constexpr size_t smem = Cfg::SMEM_BYTES;
+    auto kern = k_ntt_inv_pf<Cfg, NS>;
+    static std::atomic<int> resident[32];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int r = resident[dev & 31].load();
+    if (r == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0, sms = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::T, smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_error(e, "k_ntt_inv_pf set-up");
+        if (per_sm < 1) return set_error(HC_ERR_UNSUPPORTED, "k_ntt_inv_pf does not fit on an SM");
+        r = per_sm * sms;
+        resident[dev & 31].store(r);
+    }
+    const uint32_t grid = total < (uint32_t)r ? total : (uint32_t)r;
+    ProfileScope ps(kname<Cfg>(KK_INV), s);
+    kern<<<grid, Cfg::T, smem, s>>>(segs, total);
+    return after_launch("k_ntt_inv_pf");
+}
+
 // one-segment launch: n_groups CTAs per limb
 inline NttSegs1 one_seg(const hc_ctx *ctx, const uint64_t *in, uint64_t *out, size_t n_groups)
 {
@@ -657,13 +750,18 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
 {
     using Fused = VCfg<LOGN, V, false>;
     using Single = VCfg<LOGN, V, true>;
-    if constexpr (use_inv_tma<LOGN, V>) {
-        using TC = typename InvTma<LOGN>::Cfg;
+    if constexpr (use_inv_tma<LOGN, V> || use_inv_pf<LOGN, V>) {
+        auto run = [&](const auto &segs) {
+            if constexpr (use_inv_tma<LOGN, V>)
+                return detail::run_ntt_inv_tma<typename InvTma<LOGN>::Cfg>(segs, ctx->d_flag + 1, s);
+            else
+                return detail::run_ntt_inv_pf<typename InvPf<LOGN>::Cfg>(segs, s);
+        };
         if (kind == KK_INV || kind == KK_INVCT) {
             const size_t polys = kind == KK_INV ? a.n : 2 * a.n;
             if (polys == 0) return HC_OK;
             if (polys * ctx->L > 0x7fffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
-            return detail::run_ntt_inv_tma<TC>(detail::one_seg(ctx, a.in, a.out, polys), ctx->d_flag + 1, s);
+            return run(detail::one_seg(ctx, a.in, a.out, polys));
         }
         if (kind == KK_INVCT_SEGS) {
             NttSegs segs = *a.segs;
@@ -673,7 +771,7 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
                 segs.s[i].cta_begin = begin;
                 begin += segs.s[i].n_groups * seg_limbs(segs.s[i]);
             }
-            return detail::run_ntt_inv_tma<TC>(segs, ctx->d_flag + 1, s);
+            return run(segs);
         }
     }
     switch (kind) {

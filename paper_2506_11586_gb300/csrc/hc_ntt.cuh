@@ -265,18 +265,25 @@ __device__ __forceinline__ void fwd_transform(uint64_t (&x)[Cfg::NP][Cfg::C], ui
     }
 }
 
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // inverse: x holds element tid*C + r (contiguous) on entry, canonical values
 // < q; on exit the last-round layout (element tid + r'*T for the slot order of
-// inv_elem), canonical.
-template <class Cfg, int R = 0>
+// inv_elem), canonical.  hook() runs (in every thread) right before the last
+// round, once this transform has finished with shared memory: after its last
+// exchange, or after the caller's reads when there is one round only.
+template <class Cfg, int R = 0, class Hook = NoHook>
 __device__ __forceinline__ void inv_transform(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm,
                                               const LimbConst &lc, const ulonglong2 *__restrict__ tw,
-                                              int tid)
+                                              int tid, const Hook &hook = Hook{})
 {
+    if constexpr (R + 1 == Cfg::NROUNDS) hook();
     inv_round<Cfg, R>(x, lc, tw, tid);
     if constexpr (R + 1 < Cfg::NROUNDS) {
         inv_exchange<Cfg, R>(x, sm, tid);
-        inv_transform<Cfg, R + 1>(x, sm, lc, tw, tid);
+        inv_transform<Cfg, R + 1>(x, sm, lc, tw, tid, hook);
     }
 }
 

@@ -95,9 +95,11 @@ __global__ void k_ks_mac(const uint64_t *__restrict__ dig, const uint64_t *__res
     }
 }
 
-// out[ct][comp][i][k] = (comp == 0 ? sigma_g(c0)[i][k] : 0) + (u_i - [u_sp]) / p_sp mod q_i
-__global__ void k_ks_mod_down(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ u,
-                              uint64_t *__restrict__ out, const LimbConst *__restrict__ lq,
+// out[ct][comp][i][k] = (comp == 0 ? sigma_g(c0)[i][k] : 0) + (u_i - [u_sp]) / p_sp
+//                       (+ add[ct][comp][i][k] when add is given) mod q_i
+// (add may be out itself: each element is read before it is written, by the same thread)
+__global__ void k_ks_mod_down(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ u, uint64_t *out,
+                              const uint64_t *add, const LimbConst *__restrict__ lq,
                               const ModDown *__restrict__ md, uint64_t special, uint32_t L, uint32_t N,
                               uint32_t ginv, size_t total)
 {
@@ -124,7 +126,21 @@ __global__ void k_ks_mod_down(const uint64_t *__restrict__ ct, const uint64_t *_
             const uint64_t a = src < N ? c0[src] : negmod(c0[src - N], q);
             v = csub(v + a, q);
         }
-        out[((c * 2 + comp) * L + i) * N + k] = v;
+        const size_t o = ((c * 2 + comp) * L + i) * N + k;
+        if (add) v = csub(v + add[o], q);
+        out[o] = v;
+    }
+}
+
+// term list of n outputs with one term each: output j = ciphertext 0 times plaintext j
+__global__ void k_single_terms(uint32_t *term_ptr, uint32_t *terms, uint32_t n)
+{
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += gridDim.x * blockDim.x) {
+        term_ptr[j] = j;
+        if (j < n) {
+            terms[2 * j] = 0;
+            terms[2 * j + 1] = j;
+        }
     }
 }
 
@@ -143,8 +159,9 @@ struct Buf {
 
 bool key_ok(const hc_galois_key *k) { return k && k->magic == kMagicGaloisKey; }
 
+// out = rotate(in) (+ add, elementwise, when given; add may equal out, not in)
 hc_status rotate_into(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *in, uint64_t *out, size_t n,
-                      cudaStream_t s)
+                      cudaStream_t s, const uint64_t *add = nullptr)
 {
     const uint32_t L = ctx->L, N = ctx->N;
     const size_t dig_words = n * L * (L + 1) * (size_t)N, u_words = n * 2 * (L + 1) * (size_t)N;
@@ -171,7 +188,7 @@ hc_status rotate_into(const hc_ctx *ctx, const hc_galois_key *key, const uint64_
     if (st != HC_OK) return st;
     ProfileScope ps("k_ks_mod_down", s);
     const size_t total = n * 2 * L * (size_t)N;
-    k_ks_mod_down<<<grid_of(total), 256, 0, s>>>(in, uu, out, ctx->d_limbs, key->d_md, key->special, L, N,
+    k_ks_mod_down<<<grid_of(total), 256, 0, s>>>(in, uu, out, add, ctx->d_limbs, key->d_md, key->special, L, N,
                                                   key->ginv, total);
     HC_CUDA_TRY(cudaGetLastError());
     return HC_OK;
@@ -290,23 +307,34 @@ hc_status hc_mac_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint6
     hc_status st = check_inputs(ctx, d_ct, 2, s);
     if (st == HC_OK) st = check_inputs(ctx, d_w_ntt, n, s);
     if (st != HC_OK) return st;
-    const size_t ct_words = (size_t)2 * ctx->L * ctx->N, pt_words = (size_t)ctx->L * ctx->N;
+    // The products x * w_i do not depend on the accumulator: all n run first, in one
+    // launch (forward NTT of x once, then one MAC + inverse NTT per plaintext);
+    // the chain then only rotates and adds, the add fused into the key switch's
+    // last kernel:  P_i = x * w_i;  acc = P_{n-1};  acc = rot(acc) + P_i, i = n-2 .. 0.
+    const uint32_t L = ctx->L, N = ctx->N;
+    const size_t ct_words = (size_t)2 * L * N;
+    const size_t term_words = ((size_t)3 * n + 1 + 1) / 2;  // n + 1 offsets and 2n indices, as uint32
     Buf tmp(s);
-    tmp.p = dev_alloc(2 * ct_words * 8, s);
+    tmp.p = dev_alloc(((size_t)(n + 1) * ct_words + term_words) * 8, s);
     if (!tmp.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
-    uint64_t *bufs[2] = {(uint64_t *)tmp.p, (uint64_t *)tmp.p + ct_words};
-    // the last iteration writes d_out: pick the starting buffer by the parity of n
-    uint32_t cur = 0;
-    uint64_t *acc = n == 1 ? d_out : bufs[cur];
-    st = launch_product(ctx, d_ct, d_w_ntt + (size_t)(n - 1) * pt_words, nullptr, acc, 1, false, s);
-    for (uint32_t i = n - 1; st == HC_OK && i-- > 0;) {
-        uint64_t *next = i == 0 ? d_out : bufs[cur ^ 1];
-        st = rotate_into(ctx, key, acc, next, 1, s);
-        if (st == HC_OK) st = launch_product(ctx, d_ct, d_w_ntt + (size_t)i * pt_words, nullptr, next, 1, true, s);
-        acc = next;
-        cur ^= 1;
+    uint64_t *ctn = (uint64_t *)tmp.p, *prods = ctn + ct_words;
+    uint32_t *term_ptr = reinterpret_cast<uint32_t *>(prods + (size_t)n * ct_words), *terms = term_ptr + n + 1;
+    st = launch_ntt_fwd(ctx, d_ct, ctn, 2, s);
+    if (st != HC_OK) return st;
+    k_single_terms<<<(n + 256) / 256, 256, 0, s>>>(term_ptr, terms, n);
+    HC_CUDA_TRY(cudaGetLastError());
+    uint64_t *last = n == 1 ? d_out : prods;  // P_0 of a one-term iteration is the result
+    st = launch_mac_intt(ctx, ctn, d_w_ntt, MacTerms{term_ptr, terms}, last, n, s);
+    if (st != HC_OK || n == 1) return st;
+    const uint64_t *acc = prods + (size_t)(n - 1) * ct_words;
+    for (uint32_t i = n - 1; i-- > 0;) {
+        uint64_t *pi = prods + (size_t)i * ct_words;
+        uint64_t *dst = i == 0 ? d_out : pi;
+        st = rotate_into(ctx, key, acc, dst, 1, s, pi);
+        if (st != HC_OK) return st;
+        acc = dst;
     }
-    return st;
+    return HC_OK;
 }
 
 hc_status hc_zp_plain_preprocess(const hc_ctx *ctx, uint64_t P, const uint64_t *h_plain, size_t n, uint64_t *d_out,

@@ -149,3 +149,47 @@ def test_variant_argument_errors(L):
         L.hc_ctx_set_variant(ctx, 99, 0)
     with pytest.raises(L.HcError):
         L.hc_ctx_set_variant(ctx, L.KIND_MAC_INTT, L.N_VARIANTS)
+
+
+@pytest.mark.parametrize("N,nl,n", [(4096, 2, 700), (8192, 3, 400), (16384, 4, 120)])
+def test_persistent_inverse_many_units(L, N, nl, n):
+    """Variant 2 of the inverse transforms is a persistent kernel whose resident
+    CTAs walk more polynomial limbs than there are CTAs: each loads the next
+    limb while it finishes the current one. With n*L limbs well above the
+    resident count (two or one CTAs per SM), every limb must match variant 0
+    bit for bit, as a plain inverse NTT and as the inverse NTT of ciphertexts
+    (two components per ciphertext), and the round trip must give the input."""
+    moduli = CANONICAL_PRIMES[:nl]
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    a = uniform_residues(Stream(12, N), moduli, (n,), N)
+    d0 = to_dev(a)
+    L.hc_ntt_fwd(ctx, d0)
+    outs = []
+    for v in (0, 2):
+        L.hc_ctx_set_variant(ctx, L.KIND_NTT_INV, v)
+        d = d0.clone()
+        L.hc_ntt_inv(ctx, d)
+        torch.cuda.synchronize()
+        outs.append(to_host(d))
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[1].reshape(a.shape), a)
+    # ciphertext form (KIND_NTT_INV_CT): a 1x1 layer with O*2*L output limbs
+    C_, H, W, M = 8, 12, 12, 160
+    st = Stream(13, N)
+    K = st.int8(M * C_).astype(np.int64).reshape(M, C_, 1, 1)
+    p = conv.canonical_partition(C_, H, W, M, 1, 1, 0, N)
+    assert p.O * 2 * nl > 600
+    ct = uniform_residues(st, moduli, (p.I, 2), N)
+    w = L.hc_weights_preprocess(ctx, L.make_desc(C_, H, W, M, 1, 1, pad=0), K.astype(np.int8))
+    d_in = to_dev(ct)
+    got = []
+    for v in (0, 2):
+        L.hc_ctx_set_variant(ctx, L.KIND_NTT_INV_CT, v)
+        out = torch.full((p.O * 2 * nl * N,), -1, dtype=torch.int64, device="cuda")
+        L.hc_conv_ct_pt(ctx, w, d_in, out)
+        torch.cuda.synchronize()
+        got.append(to_host(out).reshape(p.O, 2, nl, N))
+    assert np.array_equal(got[0], got[1])
+    ks = sample_indices(N, 8, M)
+    want = conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, moduli, ks)
+    assert np.array_equal(got[1][..., ks], want)
