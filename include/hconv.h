@@ -414,7 +414,9 @@ hc_status hc_ct_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64
  * and n NTT-domain plaintexts d_w_ntt [n][L][N] (hc_zp_plain_preprocess),
  *   acc = d_ct * w_{n-1};  for i = n-2 .. 0: acc = rotate(acc) + d_ct * w_i;
  * d_out [2][L][N] = acc (coefficient domain; must not overlap d_ct).  Decrypts
- * to sum_i rot^i(m * w_i) slot-wise mod P.  Errors as hc_ct_rotate. */
+ * to sum_i rot^i(m * w_i) slot-wise mod P.  The n products run first, in one
+ * launch; scratch of (n + 1) ciphertexts plus one rotation's comes from the
+ * allocator.  Errors as hc_ct_rotate. */
 hc_status hc_mac_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct,
                         const uint64_t *d_w_ntt, uint32_t n, uint64_t *d_out, void *cuda_stream);
 
