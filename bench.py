@@ -134,6 +134,28 @@ def kernel_work(name, geo, N, L):
     return {"bytes": poly * (2 * I + P + 2 * O), "imad_eq": mac + 2 * O * L * bfly * IMAD_EQ_BUTTERFLY}
 
 
+def conv_imad_eq(I, O, products, N, L):
+    """IMAD-equivalents of one conv layer: forward NTT of 2I, MAC, inverse NTT of 2O polynomial limbs."""
+    bfly = (N // 2) * (N.bit_length() - 1)
+    return (2 * I * L * bfly * IMAD_EQ_BUTTERFLY + products * 2 * L * N * IMAD_EQ_MAC_TERM
+            + O * 2 * L * N * IMAD_EQ_REDUCE + 2 * O * L * bfly * IMAD_EQ_BUTTERFLY)
+
+
+def product_imad_eq(N, L):
+    """IMAD-equivalents of one standalone ct x pt product: NTT, pointwise product, INTT of 2L limbs."""
+    bfly = (N // 2) * (N.bit_length() - 1)
+    return 2 * L * (2 * bfly * IMAD_EQ_BUTTERFLY + N * IMAD_EQ_BUTTERFLY)
+
+
+def roofline_fracs(nbytes, imad_eq, ms):
+    """Fractions of the measured HBM peak and of the integer-pipe peak, and the larger (the bound)."""
+    peak, src = measured_peaks()
+    hbm = nbytes / (ms / 1e3) / 1e9 / peak
+    alu = imad_eq / (ms / 1e3) / 1e12 / alu_peak_imad_eq()
+    return {"hbm_frac": hbm, "alu_frac": alu, "bound": "alu" if alu >= hbm else "hbm",
+            "imad_eq": imad_eq, "hbm_peak_source": src}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -363,7 +385,8 @@ def batched_squeezenet(L, stream, reps=20, with_plain=True):
            "speedup_vs_plain": pp[0] / ms if pp[0] is not None else None,
            "bit_exact_vs_per_layer": exact_layers, "bit_exact_vs_plain": exact_plain, "kernels": kern,
            "offline_weight_ntt_s": offline_s,
-           "variants": {name: L.hc_ctx_get_variant(ctx, k) for name, k in KIND_NAMES.items()}}
+           "variants": {name: L.hc_ctx_get_variant(ctx, k) for name, k in KIND_NAMES.items()},
+           "roofline": roofline_fracs(nbytes, sum(conv_imad_eq(w.I, w.O, w.products, 8192, 3) for w in ws), ms)}
     plan.close()
     return out
 
@@ -430,7 +453,9 @@ def whole_networks(L, stream, reps=10):
                      "value": products / (ms / 1e3), "unit": UNIT, "alg_gbs": nbytes / (ms / 1e3) / 1e9,
                      "per_layer_ms": statistics.median(pl), "speedup_vs_per_layer": statistics.median(pl) / ms,
                      "bit_exact_vs_per_layer": exact, "offline_weight_ntt_s": offline_s, "kernels": kern,
-                     "variants": {k: L.hc_ctx_get_variant(ctx, v) for k, v in KIND_NAMES.items()}}
+                     "variants": {k: L.hc_ctx_get_variant(ctx, v) for k, v in KIND_NAMES.items()},
+                     "roofline": roofline_fracs(nbytes, sum(conv_imad_eq(w.I, w.O, w.products, N, nl)
+                                                            for w in ws), ms)}
         plan.close()
         del items, batched
         for w in ws:
@@ -483,7 +508,8 @@ def batched_uneven(L, stream, reps=20, with_plain=True):
            "plain_ms": statistics.median(pp) if pp[0] is not None else None, "plain_launches": products,
            "speedup_vs_per_degree": statistics.median(pd) / ms,
            "speedup_vs_plain": statistics.median(pp) / ms if pp[0] is not None else None,
-           "bit_exact_vs_per_degree": exact_deg, "bit_exact_vs_plain": exact_plain, "kernels": kern}
+           "bit_exact_vs_per_degree": exact_deg, "bit_exact_vs_plain": exact_plain, "kernels": kern,
+           "roofline": roofline_fracs(nbytes, sum(n * product_imad_eq(c.N, c.L) for c, _, _, _, n in items), ms)}
     plan.close()
     return out
 
