@@ -37,6 +37,15 @@ Multiply-accumulate-rotate.  For ciphertext x and NTT-preprocessed weights
 w_0 .. w_{n-1}: acc = x * w_{n-1}; for i = n-2 .. 0: acc = rot(acc) + x * w_i.
 The result decrypts to sum_i rot^i(m * w_i) slot-wise mod P.
 
+Matrix-vector products with it (the diagonal method).  A vector v of length
+n, n a power of two dividing N/2, is held periodically: slot (r, t) holds
+v[t mod n] in both rows r.  For an n x n matrix W put
+    w_i[r][t] = W[(t - i) mod n][t mod n],   i < n;
+then sum_i rot^i(vtilde * w_i) at slot (r, j) is sum_i W[j][(j + i) mod n]
+v[(j + i) mod n] = (W v)[j mod n]: the product, held periodically again, so
+the output has the input's format.  A rectangular matrix is padded with zero
+rows and columns to the next such n.
+
 Parity: pinned by SIMD encode/decode round trips and slot-wise products, the
 automorphism's closed form on monomials and its action on slots, decryption of
 rotated ciphertexts to rotated slot vectors, the key-switching noise bound,
@@ -246,6 +255,40 @@ def slot_mac_rotate(m, ws, P):
     for i, w in enumerate(ws):
         acc = (acc + np.roll((m * np.asarray(w, dtype=object)) % P, -i, axis=1)) % P
     return acc.astype(np.int64)
+
+
+def periodic_slots(v, N):
+    """Vector v of length n (a power of two dividing N/2) -> slots [2][N/2], slot (r, t) = v[t mod n]."""
+    v = np.asarray(v, dtype=np.int64)
+    n = v.size
+    assert n >= 1 and (N // 2) % n == 0 and n & (n - 1) == 0
+    return np.tile(v, (2, (N // 2) // n))
+
+
+def matvec_size(n_out, n_in):
+    """The padded size n: the smallest power of two >= max(n_out, n_in)."""
+    n = 1
+    while n < max(n_out, n_in):
+        n *= 2
+    return n
+
+
+def matvec_diagonals(Wm, N, P):
+    """n x n (after padding) weight slot vectors [n][2][N/2] of the diagonal method for the
+    integer matrix Wm [n_out][n_in], residues mod P: w_i[r][t] = W[(t - i) mod n][t mod n]."""
+    Wm = np.asarray(Wm, dtype=np.int64)
+    n_out, n_in = Wm.shape
+    n = matvec_size(n_out, n_in)
+    assert (N // 2) % n == 0
+    Wp = np.zeros((n, n), dtype=np.int64)
+    Wp[:n_out, :n_in] = Wm % P
+    t = np.arange(N // 2)
+    out = np.zeros((n, 2, N // 2), dtype=np.int64)
+    for i in range(n):
+        row = Wp[(t - i) % n, t % n]
+        out[i, 0] = row
+        out[i, 1] = row
+    return out
 
 
 def bfv_params(N, moduli, P):

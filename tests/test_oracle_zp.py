@@ -131,3 +131,40 @@ def test_mac_rotate_decrypts_to_the_slot_formula():
     out = zp.mac_rotate(ct, lifts, gk, 5, KP)
     got = bfv.decrypt_at(params, sk, out, list(range(N)))
     assert np.array_equal(zp.decode(got.astype(np.uint64), N, P), zp.slot_mac_rotate(m, ws, P))
+
+
+@pytest.mark.parametrize("n_out, n_in", [(1, 1), (3, 5), (8, 8), (16, 11), (64, 64)])
+def test_matvec_diagonals_give_the_matrix_product(n_out, n_in):
+    """The diagonal method on slot vectors (no encryption): sum_i rot^i(vtilde * w_i)
+    equals W v mod P at every slot, held periodically, for square, rectangular and
+    degenerate (1 x 1) matrices; checked against a plain integer matrix product."""
+    s = Stream(76, n_out * 100 + n_in)
+    Wm = s.below(P, n_out * n_in).astype(np.int64).reshape(n_out, n_in)
+    v = s.below(P, n_in).astype(np.int64)
+    n = zp.matvec_size(n_out, n_in)
+    vp = np.zeros(n, dtype=np.int64)
+    vp[:n_in] = v
+    ws = zp.matvec_diagonals(Wm, N, P)
+    assert ws.shape == (n, 2, N // 2)
+    got = zp.slot_mac_rotate(zp.periodic_slots(vp, N), list(ws), P)
+    want = np.zeros(n, dtype=object)
+    for j in range(n_out):                                   # plain matrix product, big integers
+        want[j] = sum(int(Wm[j, k]) * int(v[k]) for k in range(n_in)) % P
+    assert np.array_equal(got, zp.periodic_slots(want.astype(np.int64), N))
+
+
+def test_matvec_through_encryption():
+    """The same product through BFV: encode the periodic input, encrypt, run the
+    oracle's multiply-accumulate-rotate with the encoded diagonals, decrypt, decode."""
+    n = 4
+    s = Stream(77, 0)
+    Wm = s.below(P, n * n).astype(np.int64).reshape(n, n)
+    v = s.below(P, n).astype(np.int64)
+    s2, sk, gk = _keys(78)
+    params = zp.bfv_params(N, KP.moduli, P)
+    ct = _encrypt(s2, params, sk, zp.encode(zp.periodic_slots(v, N), N, P))
+    lifts = [zp.lift_plain(zp.encode(w, N, P), P, KP.moduli) for w in zp.matvec_diagonals(Wm, N, P)]
+    out = zp.mac_rotate(ct, lifts, gk, 5, KP)
+    dec = bfv.decrypt_at(params, sk, out, list(range(N)))
+    want = (Wm.astype(object) @ v.astype(object)) % P
+    assert np.array_equal(zp.decode(dec.astype(np.uint64), N, P), zp.periodic_slots(want.astype(np.int64), N))
