@@ -516,9 +516,10 @@ def batched_uneven(L, stream, reps=20, with_plain=True):
 
 def zp_rotations(L, stream, reps=20):
     """SecONNds-P's Z_P layer operations (Sec. 6.1, Sec. 2.1): key-switched slot
-    rotations of a batch of ciphertexts and one multiply-accumulate-rotate pass,
-    N = 8192, three limbs plus one special prime. Key, ciphertexts and weight
-    plaintexts are uniform residues: the cost does not depend on the values."""
+    rotations of a batch of ciphertexts, one multiply-accumulate-rotate pass, SIMD
+    encoding and a 64 x 64 matrix-vector layer, N = 8192, three limbs plus one
+    special prime, a 37-bit P. Key, ciphertexts and weights are uniform residues:
+    the cost does not depend on the values."""
     import numpy as np
     import torch
     from paper_2506_11586_gb300.inputs import CANONICAL_PRIMES, T_PLAIN, Stream, uniform_residues
@@ -543,9 +544,62 @@ def zp_rotations(L, stream, reps=20):
            "mac_rotate_terms": n_w, "mac_rotate_ms": statistics.median(tm),
            "mac_rotate_p99_ms": max(tm),
            "kernels_rotate": _kernel_trace(L, fr, "zp_rotate"), "kernels_mac_rotate": _kernel_trace(L, fm, "zp_mac")}
+    # SIMD encoding of 256 slot vectors, and a 64 x 64 matrix-vector layer (diagonal method:
+    # weights preprocessed once, then 64 products and 63 rotations per input ciphertext)
+    P = zp_plain_prime(N)
+    ctx_p = L.hc_ctx_create(N, [P], P)
+    n_enc = 256
+    slots = torch.from_numpy(s.below(P, n_enc * N).view(np.int64)).cuda()
+    poly = torch.empty_like(slots)
+    fe = lambda: L.hc_zp_encode(ctx_p, slots, poly, stream)
+    fe()
+    te = _events_ms(fe, reps, stream)
+    Wm = s.below(P, 64 * 64).reshape(64, 64)
+    wv = torch.empty(64 * nl * N, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_terms = L.hc_zp_matvec_preprocess(ctx, ctx_p, Wm, wv, stream)
+    pre_s = time.perf_counter() - t0
+    fv = lambda: L.hc_mac_rotate(ctx, key, cts[:2 * nl * N], wv, acc, stream)
+    fv()
+    tv = _events_ms(fv, max(3, reps // 4), stream)
+    out.update({"encode_vectors_per_call": n_enc, "encode_ms": statistics.median(te),
+                "encodes_per_s": n_enc / (statistics.median(te) / 1e3),
+                "matvec": {"n": n_terms, "preprocess_s": pre_s, "ms": statistics.median(tv),
+                           "rotations": n_terms - 1, "products": n_terms}})
+    ctx_p.close()
     key.close()
     ctx.close()
     return out
+
+
+def zp_plain_prime(N, bits=37):
+    """The largest prime below 2^bits that is 1 mod 2N (SecONNds-P's 37-bit plaintext modulus)."""
+    def is_prime(n):                       # deterministic Miller-Rabin for n < 3.3e24
+        if n < 2:
+            return False
+        bases = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41)
+        for b in bases:
+            if n % b == 0:
+                return n == b
+        d, r = n - 1, 0
+        while d % 2 == 0:
+            d, r = d // 2, r + 1
+        for b in bases:
+            x = pow(b, d, n)
+            if x in (1, n - 1):
+                continue
+            for _ in range(r - 1):
+                x = x * x % n
+                if x == n - 1:
+                    break
+            else:
+                return False
+        return True
+    p = ((1 << bits) - 1) // (2 * N) * (2 * N) + 1
+    while p >= (1 << bits) or not is_prime(p):
+        p -= 2 * N
+    return p
 
 
 def run_gb300(args):

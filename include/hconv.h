@@ -428,6 +428,50 @@ hc_status hc_mac_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint6
 hc_status hc_zp_plain_preprocess(const hc_ctx *ctx, uint64_t P, const uint64_t *h_plain, size_t n,
                                  uint64_t *d_out, void *cuda_stream);
 
+/* ------------------------------------- Z_P layers: SIMD encoding, matvec --
+ * Plaintext vectors of SecONNds-P's linear layers live in Z_P^N (Sec. 6.1),
+ * P a prime = 1 mod 2N, in the BFV batching layout: slot (r, c), r in {0, 1},
+ * c < N/2, of a polynomial p is p(zeta^e) with e = 5^c (r = 0) or -5^c (r = 1)
+ * mod 2N, zeta the smallest primitive 2N-th root mod P; sigma_5 (the Galois
+ * element of hc_ct_rotate) rotates both rows left by one slot.
+ *
+ * ctx_p is a context with the single modulus P: hc_ctx_create(N, &P, 1, P, ...)
+ * (so 2^32 < P < 2^50).
+ *
+ * hc_zp_encode: d_slots [n][2][N/2] values in [0, P) -> d_poly [n][N]
+ * coefficients in [0, P) with those slots (scatter to the slots' NTT indices,
+ * inverse NTT mod P).  hc_zp_decode: the inverse map.  Device buffers, must
+ * not overlap; decoding takes n*N*8 bytes of scratch from the allocator.
+ * Errors: HC_ERR_INVALID_ARG (not a one-modulus context, null or overlapping
+ * buffers), HC_ERR_RANGE (checked mode, a value >= P), HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_zp_encode(const hc_ctx *ctx_p, const uint64_t *d_slots, size_t n, uint64_t *d_poly,
+                       void *cuda_stream);
+hc_status hc_zp_decode(const hc_ctx *ctx_p, const uint64_t *d_poly, size_t n, uint64_t *d_slots,
+                       void *cuda_stream);
+
+/* Device-side form of hc_zp_plain_preprocess: d_poly [n][N] in [0, P) lifted
+ * centered ((P-1)/2 < v -> v - P) into every q_i of ctx and forward-NTT'd
+ * into d_out [n][L][N].  P must be odd and below every q_i.  Asynchronous.
+ * Errors: HC_ERR_INVALID_ARG, HC_ERR_CUDA. */
+hc_status hc_zp_lift_ntt(const hc_ctx *ctx, uint64_t P, const uint64_t *d_poly, size_t n, uint64_t *d_out,
+                         void *cuda_stream);
+
+/* Matrix-vector weights for hc_mac_rotate by the diagonal method (the
+ * iterative multiply-accumulate-rotate kernel of HELiKs, Sec. 6.1).  h_W is
+ * host [n_out][n_in] residues mod P = ctx_p's modulus.  With n the smallest
+ * power of two >= max(n_out, n_in) (n <= N/2), a vector v of length n_in is
+ * held periodically in both slot rows (slot (r, t) = v[t mod n], zero past
+ * n_in); the n plaintexts w_i[r][t] = W[(t - i) mod n][t mod n] (W zero-padded
+ * to n x n) are encoded on the device, lifted into ctx's q_i and NTT'd into
+ * d_out [n][L][N] (out_words >= n*L*N); *n_terms = n.  hc_mac_rotate with
+ * these n plaintexts then decrypts to W v, held the same way (slot (r, j) =
+ * (W v)[j mod n]).  Synchronises the stream.  Errors: HC_ERR_INVALID_ARG
+ * (different N, empty or too large matrix, d_out too small), HC_ERR_RANGE (an
+ * entry >= P), HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_zp_matvec_preprocess(const hc_ctx *ctx, const hc_ctx *ctx_p, const uint64_t *h_W, uint32_t n_out,
+                                  uint32_t n_in, uint64_t *d_out, size_t out_words, uint32_t *n_terms,
+                                  void *cuda_stream);
+
 /* ------------------------------------------------------------------ plans --
  * Batching across layers, products and ring degrees (Sec. 6.2; the paper's
  * closing remarks on accelerating composite HE operations).  A plan binds a

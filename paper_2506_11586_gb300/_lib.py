@@ -112,6 +112,11 @@ _SIGS = {
     "hc_ct_rotate": (C.c_int, [_P, _P, _P, _P, C.c_size_t, _P]),
     "hc_mac_rotate": (C.c_int, [_P, _P, _P, _P, C.c_uint32, _P, _P]),
     "hc_zp_plain_preprocess": (C.c_int, [_P, C.c_uint64, _P, C.c_size_t, _P, _P]),
+    "hc_zp_encode": (C.c_int, [_P, _P, C.c_size_t, _P, _P]),
+    "hc_zp_decode": (C.c_int, [_P, _P, C.c_size_t, _P, _P]),
+    "hc_zp_lift_ntt": (C.c_int, [_P, C.c_uint64, _P, C.c_size_t, _P, _P]),
+    "hc_zp_matvec_preprocess": (C.c_int, [_P, _P, _P, C.c_uint32, C.c_uint32, _P, C.c_size_t,
+                                          C.POINTER(C.c_uint32), _P]),
     "hc_conv_server_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "hc_conv_server_step_sparse": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "hc_plan_create": (C.c_int, [_P, C.c_size_t, C.POINTER(_P)]),
@@ -475,6 +480,34 @@ def hc_zp_plain_preprocess(ctx, P, h_plain, out, stream=None):
     h = np.ascontiguousarray(h_plain, dtype=np.uint64)
     n = h.size // ctx.N
     _check(lib().hc_zp_plain_preprocess(ctx.ptr, int(P), C.c_void_p(h.ctypes.data), n, _dptr(out), _stream(stream)))
+
+
+def hc_zp_encode(ctx_p, slots, poly, stream=None):
+    """slots: device [n][2][N/2] values in [0, P); poly: device [n][N] (ctx_p: the one-modulus P context)."""
+    n = _npolys(ctx_p, slots)
+    _check(lib().hc_zp_encode(ctx_p.ptr, _dptr(slots), n, _dptr(poly), _stream(stream)))
+
+
+def hc_zp_decode(ctx_p, poly, slots, stream=None):
+    n = _npolys(ctx_p, poly)
+    _check(lib().hc_zp_decode(ctx_p.ptr, _dptr(poly), n, _dptr(slots), _stream(stream)))
+
+
+def hc_zp_lift_ntt(ctx, P, poly, out, stream=None):
+    """poly: device [n][N] in [0, P); out: device [n][L][N]."""
+    n = poly.numel() // ctx.N
+    _check(lib().hc_zp_lift_ntt(ctx.ptr, int(P), _dptr(poly), n, _dptr(out), _stream(stream)))
+
+
+def hc_zp_matvec_preprocess(ctx, ctx_p, W, out, stream=None):
+    """W: host [n_out][n_in] residues mod P; out: device tensor of at least n*L*N words.
+    Returns n, the number of plaintexts written (the iteration's length)."""
+    Wm = np.ascontiguousarray(W, dtype=np.uint64)
+    n_out, n_in = Wm.shape
+    nt = C.c_uint32()
+    _check(lib().hc_zp_matvec_preprocess(ctx.ptr, ctx_p.ptr, C.c_void_p(Wm.ctypes.data), n_out, n_in, _dptr(out),
+                                         out.numel(), C.byref(nt), _stream(stream)))
+    return nt.value
 
 
 class Plan(_Handle):

@@ -127,3 +127,91 @@ def test_rotation_argument_errors(L):
         L.hc_zp_plain_preprocess(ctx, P, np.full(N, P, dtype=np.uint64), torch.empty(nl * N, dtype=torch.int64,
                                                                                      device="cuda"))
     assert e.value.status == L.HC_ERR_RANGE
+
+
+def _plain_ctx(L, N, P):
+    return L.hc_ctx_create(N, [P], P)
+
+
+@pytest.mark.parametrize("N", [4096, 8192])
+def test_simd_encode_decode_match_oracle(L, N):
+    """hc_zp_encode / hc_zp_decode against the oracle's BFV batching (the slot
+    layout of the rotations): every coefficient of every encoding equal, decode
+    inverts encode, and the encodings multiply slot-wise (sigma_5 rotates them)."""
+    P = zp.plaintext_prime(N, 37)
+    ctx_p = _plain_ctx(L, N, P)
+    s = Stream(95, N)
+    ms = np.stack([_slots(s, N, P) for _ in range(3)])
+    d_slots = to_dev(ms)
+    d_poly = torch.full((3 * N,), -1, dtype=torch.int64, device="cuda")
+    L.hc_zp_encode(ctx_p, d_slots, d_poly)
+    torch.cuda.synchronize()
+    got = to_host(d_poly).reshape(3, N)
+    for i in range(3 if N == 4096 else 1):                    # the oracle's encoder is O(N^2)
+        assert np.array_equal(got[i], zp.encode(ms[i], N, P)), i
+    back = torch.full_like(d_slots, -1)
+    L.hc_zp_decode(ctx_p, d_poly, back)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(back).reshape(ms.shape), ms)
+    for i in range(3):
+        assert np.array_equal(zp.decode(got[i], N, P), ms[i])
+
+
+def test_matvec_layer_decrypts_to_the_matrix_product(L):
+    """A HELiKs-style matrix-vector layer end to end on the GPU: the server's
+    weights through hc_zp_matvec_preprocess (diagonals, SIMD encoding, lift, NTT),
+    the client's periodic input vector encrypted, hc_mac_rotate with the Galois key
+    for sigma_5; decryption gives W v mod P in the input's periodic format. The
+    plaintexts equal the oracle's diagonal encodings, and a rectangular matrix is
+    padded as the oracle pads it. N = 8192, three limbs, a 37-bit P."""
+    N, nl = 8192, 3
+    kp, P, s, sk, gk, params = _setup(N, nl, 37, 96)
+    ctx = L.hc_ctx_create(N, kp.moduli, P)
+    ctx_p = _plain_ctx(L, N, P)
+    key = L.hc_galois_key_create(ctx, kp.special, 5, gk)
+    n_out, n_in = 12, 16
+    Wm = s.below(P, n_out * n_in).astype(np.uint64).reshape(n_out, n_in)
+    v = s.below(P, n_in).astype(np.int64)
+    n = zp.matvec_size(n_out, n_in)
+    w_ntt = torch.empty(n * nl * N, dtype=torch.int64, device="cuda")
+    assert L.hc_zp_matvec_preprocess(ctx, ctx_p, Wm, w_ntt) == n
+    # the resident plaintexts are the NTT of the lifted oracle encodings of the diagonals
+    diag = zp.matvec_diagonals(Wm.astype(np.int64), N, P)
+    for i in (0, n - 1):
+        lift = zp.lift_plain(zp.encode(diag[i], N, P), P, kp.moduli)
+        chk = to_dev(lift)
+        L.hc_ntt_fwd(ctx, chk)
+        torch.cuda.synchronize()
+        assert torch.equal(chk.reshape(-1), w_ntt.view(n, -1)[i]), i
+    ct = _encrypt(s, params, sk, zp.encode(zp.periodic_slots(v, N), N, P))
+    out = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
+    L.hc_mac_rotate(ctx, key, to_dev(ct), w_ntt, out)
+    L.hc_ctx_device_status(ctx)
+    dec = bfv.decrypt_at(params, sk, to_host(out).reshape(2, nl, N), list(range(N)))
+    want = np.zeros(n, dtype=np.int64)
+    want[:n_out] = (Wm.astype(object) @ v.astype(object)) % P
+    assert np.array_equal(zp.decode(dec.astype(np.uint64), N, P), zp.periodic_slots(want, N))
+
+
+def test_zp_encoding_argument_errors(L):
+    N = 4096
+    P = zp.plaintext_prime(N, 37)
+    ctx_p = _plain_ctx(L, N, P)
+    ctx2 = L.hc_ctx_create(N, CANONICAL_PRIMES[:2], P)
+    buf = torch.zeros(N, dtype=torch.int64, device="cuda")
+    with pytest.raises(L.HcError) as e:
+        L.hc_zp_encode(ctx2, torch.zeros(2 * N, dtype=torch.int64, device="cuda"), buf)   # two moduli
+    assert e.value.status == L.HC_ERR_INVALID_ARG
+    with pytest.raises(L.HcError) as e:
+        L.hc_zp_encode(ctx_p, buf, buf)                                                    # in place
+    assert e.value.status == L.HC_ERR_INVALID_ARG
+    with pytest.raises(L.HcError) as e:                                                   # too large for N/2
+        L.hc_zp_matvec_preprocess(ctx2, ctx_p, np.zeros((N, 1), dtype=np.uint64), buf)
+    assert e.value.status == L.HC_ERR_INVALID_ARG
+    with pytest.raises(L.HcError) as e:                                                   # entry >= P
+        L.hc_zp_matvec_preprocess(ctx2, ctx_p, np.full((2, 2), P, dtype=np.uint64),
+                                  torch.zeros(2 * 2 * N, dtype=torch.int64, device="cuda"))
+    assert e.value.status == L.HC_ERR_RANGE
+    with pytest.raises(L.HcError) as e:                                                   # d_out too small
+        L.hc_zp_matvec_preprocess(ctx2, ctx_p, np.zeros((4, 4), dtype=np.uint64), buf)
+    assert e.value.status == L.HC_ERR_INVALID_ARG
