@@ -563,10 +563,17 @@ def zp_rotations(L, stream, reps=20):
     fv = lambda: L.hc_mac_rotate(ctx, key, cts[:2 * nl * N], wv, acc, stream)
     fv()
     tv = _events_ms(fv, max(3, reps // 4), stream)
+    # the same layer for all 64 ciphertexts at once (hc_mac_rotate_many: one rotation chain)
+    outs = torch.empty_like(cts)
+    fb = lambda: L.hc_mac_rotate_many(ctx, key, cts, wv, outs, stream)
+    fb()
+    tb = _events_ms(fb, max(3, reps // 4), stream)
     out.update({"encode_vectors_per_call": n_enc, "encode_ms": statistics.median(te),
                 "encodes_per_s": n_enc / (statistics.median(te) / 1e3),
                 "matvec": {"n": n_terms, "preprocess_s": pre_s, "ms": statistics.median(tv),
-                           "rotations": n_terms - 1, "products": n_terms}})
+                           "rotations": n_terms - 1, "products": n_terms,
+                           "batch": n_ct, "batch_ms": statistics.median(tb),
+                           "batch_vectors_per_s": n_ct / (statistics.median(tb) / 1e3)}})
     ctx_p.close()
     key.close()
     ctx.close()

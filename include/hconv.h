@@ -420,6 +420,15 @@ hc_status hc_ct_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64
 hc_status hc_mac_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct,
                         const uint64_t *d_w_ntt, uint32_t n, uint64_t *d_out, void *cuda_stream);
 
+/* The same iteration for m ciphertexts d_ct [m][2][L][N] that share the n
+ * plaintexts (e.g. m client vectors through one matrix-vector layer), run in
+ * lockstep: the m*n products in one launch, then n - 1 rotations of all m
+ * accumulators at once.  d_out [m][2][L][N] (must not overlap d_ct); scratch
+ * of (m*n + m) ciphertexts plus one rotation of m.  hc_mac_rotate is m = 1.
+ * Errors as hc_ct_rotate. */
+hc_status hc_mac_rotate_many(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct, uint32_t m,
+                             const uint64_t *d_w_ntt, uint32_t n, uint64_t *d_out, void *cuda_stream);
+
 /* Weight preprocessing for the iteration: n plaintext polynomials h_plain
  * [n][N] with coefficients in [0, P) (BFV-SIMD encoded by the caller), lifted
  * centered ((P-1)/2 < v -> v - P) into every q_i and forward-NTT'd into the

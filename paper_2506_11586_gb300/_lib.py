@@ -111,6 +111,7 @@ _SIGS = {
     "hc_galois_key_create": (C.c_int, [_P, C.c_uint64, C.c_uint32, _P, C.POINTER(_P), _P]),
     "hc_ct_rotate": (C.c_int, [_P, _P, _P, _P, C.c_size_t, _P]),
     "hc_mac_rotate": (C.c_int, [_P, _P, _P, _P, C.c_uint32, _P, _P]),
+    "hc_mac_rotate_many": (C.c_int, [_P, _P, _P, C.c_uint32, _P, C.c_uint32, _P, _P]),
     "hc_zp_plain_preprocess": (C.c_int, [_P, C.c_uint64, _P, C.c_size_t, _P, _P]),
     "hc_zp_encode": (C.c_int, [_P, _P, C.c_size_t, _P, _P]),
     "hc_zp_decode": (C.c_int, [_P, _P, C.c_size_t, _P, _P]),
@@ -473,6 +474,13 @@ def hc_ct_rotate(ctx, key, ct_in, ct_out, stream=None):
 def hc_mac_rotate(ctx, key, ct, w_ntt, out, stream=None):
     n = _npolys(ctx, w_ntt)
     _check(lib().hc_mac_rotate(ctx.ptr, key.ptr, _dptr(ct), _dptr(w_ntt), n, _dptr(out), _stream(stream)))
+
+
+def hc_mac_rotate_many(ctx, key, cts, w_ntt, out, stream=None):
+    """cts: device [m][2][L][N]; w_ntt: device [n][L][N] shared by all m; out: device [m][2][L][N]."""
+    m = _npolys(ctx, cts) // 2
+    n = _npolys(ctx, w_ntt)
+    _check(lib().hc_mac_rotate_many(ctx.ptr, key.ptr, _dptr(cts), m, _dptr(w_ntt), n, _dptr(out), _stream(stream)))
 
 
 def hc_zp_plain_preprocess(ctx, P, h_plain, out, stream=None):

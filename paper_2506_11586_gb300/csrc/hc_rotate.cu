@@ -132,14 +132,15 @@ __global__ void k_ks_mod_down(const uint64_t *__restrict__ ct, const uint64_t *_
     }
 }
 
-// term list of n outputs with one term each: output j = ciphertext 0 times plaintext j
-__global__ void k_single_terms(uint32_t *term_ptr, uint32_t *terms, uint32_t n)
+// term list of mn outputs with one term each: output o = ciphertext o mod m times
+// plaintext o / m
+__global__ void k_outer_terms(uint32_t *term_ptr, uint32_t *terms, uint32_t m, uint32_t mn)
 {
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += gridDim.x * blockDim.x) {
-        term_ptr[j] = j;
-        if (j < n) {
-            terms[2 * j] = 0;
-            terms[2 * j + 1] = j;
+    for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o <= mn; o += gridDim.x * blockDim.x) {
+        term_ptr[o] = o;
+        if (o < mn) {
+            terms[2 * o] = o % m;
+            terms[2 * o + 1] = o / m;
         }
     }
 }
@@ -296,45 +297,54 @@ hc_status hc_ct_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64
     return rotate_into(ctx, key, d_ct_in, d_ct_out, n_ct, s);
 }
 
-hc_status hc_mac_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct, const uint64_t *d_w_ntt,
-                        uint32_t n, uint64_t *d_out, void *cuda_stream)
+hc_status hc_mac_rotate_many(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct, uint32_t m,
+                             const uint64_t *d_w_ntt, uint32_t n, uint64_t *d_out, void *cuda_stream)
 {
     if (!ctx || ctx->magic != kMagicCtx || !key_ok(key)) return set_error(HC_ERR_INVALID_ARG, "invalid context or key");
     if (key->ctx != ctx) return set_error(HC_ERR_INVALID_ARG, "key was made for another context");
-    if (!d_ct || !d_w_ntt || !d_out || n == 0) return set_error(HC_ERR_INVALID_ARG, "null buffer or n = 0");
+    if (!d_ct || !d_w_ntt || !d_out || n == 0 || m == 0) return set_error(HC_ERR_INVALID_ARG, "null buffer or empty batch");
+    if ((uint64_t)n * m > 0x3fffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
     DeviceGuard dg(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-    hc_status st = check_inputs(ctx, d_ct, 2, s);
+    hc_status st = check_inputs(ctx, d_ct, (size_t)2 * m, s);
     if (st == HC_OK) st = check_inputs(ctx, d_w_ntt, n, s);
     if (st != HC_OK) return st;
-    // The products x * w_i do not depend on the accumulator: all n run first, in one
-    // launch (forward NTT of x once, then one MAC + inverse NTT per plaintext);
-    // the chain then only rotates and adds, the add fused into the key switch's
-    // last kernel:  P_i = x * w_i;  acc = P_{n-1};  acc = rot(acc) + P_i, i = n-2 .. 0.
+    // The products x_j * w_i do not depend on the accumulators: all m*n run first, in
+    // one launch (forward NTT of the x_j once, then one MAC + inverse NTT per product);
+    // the chain then only rotates and adds, all m accumulators per step, the add fused
+    // into the key switch's last kernel:
+    //   P_i = x * w_i (m ciphertexts);  acc = P_{n-1};  acc = rot(acc) + P_i, i = n-2 .. 0.
     const uint32_t L = ctx->L, N = ctx->N;
-    const size_t ct_words = (size_t)2 * L * N;
-    const size_t term_words = ((size_t)3 * n + 1 + 1) / 2;  // n + 1 offsets and 2n indices, as uint32
+    const size_t ct_words = (size_t)2 * L * N, mn = (size_t)m * n;
+    const size_t term_words = (3 * mn + 1 + 1) / 2;  // mn + 1 offsets and 2mn indices, as uint32
     Buf tmp(s);
-    tmp.p = dev_alloc(((size_t)(n + 1) * ct_words + term_words) * 8, s);
+    tmp.p = dev_alloc(((mn + m) * ct_words + term_words) * 8, s);
     if (!tmp.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
-    uint64_t *ctn = (uint64_t *)tmp.p, *prods = ctn + ct_words;
-    uint32_t *term_ptr = reinterpret_cast<uint32_t *>(prods + (size_t)n * ct_words), *terms = term_ptr + n + 1;
-    st = launch_ntt_fwd(ctx, d_ct, ctn, 2, s);
+    uint64_t *ctn = (uint64_t *)tmp.p, *prods = ctn + (size_t)m * ct_words;  // prods [n][m][2][L][N]
+    uint32_t *term_ptr = reinterpret_cast<uint32_t *>(prods + mn * ct_words), *terms = term_ptr + mn + 1;
+    st = launch_ntt_fwd(ctx, d_ct, ctn, (size_t)2 * m, s);
     if (st != HC_OK) return st;
-    k_single_terms<<<(n + 256) / 256, 256, 0, s>>>(term_ptr, terms, n);
+    k_outer_terms<<<(unsigned)((mn + 256) / 256), 256, 0, s>>>(term_ptr, terms, m, (uint32_t)mn);
     HC_CUDA_TRY(cudaGetLastError());
-    uint64_t *last = n == 1 ? d_out : prods;  // P_0 of a one-term iteration is the result
-    st = launch_mac_intt(ctx, ctn, d_w_ntt, MacTerms{term_ptr, terms}, last, n, s);
+    uint64_t *first = n == 1 ? d_out : prods;  // P_0 of a one-term iteration is the result
+    st = launch_mac_intt(ctx, ctn, d_w_ntt, MacTerms{term_ptr, terms}, first, mn, s);
     if (st != HC_OK || n == 1) return st;
-    const uint64_t *acc = prods + (size_t)(n - 1) * ct_words;
+    const size_t step = (size_t)m * ct_words;
+    const uint64_t *acc = prods + (size_t)(n - 1) * step;
     for (uint32_t i = n - 1; i-- > 0;) {
-        uint64_t *pi = prods + (size_t)i * ct_words;
+        uint64_t *pi = prods + (size_t)i * step;
         uint64_t *dst = i == 0 ? d_out : pi;
-        st = rotate_into(ctx, key, acc, dst, 1, s, pi);
+        st = rotate_into(ctx, key, acc, dst, m, s, pi);
         if (st != HC_OK) return st;
         acc = dst;
     }
     return HC_OK;
+}
+
+hc_status hc_mac_rotate(const hc_ctx *ctx, const hc_galois_key *key, const uint64_t *d_ct, const uint64_t *d_w_ntt,
+                        uint32_t n, uint64_t *d_out, void *cuda_stream)
+{
+    return hc_mac_rotate_many(ctx, key, d_ct, 1, d_w_ntt, n, d_out, cuda_stream);
 }
 
 hc_status hc_zp_plain_preprocess(const hc_ctx *ctx, uint64_t P, const uint64_t *h_plain, size_t n, uint64_t *d_out,

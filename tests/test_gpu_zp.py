@@ -215,3 +215,32 @@ def test_zp_encoding_argument_errors(L):
     with pytest.raises(L.HcError) as e:                                                   # d_out too small
         L.hc_zp_matvec_preprocess(ctx2, ctx_p, np.zeros((4, 4), dtype=np.uint64), buf)
     assert e.value.status == L.HC_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("n", [1, 3])
+def test_mac_rotate_many_equals_one_by_one(L, n):
+    """m ciphertexts through the same n plaintexts in lockstep (hc_mac_rotate_many)
+    give, ciphertext by ciphertext, the bits of hc_mac_rotate, and decrypt to the
+    slot formula; m = 5 spans several products per plaintext and a batched key switch."""
+    N, nl, m = 4096, 2, 5
+    kp, P, s, sk, gk, params = _setup(N, nl, 17, 97 + n)
+    ctx = L.hc_ctx_create(N, kp.moduli, P)
+    key = L.hc_galois_key_create(ctx, kp.special, 5, gk)
+    ms = [_slots(s, N, P) for _ in range(m)]
+    ws = [_slots(s, N, P) for _ in range(n)]
+    cts = np.stack([_encrypt(s, params, sk, zp.encode(x, N, P)) for x in ms])
+    polys = np.stack([zp.encode(w, N, P) for w in ws])
+    w_ntt = torch.empty(n * nl * N, dtype=torch.int64, device="cuda")
+    L.hc_zp_plain_preprocess(ctx, P, polys, w_ntt)
+    d_cts = to_dev(cts)
+    out = torch.full((m * 2 * nl * N,), -1, dtype=torch.int64, device="cuda")
+    L.hc_mac_rotate_many(ctx, key, d_cts, w_ntt, out)
+    L.hc_ctx_device_status(ctx)
+    got = to_host(out).reshape(m, 2, nl, N)
+    one = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
+    for j in range(m):
+        L.hc_mac_rotate(ctx, key, to_dev(cts[j]), w_ntt, one)
+        torch.cuda.synchronize()
+        assert np.array_equal(got[j], to_host(one).reshape(2, nl, N)), j
+        dec = bfv.decrypt_at(params, sk, got[j], list(range(N)))
+        assert np.array_equal(zp.decode(dec.astype(np.uint64), N, P), zp.slot_mac_rotate(ms[j], ws, P)), j
