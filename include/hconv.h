@@ -98,13 +98,18 @@ hc_status hc_selftest_wait_timeout(const hc_ctx *ctx, uint32_t limit, void *cuda
  * ciphertexts, 5 inverse NTT of whole ciphertexts, 6 blocked convolution MAC,
  * 7 convolution launch form.  variant (0..2) selects, for kinds 0-5, the radix
  * per register round, the polynomials per CTA and the CTAs per SM for the
- * context's N (variant 2 of the inverse kinds at N <= 8192 is a persistent,
- * TMA-fed kernel); for kind 6 the weight rows per pipeline stage (about 8, 16
- * or 32; a 32-slot chunk width is supported by the kernel but measured slower); for kind 7 either three launches per ring degree (forward NTTs,
- * MACs, inverse NTTs: variant 0) or one persistent launch whose CTAs take the
+ * context's N; variant 2 of the inverse kinds is a persistent kernel (TMA-fed
+ * at N = 4096, prefetching into its exchange buffer at N >= 8192; with fewer
+ * limbs than resident CTAs there, one cluster of two CTAs per limb) and
+ * variant 2 of the forward kinds at N >= 8192 transforms each limb with a
+ * cluster of two CTAs.  For kind 6 it selects the weight rows per pipeline stage (about
+ * 8, 16 or 32).  For kind 7: three launches per ring degree (forward NTTs,
+ * MACs, inverse NTTs: variant 0), one persistent launch whose CTAs take the
  * layers' NTT, MAC and INTT tasks in order and wait on per-limb completion
- * counters (variants 1 and 2).  Every variant
- * computes the same bits, only speed differs.  hc_ctx_create picks defaults.
+ * counters (variant 1), or three launches per limb, the limbs' chains on
+ * parallel streams (variant 2).  Every variant computes the same bits, only
+ * speed differs.  hc_ctx_create picks defaults: variant 2 for kinds 0, 1, 4
+ * and 5 at N >= 8192, variant 0 otherwise.
  * Changing a variant while other threads use the context is a data race.
  * Errors: HC_ERR_INVALID_ARG (bad handle, kind or variant). */
 hc_status hc_ctx_set_variant(hc_ctx *ctx, uint32_t kind, uint32_t variant);

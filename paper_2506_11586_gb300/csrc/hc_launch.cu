@@ -48,10 +48,13 @@ __global__ void k_range_check(const uint64_t *__restrict__ p, const LimbConst *_
 }
 
 
+// Launch shapes a context starts with (the autotuner may change them).  Measured
+// on GB300: at N >= 8192 the forward transforms run fastest as two-CTA clusters
+// and the inverse ones as the persistent prefetching kernel (variant 2 of both),
+// for a few polynomials (latency) and for a layer's hundreds (throughput) alike.
 int default_variant(int kind, uint32_t logn)
 {
-    (void)kind;
-    (void)logn;
+    if (logn >= 13 && (kind == KK_FWD || kind == KK_FWDCT || kind == KK_INV || kind == KK_INVCT)) return 2;
     return 0;
 }
 

@@ -104,14 +104,19 @@ __device__ __forceinline__ void static_for(F &&f)
 }
 
 // ---- one forward round: K Cooley-Tukey stages in registers ---------------------
-template <class Cfg, int R, int SIG>
+// HALF: the transform is one half of a transform of twice the size, after that
+// transform's first stage (see k_ntt_fwd_pair): local stage s, group i uses the
+// full table's entry tmul*2^s + i, tmul = 2 + the half's index; every round
+// reads the natural table.
+template <class Cfg, int R, int SIG, bool HALF = false>
 __device__ __forceinline__ void fwd_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const ulonglong2 *__restrict__ tw,
-                                          const ulonglong2 *__restrict__ twr, uint64_t q, int v, int g0, int tid)
+                                          const ulonglong2 *__restrict__ twr, uint64_t q, int v, int g0, int tid,
+                                          int tmul = 1)
 {
     using RS = RoundShape<Cfg, R>;
     static_assert(Cfg::LOGC >= 3 && Cfg::LOGC <= 5, "last-round tables exist for LOGC = 3, 4, 5");
     constexpr int half = RS::KK >> (SIG + 1);
-    constexpr bool last = R == Cfg::NROUNDS - 1;  // every thread has its own twiddles (g0 = tid*SUBS + v)
+    constexpr bool last = R == Cfg::NROUNDS - 1 && !HALF;  // every thread has its own twiddles (g0 = tid*SUBS + v)
     const uint64_t nq = 0ull - q, q4 = 4 * q;
 #pragma unroll
     for (int lam = 0; lam < (1 << SIG); ++lam) {
@@ -120,7 +125,7 @@ __device__ __forceinline__ void fwd_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
         const ulonglong2 w =
             last ? __ldg(twr + (size_t)(3 + Cfg::LOGC - 3) * Cfg::N + ((1 << (RS::S0 + SIG)) - (1 << RS::S0)) +
                          ((v << SIG) + lam) * Cfg::T + tid)
-                 : __ldg(tw + (1 << (RS::S0 + SIG)) + (g0 << SIG) + lam);
+                 : __ldg(tw + ((HALF ? tmul : 1) << (RS::S0 + SIG)) + (g0 << SIG) + lam);
 #pragma unroll
         for (int jj = 0; jj < half; ++jj) {
             const int j = v * RS::KK + lam * 2 * half + jj;
@@ -135,23 +140,29 @@ __device__ __forceinline__ void fwd_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
     }
 }
 
-template <class Cfg, int R>
+template <class Cfg, int R, bool HALF = false>
 __device__ __forceinline__ void fwd_round(uint64_t (&x)[Cfg::NP][Cfg::C], const ulonglong2 *__restrict__ tw,
-                                          const ulonglong2 *__restrict__ twr, uint64_t q, int tid)
+                                          const ulonglong2 *__restrict__ twr, uint64_t q, int tid, int tmul = 1)
 {
     using RS = RoundShape<Cfg, R>;
     constexpr int S = Cfg::N >> (RS::S0 + RS::K);
     static_for<0, RS::SUBS>([&](auto vc) {
         constexpr int v = decltype(vc)::value;
         const int g0 = (tid * RS::SUBS + v) / S;
-        static_for<0, RS::K>([&](auto sc) { fwd_stage<Cfg, R, decltype(sc)::value>(x, tw, twr, q, v, g0, tid); });
+        static_for<0, RS::K>([&](auto sc) {
+            fwd_stage<Cfg, R, decltype(sc)::value, HALF>(x, tw, twr, q, v, g0, tid, tmul);
+        });
     });
 }
 
 // ---- one inverse round: K Gentleman-Sande stages in registers ------------------
-template <class Cfg, int R, int SIG>
+// HALF: the transform is one half of a transform of twice the size, before that
+// transform's last stage (see k_ntt_inv_pair): stage s, group i uses the full
+// table's entry tmul*(N >> (s+1)) + i (N this transform's size, tmul = 2 + the
+// half's index); every round reads the natural table and no stage is the last.
+template <class Cfg, int R, int SIG, bool HALF = false>
 __device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const LimbConst &lc,
-                                          const ulonglong2 *__restrict__ tw, int v, int blk)
+                                          const ulonglong2 *__restrict__ tw, int v, int blk, int tmul = 1)
 {
     using RS = RoundShape<Cfg, R>;
     static_assert(Cfg::LOGC >= 3 && Cfg::LOGC <= 5, "first-round tables exist for LOGC = 3, 4, 5");
@@ -160,7 +171,7 @@ __device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
     constexpr int ngrp = RS::KK >> (SIG + 1);
     const uint64_t q = lc.q, nq = 0ull - q;
     const uint64_t qs = q << s;       // bound of the stage's inputs
-    if constexpr (s == Cfg::LOGN - 1) {
+    if constexpr (s == Cfg::LOGN - 1 && !HALF) {
         // last stage: N^-1 merged into both outputs, canonical result
 #pragma unroll
         for (int grp = 0; grp < ngrp; ++grp) {
@@ -181,8 +192,9 @@ __device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
             // first round: blk is the thread index, and the rearranged table gives the
             // warp consecutive entries; later rounds share each twiddle across threads
             const ulonglong2 w =
-                R == 0 ? __ldg(lc.tw_r + (size_t)(Cfg::LOGC - 3) * Cfg::N + (Cfg::N - (Cfg::N >> s)) + grp * Cfg::T + blk)
-                       : __ldg(tw + (Cfg::N >> (s + 1)) + blk * ngrp + grp);
+                R == 0 && !HALF
+                    ? __ldg(lc.tw_r + (size_t)(Cfg::LOGC - 3) * Cfg::N + (Cfg::N - (Cfg::N >> s)) + grp * Cfg::T + blk)
+                    : __ldg(tw + (HALF ? tmul : 1) * (Cfg::N >> (s + 1)) + blk * ngrp + grp);
 #pragma unroll
             for (int jj = 0; jj < dist; ++jj) {
                 const int j = v * RS::KK + grp * 2 * dist + jj;
@@ -198,16 +210,18 @@ __device__ __forceinline__ void inv_stage(uint64_t (&x)[Cfg::NP][Cfg::C], const 
     }
 }
 
-template <class Cfg, int R>
+template <class Cfg, int R, bool HALF = false>
 __device__ __forceinline__ void inv_round(uint64_t (&x)[Cfg::NP][Cfg::C], const LimbConst &lc,
-                                          const ulonglong2 *__restrict__ tw, int tid)
+                                          const ulonglong2 *__restrict__ tw, int tid, int tmul = 1)
 {
     using RS = RoundShape<Cfg, R>;
     constexpr int S = 1 << RS::S0;
     static_for<0, RS::SUBS>([&](auto vc) {
         constexpr int v = decltype(vc)::value;
         const int blk = (tid + v * Cfg::T) / S;
-        static_for<0, RS::K>([&](auto sc) { inv_stage<Cfg, R, decltype(sc)::value>(x, lc, tw, v, blk); });
+        static_for<0, RS::K>([&](auto sc) {
+            inv_stage<Cfg, R, decltype(sc)::value, HALF>(x, lc, tw, v, blk, tmul);
+        });
     });
 }
 
@@ -253,15 +267,15 @@ __device__ __forceinline__ void inv_exchange(uint64_t (&x)[Cfg::NP][Cfg::C], uin
 // ---- whole transforms -----------------------------------------------------------
 // forward: x holds the round-0 layout (element tid + r*T) on entry and the
 // last-round layout (element tid*C + r, contiguous) on exit.
-template <class Cfg, int R = 0>
+template <class Cfg, int R = 0, bool HALF = false>
 __device__ __forceinline__ void fwd_transform(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm,
                                               const ulonglong2 *__restrict__ tw, const ulonglong2 *__restrict__ twr,
-                                              uint64_t q, int tid)
+                                              uint64_t q, int tid, int tmul = 1)
 {
-    fwd_round<Cfg, R>(x, tw, twr, q, tid);
+    fwd_round<Cfg, R, HALF>(x, tw, twr, q, tid, tmul);
     if constexpr (R + 1 < Cfg::NROUNDS) {
         fwd_exchange<Cfg, R>(x, sm, tid);
-        fwd_transform<Cfg, R + 1>(x, sm, tw, twr, q, tid);
+        fwd_transform<Cfg, R + 1, HALF>(x, sm, tw, twr, q, tid, tmul);
     }
 }
 
@@ -274,16 +288,16 @@ struct NoHook {
 // inv_elem), canonical.  hook() runs (in every thread) right before the last
 // round, once this transform has finished with shared memory: after its last
 // exchange, or after the caller's reads when there is one round only.
-template <class Cfg, int R = 0, class Hook = NoHook>
+template <class Cfg, int R = 0, class Hook = NoHook, bool HALF = false>
 __device__ __forceinline__ void inv_transform(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm,
                                               const LimbConst &lc, const ulonglong2 *__restrict__ tw,
-                                              int tid, const Hook &hook = Hook{})
+                                              int tid, const Hook &hook = Hook{}, int tmul = 1)
 {
     if constexpr (R + 1 == Cfg::NROUNDS) hook();
-    inv_round<Cfg, R>(x, lc, tw, tid);
+    inv_round<Cfg, R, HALF>(x, lc, tw, tid, tmul);
     if constexpr (R + 1 < Cfg::NROUNDS) {
         inv_exchange<Cfg, R>(x, sm, tid);
-        inv_transform<Cfg, R + 1>(x, sm, lc, tw, tid, hook);
+        inv_transform<Cfg, R + 1, Hook, HALF>(x, sm, lc, tw, tid, hook, tmul);
     }
 }
 
