@@ -47,89 +47,97 @@ __device__ __forceinline__ uint64_t reduce_any(uint64_t v, const LimbConst &lc)
     return canon3(reduce_lazy(v, (uint32_t)lc.one_s, 0ull - lc.q), lc.q);
 }
 
+// The three kernels below run on 2-D grids: blockIdx.y walks the rows (one
+// polynomial limb of the output per row, the row's indices decoded once per
+// block), x the N coefficients (N a power of two, so no division per element).
+constexpr uint32_t kKsBlock = 256;
+
 // digits of sigma_g(c1): dig[ct][j][i][k] = sigma_g(c1)[j][k] mod m_i over the L+1
-// moduli m_i of Q*p_sp (gather: output coefficient k takes source k*ginv mod 2N)
+// moduli m_i of Q*p_sp (gather: output coefficient k takes source k*ginv mod 2N);
+// rows (ct, j)
 __global__ void k_ks_digits(const uint64_t *__restrict__ ct, uint64_t *__restrict__ dig,
                             const LimbConst *__restrict__ lq, const LimbConst *__restrict__ lqp, uint32_t L,
-                            uint32_t N, uint32_t ginv, size_t total)
+                            uint32_t N, uint32_t ginv, uint32_t rows)
 {
-    const uint32_t n2 = 2 * N;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const uint32_t k = (uint32_t)(t % N);
-        const size_t r = t / N;
-        const uint32_t j = (uint32_t)(r % L);
-        const size_t c = r / L;
+    const uint32_t k = blockIdx.x * kKsBlock + threadIdx.x;
+    const uint32_t mask2 = 2 * N - 1;
+    const uint32_t src = (uint32_t)(((uint64_t)k * ginv) & mask2);
+    for (uint32_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const uint32_t c = r / L, j = r - c * L;
         const uint64_t qj = lq[j].q;
-        const uint32_t src = (uint32_t)(((uint64_t)k * ginv) % n2);
-        const uint64_t *c1 = ct + ((c * 2 + 1) * L + j) * N;
+        const uint64_t *c1 = ct + ((size_t)(c * 2 + 1) * L + j) * N;
         const uint64_t v = src < N ? c1[src] : negmod(c1[src - N], qj);
-        uint64_t *d = dig + ((c * L + j) * (L + 1)) * N + k;
+        uint64_t *d = dig + (size_t)r * (L + 1) * N + k;
         for (uint32_t i = 0; i <= L; ++i) d[(size_t)i * N] = i == j ? v : reduce_any(v, lqp[i]);
     }
 }
 
-// u[ct][comp][i][k] = sum_j dig[ct][j][i][k] * key[j][comp][i][k] mod m_i (NTT domain)
+// u[ct][comp][i][k] = sum_j dig[ct][j][i][k] * key[j][comp][i][k] mod m_i (NTT domain);
+// rows (ct, i)
 __global__ void k_ks_mac(const uint64_t *__restrict__ dig, const uint64_t *__restrict__ key,
                          uint64_t *__restrict__ u, const LimbConst *__restrict__ lqp, uint32_t L, uint32_t N,
-                         size_t total)
+                         uint32_t rows)
 {
+    const uint32_t k = blockIdx.x * kKsBlock + threadIdx.x;
     const uint32_t L1 = L + 1;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const uint32_t k = (uint32_t)(t % N);
-        const size_t r = t / N;
-        const uint32_t i = (uint32_t)(r % L1);
-        const size_t c = r / L1;
+    for (uint32_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const uint32_t c = r / L1, i = r - c * L1;
         const LimbConst &lc = lqp[i];
         const uint64_t q = lc.q, nq = 0ull - q;
         MacAcc a0, a1;
         mac_zero(a0);
         mac_zero(a1);
         for (uint32_t j = 0; j < L; ++j) {
-            const uint64_t x = dig[((c * L + j) * L1 + i) * N + k];
+            const uint64_t x = dig[((size_t)(c * L + j) * L1 + i) * N + k];
             mac_add(a0, x, key[((size_t)(j * 2) * L1 + i) * N + k]);
             mac_add(a1, x, key[((size_t)(j * 2 + 1) * L1 + i) * N + k]);
         }
         const uint32_t ones = (uint32_t)lc.one_s;
-        u[((c * 2) * L1 + i) * N + k] = mac_reduce(a0, q, nq, lc.r64, lc.r64_s, ones);
-        u[((c * 2 + 1) * L1 + i) * N + k] = mac_reduce(a1, q, nq, lc.r64, lc.r64_s, ones);
+        u[((size_t)(c * 2) * L1 + i) * N + k] = mac_reduce(a0, q, nq, lc.r64, lc.r64_s, ones);
+        u[((size_t)(c * 2 + 1) * L1 + i) * N + k] = mac_reduce(a1, q, nq, lc.r64, lc.r64_s, ones);
     }
 }
 
 // out[ct][comp][i][k] = (comp == 0 ? sigma_g(c0)[i][k] : 0) + (u_i - [u_sp]) / p_sp
-//                       (+ add[ct][comp][i][k] when add is given) mod q_i
+//                       (+ add[ct][comp][i][k] when add is given) mod q_i;  rows (ct, comp, i)
 // (add may be out itself: each element is read before it is written, by the same thread)
 __global__ void k_ks_mod_down(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ u, uint64_t *out,
                               const uint64_t *add, const LimbConst *__restrict__ lq,
                               const ModDown *__restrict__ md, uint64_t special, uint32_t L, uint32_t N,
-                              uint32_t ginv, size_t total)
+                              uint32_t ginv, uint32_t rows)
 {
-    const uint32_t n2 = 2 * N, L1 = L + 1;
+    const uint32_t k = blockIdx.x * kKsBlock + threadIdx.x;
+    const uint32_t mask2 = 2 * N - 1, L1 = L + 1;
     const uint64_t half = (special - 1) / 2;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const uint32_t k = (uint32_t)(t % N);
-        const size_t r = t / N;
-        const uint32_t i = (uint32_t)(r % L);
-        const uint32_t comp = (uint32_t)((r / L) % 2);
-        const size_t c = r / (2 * (size_t)L);
+    const uint32_t src = (uint32_t)(((uint64_t)k * ginv) & mask2);
+    for (uint32_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const uint32_t cc = r / L, i = r - cc * L;  // cc = ct * 2 + comp
+        const uint32_t comp = cc & 1;
         const LimbConst &lc = lq[i];
         const uint64_t q = lc.q;
-        const uint64_t ui = u[((c * 2 + comp) * L1 + i) * N + k];
-        const uint64_t usp = u[((c * 2 + comp) * L1 + L) * N + k];
+        const uint64_t ui = u[((size_t)cc * L1 + i) * N + k];
+        const uint64_t usp = u[((size_t)cc * L1 + L) * N + k];
         const uint64_t rsp = reduce_any(usp, lc);  // usp mod q_i
         // the centered residue: usp - p_sp when usp > (p_sp - 1) / 2
-        const uint64_t cen = usp > half ? (rsp >= md[i].p_mod_q ? rsp - md[i].p_mod_q : rsp + q - md[i].p_mod_q) : rsp;
+        const uint64_t pm = md[i].p_mod_q;
+        const uint64_t cen = usp > half ? (rsp >= pm ? rsp - pm : rsp + q - pm) : rsp;
         const uint64_t diff = ui >= cen ? ui - cen : ui + q - cen;
         uint64_t v = canon4(shoup_lazy(diff, md[i].pinv, md[i].pinv_s, 0ull - q), q);
         if (comp == 0) {
-            const uint32_t src = (uint32_t)(((uint64_t)k * ginv) % n2);
-            const uint64_t *c0 = ct + ((c * 2) * L + i) * N;
+            const uint64_t *c0 = ct + ((size_t)cc * L + i) * N;
             const uint64_t a = src < N ? c0[src] : negmod(c0[src - N], q);
             v = csub(v + a, q);
         }
-        const size_t o = ((c * 2 + comp) * L + i) * N + k;
+        const size_t o = (size_t)r * N + k;
         if (add) v = csub(v + add[o], q);
         out[o] = v;
     }
+}
+
+// grid of one of the kernels above: N / kKsBlock blocks across, rows (at most 65535) down
+dim3 ks_grid(uint32_t N, size_t rows)
+{
+    return dim3(N / kKsBlock, (unsigned)(rows < 65535 ? (rows ? rows : 1) : 65535));
 }
 
 // term list of mn outputs with one term each: output o = ciphertext o mod m times
@@ -143,12 +151,6 @@ __global__ void k_outer_terms(uint32_t *term_ptr, uint32_t *terms, uint32_t m, u
             terms[2 * o + 1] = o / m;
         }
     }
-}
-
-unsigned grid_of(size_t total)
-{
-    const size_t b = (total + 255) / 256;
-    return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
 }
 
 struct Buf {
@@ -171,26 +173,28 @@ hc_status rotate_into(const hc_ctx *ctx, const hc_galois_key *key, const uint64_
     u.p = dev_alloc(u_words * 8, s);
     if (!dig.p || !u.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
     uint64_t *dd = (uint64_t *)dig.p, *uu = (uint64_t *)u.p;
+    if ((size_t)n * 2 * (L + 1) > 0xffffffffu) return set_error(HC_ERR_INVALID_ARG, "batch too large");
     {
         ProfileScope ps("k_ks_digits", s);
-        const size_t total = n * L * (size_t)N;
-        k_ks_digits<<<grid_of(total), 256, 0, s>>>(in, dd, ctx->d_limbs, key->qp->d_limbs, L, N, key->ginv, total);
+        const uint32_t rows = (uint32_t)(n * L);
+        k_ks_digits<<<ks_grid(N, rows), kKsBlock, 0, s>>>(in, dd, ctx->d_limbs, key->qp->d_limbs, L, N, key->ginv,
+                                                         rows);
         HC_CUDA_TRY(cudaGetLastError());
     }
     hc_status st = launch_ntt_fwd(key->qp, dd, dd, n * L, s);  // digits: n*L polys over Q*p_sp
     if (st != HC_OK) return st;
     {
         ProfileScope ps("k_ks_mac", s);
-        const size_t total = n * (L + 1) * (size_t)N;
-        k_ks_mac<<<grid_of(total), 256, 0, s>>>(dd, key->d_key, uu, key->qp->d_limbs, L, N, total);
+        const uint32_t rows = (uint32_t)(n * (L + 1));
+        k_ks_mac<<<ks_grid(N, rows), kKsBlock, 0, s>>>(dd, key->d_key, uu, key->qp->d_limbs, L, N, rows);
         HC_CUDA_TRY(cudaGetLastError());
     }
     st = launch_ntt_inv(key->qp, uu, uu, 2 * n, s);
     if (st != HC_OK) return st;
     ProfileScope ps("k_ks_mod_down", s);
-    const size_t total = n * 2 * L * (size_t)N;
-    k_ks_mod_down<<<grid_of(total), 256, 0, s>>>(in, uu, out, add, ctx->d_limbs, key->d_md, key->special, L, N,
-                                                  key->ginv, total);
+    const uint32_t rows = (uint32_t)(n * 2 * L);
+    k_ks_mod_down<<<ks_grid(N, rows), kKsBlock, 0, s>>>(in, uu, out, add, ctx->d_limbs, key->d_md, key->special, L,
+                                                        N, key->ginv, rows);
     HC_CUDA_TRY(cudaGetLastError());
     return HC_OK;
 }
