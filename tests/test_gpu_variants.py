@@ -193,3 +193,24 @@ def test_persistent_inverse_many_units(L, N, nl, n):
     ks = sample_indices(N, 8, M)
     want = conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, moduli, ks)
     assert np.array_equal(got[1][..., ks], want)
+
+
+def test_default_launch_shapes(L):
+    """A new context starts with the measured-best transforms at N >= 8192 (the
+    two-CTA cluster forward and the persistent / cluster inverse, variant 2) and
+    variant 0 for everything else; a forward-inverse round trip under the defaults
+    at every degree, with few and with many limbs, returns the input."""
+    for N, nl in SIZES:
+        ctx = L.hc_ctx_create(N, CANONICAL_PRIMES[:nl], T_PLAIN)
+        want = 2 if N >= 8192 else 0
+        for kind in (L.KIND_NTT_FWD, L.KIND_NTT_INV, L.KIND_NTT_FWD_CT, L.KIND_NTT_INV_CT):
+            assert L.hc_ctx_get_variant(ctx, kind) == want, (N, kind)
+        for kind in (L.KIND_MAC_INTT, L.KIND_PRODUCT, L.KIND_MAC_CONV, L.KIND_CONV_FORM):
+            assert L.hc_ctx_get_variant(ctx, kind) == 0, (N, kind)
+        for n in (1, 400 if N < 16384 else 160):
+            a = uniform_residues(Stream(14, n), CANONICAL_PRIMES[:nl], (n,), N)
+            d = to_dev(a)
+            L.hc_ntt_fwd(ctx, d)
+            L.hc_ntt_inv(ctx, d)
+            torch.cuda.synchronize()
+            assert np.array_equal(to_host(d).reshape(a.shape), a), (N, n)
