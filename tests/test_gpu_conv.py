@@ -146,6 +146,23 @@ def test_layer_56x56x64_parity(L, layer_56x56x64):
     assert torch.equal(d_plain, d_out)
 
 
+def test_layer_56x56x64_every_coefficient(L, layer_56x56x64):
+    """Every residue of the metric layer's output (256 ciphertexts x 2
+    components x 3 limbs x 8192 coefficients) equals the oracle's sparse
+    schoolbook convolution, under the tuned launch form of the bench (the
+    limbs' chains on parallel streams) and under one launch per phase."""
+    x, K, p, params, sk, ct = layer_56x56x64
+    ctx, w = _gpu_layer(L, p, params, K)
+    want = conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, params.moduli)
+    d_in = to_dev(ct)
+    for form in (2, 0):
+        L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, form)
+        d_out = torch.full((p.O * 2 * 3 * p.N,), -1, dtype=torch.int64, device="cuda")
+        L.hc_conv_ct_pt(ctx, w, d_in, d_out)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(d_out).reshape(p.O, 2, 3, p.N), want), form
+
+
 def test_conv_argument_errors(L):
     N, moduli = 4096, CANONICAL_PRIMES[:2]
     ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
