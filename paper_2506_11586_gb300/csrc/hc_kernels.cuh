@@ -975,7 +975,14 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
     }
     case KK_MAC: return detail::run_mac_intt<Fused>(ctx, a.in, a.pt, a.terms, a.out, a.n, s);
     case KK_PROD: return detail::run_product<Fused>(ctx, a.in, a.pt, a.out_index, a.out, a.n, a.accumulate, s);
-    case KK_INV_EXTRACT: return detail::run_inv_extract<Single>(ctx, *a.ex, s);
+    case KK_INV_EXTRACT:
+        // variant 2 of the inverse kinds is persistent at N >= 8192; the epilogue
+        // kernel (one output limb per CTA, shared memory busy until its last store)
+        // takes the best one-CTA shape there, variant 1's
+        if constexpr (V == 2 && LOGN >= 13)
+            return detail::run_inv_extract<VCfg<LOGN, 1, true>>(ctx, *a.ex, s);
+        else
+            return detail::run_inv_extract<Single>(ctx, *a.ex, s);
     default: return set_error(HC_ERR_INVALID_ARG, "unknown kernel kind %d", kind);
     }
 }
