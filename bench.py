@@ -3,10 +3,10 @@
 
 One step = one online HE convolution layer through the C ABI: forward NTT of
 every input ciphertext, NTT-domain multiply-accumulate against the resident
-NTT-preprocessed weights, inverse NTT of the outputs -- by default the layer as
-a one-item plan (hc_plan_run) replayed from the CUDA graph the plan captures,
-with --step-api direct one hc_conv_ct_pt call; the line carries the other entry
-point's time too.  Workload:
+NTT-preprocessed weights, inverse NTT of the outputs -- by default one
+hc_conv_ct_pt call, with --step-api plan the layer as a one-item plan
+(hc_plan_run) replayed from the CUDA graph the plan captures; the line carries
+the other entry point's time too.  Workload:
 56x56x64 activations -> 64 output channels, 3x3, stride 1, pad 1, packed into
 N = 8192 polynomials over three 50-bit primes (I = 32 input ciphertexts,
 P = 512 weight plaintexts, O = 256 output ciphertexts, 2048 ct x pt products).
@@ -25,7 +25,16 @@ The same line also carries, measured in the same run:
               requests drawn half from the SqueezeNet-1.1 layers and half
               from the 46 stride-1 ResNet-50 convolution instances
               (N = 16384, L = 4), weights resident, continuous batching under
-              a 32 GiB device budget: p50/p99 latency and products/s.
+              a 32 GiB device budget: p50/p99 latency and products/s;
+  networks -- every linear layer of SqueezeNet-1.1 and of ResNet-50, each
+              network one plan;
+  server_step, preprocessing_modes, e2e, plain, cpu_baseline -- the server's
+              whole step, the online / no-NTT weight modes, the host-buffer
+              entry point, the one-launch-per-product form and the oracle's
+              rate, all on the same layer;
+  zp       -- SecONNds-P's Z_P operations (rotations, the multiply-
+              accumulate-rotate iteration, SIMD encoding, a matrix-vector
+              layer) at N = 8192, L = 3.
 
 Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle (plain
 schoolbook convolution) on a bounded sample of the same workload instead.
