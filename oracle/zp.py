@@ -293,3 +293,185 @@ def matvec_diagonals(Wm, N, P):
 
 def bfv_params(N, moduli, P):
     return bfv.Params(N, tuple(moduli), P)
+
+
+# ---- convolution layers over Z_P ----------------------------------------------------------
+#
+# Reading (SecONNds-P runs its convolutions with HELiKs' kernels over Z_P^N, Sec. 6.1 and
+# Sec. 2.3; the paper cites those kernels and prints none of their packings).  A stride-1
+# convolution of C input channels of H x W (zero padding p, kernel kh x kw) into M output
+# channels, as the multiply-accumulate-rotate iteration:
+#   * input channel c is one ciphertext whose two slot rows both hold the zero-padded image,
+#     Hp = H + 2p rows of Wp = W + 2p slots, row-major from slot 0 (Hp*Wp <= N/2, zeros
+#     after it);
+#   * output ciphertext y holds output channel 2y + r in slot row r, output pixel (i, j) at
+#     slot i*Wp + j (i < Ho = Hp - kh + 1, j < Wo = Wp - kw + 1; other slots unspecified);
+#   * kernel offset i = l*kw + l' shifts by delta_i = l*Wp + l'; the weight plaintext
+#     w_{y,i,c} holds the constant K[2y + r][c][l][l'] in slot row r (0 past M);
+#   * each iteration's product is the sum over the input channels,
+#         P_i = sum_c x_c * w_{y,i,c};  acc = P_{n-1};  acc = rot^(delta_{i+1} - delta_i)(acc) + P_i,
+#     which leaves sum_i rot^(delta_i)(P_i), whose slot (r, i*Wp + j) is
+#         sum_{c,l,l'} K[2y+r][c][l][l'] * x_pad[c][i + l][j + l'] = conv(x, K)[2y + r][i][j] mod P;
+#   * a rotation by s slots is sigma_g with g = 5^s mod 2N; the steps are 1 (within a
+#     kernel row) and Wp - kw + 1 (to the next kernel row), so two Galois keys serve a
+#     layer; an output slot reads slots up to Hp*Wp - 1 < N/2, so no row wraps around.
+
+@dataclass
+class ConvShape:
+    C: int
+    H: int
+    W: int
+    M: int
+    kh: int
+    kw: int
+    pad: int
+    N: int
+
+    @property
+    def Hp(self):
+        return self.H + 2 * self.pad
+
+    @property
+    def Wp(self):
+        return self.W + 2 * self.pad
+
+    @property
+    def Ho(self):
+        return self.Hp - self.kh + 1
+
+    @property
+    def Wo(self):
+        return self.Wp - self.kw + 1
+
+    @property
+    def Y(self):
+        """Output ciphertexts: two output channels each."""
+        return (self.M + 1) // 2
+
+    @property
+    def offsets(self):
+        """delta_i = l*Wp + l' for kernel offset i = l*kw + l'."""
+        return [l * self.Wp + m for l in range(self.kh) for m in range(self.kw)]
+
+    @property
+    def steps(self):
+        """Rotation before adding P_i, i < n - 1: delta_{i+1} - delta_i."""
+        d = self.offsets
+        return [d[i + 1] - d[i] for i in range(len(d) - 1)]
+
+    def fits(self):
+        return self.Hp * self.Wp <= self.N // 2 and self.Ho >= 1 and self.Wo >= 1
+
+
+def galois_step(s, N):
+    """The Galois element of a left rotation of both slot rows by s slots."""
+    return pow(5, s, 2 * N)
+
+
+def conv_input_slots(x, shape: ConvShape, P):
+    """x [C][H][W] residues mod P -> slot vectors [C][2][N/2] (padded image in both rows)."""
+    x = np.asarray(x, dtype=np.int64) % P
+    out = np.zeros((shape.C, 2, shape.N // 2), dtype=np.int64)
+    for c in range(shape.C):
+        img = np.zeros((shape.Hp, shape.Wp), dtype=np.int64)
+        img[shape.pad:shape.pad + shape.H, shape.pad:shape.pad + shape.W] = x[c]
+        out[c, :, :shape.Hp * shape.Wp] = img.reshape(-1)
+    return out
+
+
+def conv_weight_slots(K, shape: ConvShape, P):
+    """K [M][C][kh][kw] residues mod P -> slot vectors [Y][kh*kw][C][2][N/2]: slot row r of
+    w_{y,i,c} is the constant K[2y + r][c][l][l'] (0 past M)."""
+    K = np.asarray(K, dtype=np.int64) % P
+    n = shape.kh * shape.kw
+    out = np.zeros((shape.Y, n, shape.C, 2, shape.N // 2), dtype=np.int64)
+    for y in range(shape.Y):
+        for r in range(2):
+            m = 2 * y + r
+            if m >= shape.M:
+                continue
+            for i in range(n):
+                l, lp = divmod(i, shape.kw)
+                for c in range(shape.C):
+                    out[y, i, c, r, :] = K[m, c, l, lp]
+    return out
+
+
+def conv_output(slots, shape: ConvShape):
+    """Output slot vectors [Y][2][N/2] -> y [M][Ho][Wo]."""
+    out = np.zeros((shape.M, shape.Ho, shape.Wo), dtype=np.int64)
+    for m in range(shape.M):
+        y, r = divmod(m, 2)
+        for i in range(shape.Ho):
+            out[m, i] = slots[y][r][i * shape.Wp:i * shape.Wp + shape.Wo]
+    return out
+
+
+def slot_conv(xs, ws, shape: ConvShape, P):
+    """The plain counterpart on slot vectors: sum_i rot^(delta_i)(sum_c xs[c] * ws[y][i][c]) mod P,
+    rot = left rotation of both rows; returns [Y][2][N/2]."""
+    xs = np.asarray(xs, dtype=object)
+    out = np.zeros((shape.Y, 2, shape.N // 2), dtype=object)
+    for y in range(shape.Y):
+        for i, d in enumerate(shape.offsets):
+            p = sum((xs[c] * np.asarray(ws[y][i][c], dtype=object)) % P for c in range(shape.C)) % P
+            out[y] = (out[y] + np.roll(p, -d, axis=1)) % P
+    return out.astype(np.int64)
+
+
+def conv2d_mod(x, K, pad, P):
+    """Plain stride-1 cross-correlation mod P by a direct loop (big integers)."""
+    x = np.asarray(x, dtype=object)
+    K = np.asarray(K, dtype=object)
+    C, H, W = x.shape
+    M, _, kh, kw = K.shape
+    xp = np.zeros((C, H + 2 * pad, W + 2 * pad), dtype=object)
+    xp[:, pad:pad + H, pad:pad + W] = x
+    Ho, Wo = H + 2 * pad - kh + 1, W + 2 * pad - kw + 1
+    out = np.zeros((M, Ho, Wo), dtype=object)
+    for m in range(M):
+        for i in range(Ho):
+            for j in range(Wo):
+                out[m, i, j] = int((xp[:, i:i + kh, j:j + kw] * K[m]).sum()) % P
+    return out.astype(np.int64)
+
+
+def centered(p, P):
+    """Plaintext polynomial [N] in [0, P) -> its centered integer coefficients."""
+    p = np.asarray(p, dtype=np.int64)
+    return np.where(p > (P - 1) // 2, p - P, p)
+
+
+def mul_plain_small(ct, w_cen, moduli):
+    """(c0 * w, c1 * w) over R_Q for a plaintext given by its centered integer coefficients:
+    the product of mul_plain with lift_plain(w), summed over w's nonzero terms only."""
+    sp = core.sparse_of(w_cen)
+    N = ct.shape[-1]
+    out = np.zeros_like(ct)
+    for comp in range(2):
+        for i, q in enumerate(moduli):
+            out[comp, i] = core.negacyclic_sparse(ct[comp, i], sp, N, q)
+    return out
+
+
+def conv_mac_rotate(cts, w_polys, keys, shape: ConvShape, kp: KsParams, P):
+    """The layer on ciphertexts: cts [C][2][L][N] (coefficient domain), w_polys
+    [Y][kh*kw][C][N] encoded weight plaintexts in [0, P), keys {step s: Galois key of
+    5^s}; returns [Y][2][L][N]:
+        P_i = sum_c cts[c] * w_{y,i,c};  acc = P_{n-1};  acc = rot^(step_i)(acc) + P_i."""
+    n = shape.kh * shape.kw
+    out = np.zeros((shape.Y, 2, kp.L, kp.N), dtype=np.uint64)
+    for y in range(shape.Y):
+        prods = []
+        for i in range(n):
+            acc = None
+            for c in range(shape.C):
+                t = mul_plain_small(cts[c], centered(w_polys[y][i][c], P), kp.moduli)
+                acc = t if acc is None else add(acc, t, kp.moduli)
+            prods.append(acc)
+        acc = prods[n - 1]
+        for i in range(n - 2, -1, -1):
+            s = shape.steps[i]
+            acc = add(rotate(acc, keys[s], galois_step(s, kp.N), kp), prods[i], kp.moduli)
+        out[y] = acc
+    return out
