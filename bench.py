@@ -25,7 +25,13 @@ The same line also carries, measured in the same run:
               requests drawn half from the SqueezeNet-1.1 layers and half
               from the 46 stride-1 ResNet-50 convolution instances
               (N = 16384, L = 4), weights resident, continuous batching under
-              a 32 GiB device budget: p50/p99 latency and products/s;
+              a 32 GiB device budget: p50/p99 latency and products/s; the
+              same at 800 requests/s (batches form), and at 200 requests/s
+              with every batch at one stream priority (the comparison);
+  products16 -- 16 ct x pt products at N = 4096, L = 2: independent, the
+              same accumulated into one slot, and one call per product;
+  int_probe -- the integer multiply pipe's measured rate (lazy Shoup
+              products, 32-bit and wide multiply-adds) against the peak;
   networks -- every linear layer of SqueezeNet-1.1 and of ResNet-50, each
               network one plan;
   server_step, preprocessing_modes, e2e, plain, cpu_baseline -- the server's
@@ -86,6 +92,7 @@ def parse():
     ap.add_argument("--no-batched-plain", action="store_true", help="skip the one-launch-per-product comparisons")
     ap.add_argument("--serving-requests", type=int, default=6000)
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--serving-rate-high", type=float, default=800.0)
     return ap.parse_args()
 
 
@@ -95,12 +102,29 @@ def workload_shape():
 
 
 def geometry():
+    """The layer's partition and counts through the library (the product's own geometry)."""
     from paper_2506_11586_gb300 import _lib as L
     sh, N, moduli = workload_shape()
     res, I, P, O = L.hc_conv_partition(L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), N)
     G = (sh.C + res.Cw - 1) // res.Cw
     B = I // G
     return dict(I=I, P=P, O=O, G=G, B=B, products=sh.M * G * B, Cw=res.Cw, Hw=res.Hw, Ww=res.Ww)
+
+
+def oracle_geometry():
+    """The same layer's partition from the oracle alone (the reference arm never loads the library)."""
+    from oracle import conv
+    sh, N, moduli = workload_shape()
+    p = conv.canonical_partition(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, sh.pad, N)
+    return dict(I=p.I, P=p.P, O=p.O, G=p.G, B=p.B, products=p.products, Cw=p.Cw, Hw=p.Hw, Ww=p.Ww)
+
+
+def run_config(geo, N, nl, world):
+    """The workload description both arms print (identical keys and values)."""
+    return {"workload": WORKLOAD, "N": N, "L": nl, "I": geo["I"], "P": geo["P"], "O": geo["O"],
+            "products_per_layer": geo["products"], "partition": [geo["Cw"], geo["Hw"], geo["Ww"]],
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "GPU arm: 512 MB buffer written between timed steps (flushes the 129 MB L2)"}
 
 
 def alg_bytes(geo, N, L):
@@ -116,14 +140,41 @@ def alg_bytes(geo, N, L):
 IMAD_EQ_BUTTERFLY, IMAD_EQ_MAC_TERM, IMAD_EQ_REDUCE = 14, 8, 19
 
 
-def alu_peak_imad_eq():
-    """T IMAD-equivalents/s: 64 per clock per SM at the maximum SM clock."""
-    mhz, sms = 2070.0, 152
+def device_sms():
+    """Streaming multiprocessors of the current device (152 on GB300); None without a GPU."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        pass
+    return None
+
+
+def peak_sm_mhz():
+    mhz = 2070.0
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             mhz = float(json.load(f).get("sm_max_mhz", mhz))
-    return 64 * sms * mhz * 1e6 / 1e12
+    return mhz
+
+
+def alu_peak_imad_eq(sms=None):
+    """T IMAD-equivalents/s: 64 per clock per SM x the device's SMs x the maximum SM clock."""
+    sms = sms or device_sms() or 152
+    return 64 * sms * peak_sm_mhz() * 1e6 / 1e12
+
+
+def int_probe(L, ctx, stream, iters=4096):
+    """The library's integer-pipe probe: lazy Shoup multiplications, narrow and wide
+    multiply-adds, each as operations/s and as a fraction of the derived peak."""
+    out = {"sms": device_sms(), "peak_t_imad_eq_s": alu_peak_imad_eq(), "peak_sm_mhz": peak_sm_mhz()}
+    for name, form in (("shoup_lazy", 0), ("mad_lo_u32", 1), ("mad_wide_u32", 2)):
+        rate, ms, eq = L.hc_probe_int_rate(ctx, form, iters if form == 0 else iters * 8, stream)
+        out[name] = {"ops_per_s": rate, "imad_eq_per_op": eq, "t_imad_eq_per_s": rate * eq / 1e12,
+                     "frac_of_peak": rate * eq / 1e12 / out["peak_t_imad_eq_s"], "ms": ms}
+    return out
 
 
 def kernel_work(name, geo, N, L):
@@ -263,55 +314,87 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(seconds, seed=2, max_outputs=None):
+class OracleLayer:
+    """The metric layer set up once for the oracle: packed weights, one seeded input
+    batch, and a seeded order of output ciphertexts; run(k) computes the next k
+    output ciphertexts by the oracle's sparse schoolbook products."""
+
+    def __init__(self, seed=2):
+        import numpy as np
+        from oracle import conv
+        from paper_2506_11586_gb300.inputs import Stream, conv_tensors, uniform_residues
+        sh, N, self.moduli = workload_shape()
+        _, K = conv_tensors(sh, seed=seed)
+        self.p = conv.canonical_partition(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, sh.pad, N)
+        self.ct = uniform_residues(Stream(seed, 5), self.moduli, (self.p.I, 2), N)
+        self.Kp = conv.pack_weights(K.astype(np.int64), self.p)
+        self.order = [int(o) for o in Stream(seed, 6).u64(self.p.O).argsort()]
+        self.next = 0
+        self.conv = conv
+
+    def run(self, k):
+        """k output ciphertexts (cycling through the layer); returns the products computed."""
+        for _ in range(k):
+            o = self.order[self.next % self.p.O]
+            self.next += 1
+            self.conv.conv_ct_pt(self.ct, self.Kp, self.p, self.moduli, outputs=[o])
+        return k * self.p.G
+
+
+def oracle_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_oracle_rate(seconds, layer=None):
     """Oracle convolution (plain schoolbook) of as many output ciphertexts as fit in
-    ~`seconds`; returns (products/s, outputs done, products done, elapsed, threads)."""
-    import numpy as np
-    from oracle import conv
-    from paper_2506_11586_gb300.inputs import Stream, conv_tensors, uniform_residues
-    sh, N, moduli = workload_shape()
-    _, K = conv_tensors(sh, seed=seed)
-    p = conv.canonical_partition(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, sh.pad, N)
-    ct = uniform_residues(Stream(seed, 5), moduli, (p.I, 2), N)
-    Kp = conv.pack_weights(K.astype(np.int64), p)
-    order = Stream(seed, 6).u64(p.O).argsort()
-    done, t0 = 0, time.perf_counter()
-    while done < p.O and (max_outputs is None or done < max_outputs):
-        conv.conv_ct_pt(ct, Kp, p, moduli, outputs=[int(order[done])])
+    ~`seconds`, set-up excluded; returns (products/s, outputs done, products done,
+    elapsed, threads)."""
+    layer = layer or OracleLayer()
+    layer.run(1)                                   # warm-up (first-call costs of the C core)
+    done = prods = 0
+    t0 = time.perf_counter()
+    while done < layer.p.O:
+        prods += layer.run(1)
         done += 1
-        if max_outputs is None and time.perf_counter() - t0 >= seconds:
+        if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return done * p.G / el, done, done * p.G, el, threads
+    return prods / el, done, prods, el, oracle_threads()
+
+
+# output ciphertexts per step of the reference arm: 16 of the layer's 256 (128 products)
+REFERENCE_OUTPUTS_PER_STEP = 16
 
 
 def run_reference(args):
+    """The oracle on the host cores, on a bounded sample of the same layer per step.
+    Loads only the oracle's C core: the partition comes from oracle.conv."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    geo = geometry()
     from oracle import build_oracle
     build_oracle()
-    per_step_outputs = 2
+    geo = oracle_geometry()
+    sh, N, moduli = workload_shape()
+    layer = OracleLayer()
     for _ in range(args.warmup):
-        cpu_oracle_rate(0, max_outputs=per_step_outputs)
+        layer.run(REFERENCE_OUTPUTS_PER_STEP)
     times = []
     products = 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        _, _, prods, _, threads = cpu_oracle_rate(0, max_outputs=per_step_outputs)
+        products += layer.run(REFERENCE_OUTPUTS_PER_STEP)
         times.append(time.perf_counter() - t0)
-        products += prods
     total = sum(times)
     value = products / total
-    sample = ("%d of %d output ciphertexts per step (%d products), schoolbook oracle"
-              % (per_step_outputs, geo["O"], per_step_outputs * geo["G"]))
+    sample = ("%d of %d output ciphertexts per step (%d products), sparse schoolbook oracle, set-up untimed"
+              % (REFERENCE_OUTPUTS_PER_STEP, geo["O"], REFERENCE_OUTPUTS_PER_STEP * geo["G"]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "products_per_layer": geo["products"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": run_config(geo, N, len(moduli), 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -523,6 +606,62 @@ def batched_uneven(L, stream, reps=20, with_plain=True):
     return out
 
 
+def products16(L, stream, flush, reps=50):
+    """The plain ct x pt batch (seed 1): N = 4096, two 50-bit primes, 16 products of
+    uniform residues.  The 16 independent products (one output slot each) in one
+    hc_ctpt_mac call, the same 16 accumulated into one slot in one call, and the
+    plain form (one call, i.e. one fused NTT -> product -> INTT launch, per product);
+    L2 flushed before every timed call.  The batch is 5.2 MB, so it is bound by
+    launch latency and the transforms' dependency chains, not by HBM."""
+    import numpy as np
+    import torch
+    from paper_2506_11586_gb300.inputs import CANONICAL_PRIMES, T_PLAIN, Stream, uniform_residues
+    N, nl, n = 4096, 2, 16
+    ctx = L.hc_ctx_create(N, CANONICAL_PRIMES[:nl], T_PLAIN)
+    s = Stream(1, 0)
+    # flat device tensors, so that slices select products
+    ct = torch.from_numpy(uniform_residues(s, CANONICAL_PRIMES[:nl], (n, 2), N).view(np.int64).reshape(-1)).cuda()
+    pt = torch.from_numpy(uniform_residues(s, CANONICAL_PRIMES[:nl], (n,), N).view(np.int64).reshape(-1)).cuda()
+    L.hc_ntt_fwd(ctx, pt, stream)
+    out = torch.empty_like(ct)
+    acc = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
+    plain_out = torch.empty_like(ct)
+    poly = N * nl
+    per = 2 * poly
+
+    def plain():
+        for j in range(n):
+            L.hc_ctpt_mac(ctx, ct[j * per:(j + 1) * per], pt[j * poly:(j + 1) * poly], np.zeros(1),
+                          plain_out[j * per:(j + 1) * per], stream)
+    fi = lambda: L.hc_ctpt_mac(ctx, ct, pt, np.arange(n), out, stream)
+    fa = lambda: L.hc_ctpt_mac(ctx, ct, pt, np.zeros(n), acc, stream)
+    for f in (fi, fa, plain):
+        for _ in range(3):
+            f()
+    ti, ta = _events_ms(fi, reps, stream, flush), _events_ms(fa, reps, stream, flush)
+    tp = _events_ms(plain, max(5, reps // 5), stream, flush)
+    exact = bool(torch.equal(out, plain_out))
+    bfly = (N // 2) * (N.bit_length() - 1)
+    ind_bytes = n * 8 * N * nl * 5
+    acc_bytes = n * 8 * N * nl * 3 + 8 * N * nl * 2
+    acc_imad = (n * 2 * nl * bfly * IMAD_EQ_BUTTERFLY + n * 2 * nl * N * IMAD_EQ_MAC_TERM
+                + 2 * nl * N * IMAD_EQ_REDUCE + 2 * nl * bfly * IMAD_EQ_BUTTERFLY)
+    mi, ma, mp = statistics.median(ti), statistics.median(ta), statistics.median(tp)
+    res = {"workload": "ctpt_16_products_N4096_L2", "products": n,
+           "independent": {"ms": mi, "p99_ms": sorted(ti)[int(0.99 * (len(ti) - 1))], "value": n / (mi / 1e3),
+                           "unit": UNIT, "alg_bytes": ind_bytes,
+                           "roofline": roofline_fracs(ind_bytes, n * product_imad_eq(N, nl), mi),
+                           "kernels": _kernel_trace(L, fi, "products16_independent")},
+           "accumulated": {"ms": ma, "p99_ms": sorted(ta)[int(0.99 * (len(ta) - 1))], "value": n / (ma / 1e3),
+                           "unit": UNIT, "alg_bytes": acc_bytes, "roofline": roofline_fracs(acc_bytes, acc_imad, ma),
+                           "kernels": _kernel_trace(L, fa, "products16_accumulated")},
+           "plain": {"ms": mp, "value": n / (mp / 1e3), "unit": UNIT, "launches": n,
+                     "bit_exact_vs_batched": exact},
+           "speedup_vs_plain": mp / mi}
+    ctx.close()
+    return res
+
+
 def zp_rotations(L, stream, reps=20):
     """SecONNds-P's Z_P layer operations (Sec. 6.1, Sec. 2.1): key-switched slot
     rotations of a batch of ciphertexts, one multiply-accumulate-rotate pass, SIMD
@@ -583,10 +722,68 @@ def zp_rotations(L, stream, reps=20):
                            "rotations": n_terms - 1, "products": n_terms,
                            "batch": n_ct, "batch_ms": statistics.median(tb),
                            "batch_vectors_per_s": n_ct / (statistics.median(tb) / 1e3)}})
+    out["conv"] = zp_conv_section(L, stream, ctx, ctx_p, key, s, moduli, special, reps)
     ctx_p.close()
     key.close()
     ctx.close()
     return out
+
+
+def zp_rotation_imad_eq(N, nl):
+    """IMAD-equivalents of one key-switched rotation of one ciphertext: forward NTT of the
+    L digits over L+1 moduli, the digit-key MAC, inverse NTT of 2(L+1) limbs, mod-down."""
+    bfly = (N // 2) * (N.bit_length() - 1)
+    return ((nl * (nl + 1) + 2 * (nl + 1)) * bfly * IMAD_EQ_BUTTERFLY
+            + nl * 2 * (nl + 1) * N * IMAD_EQ_MAC_TERM + 2 * (nl + 1) * N * IMAD_EQ_REDUCE
+            + 2 * nl * N * IMAD_EQ_BUTTERFLY)
+
+
+def zp_conv_section(L, stream, ctx, ctx_p, key_1, s, moduli, special, reps):
+    """SecONNds-P's convolution over Z_P (Sec. 6.1): SqueezeNet-1.1's fire2 expand 3x3
+    layer (16 -> 64 channels, 55 x 55, pad 1) as the multiply-accumulate-rotate
+    iteration at N = 8192, L = 3: 16 input ciphertexts, 32 output ciphertexts, 4608
+    ct x pt products, 256 rotations.  Uniform residues stand in for the ciphertexts and
+    the second Galois key; int8 weights mod P."""
+    import numpy as np
+    import torch
+    from paper_2506_11586_gb300.inputs import uniform_residues
+    N, nl = ctx.N, ctx.L
+    C_, H, W, M, k, pad = 16, 55, 55, 64, 3, 1
+    Wp = W + 2 * pad
+    g_row = pow(5, Wp - k + 1, 2 * N)
+    key_row = L.hc_galois_key_create(ctx, special, g_row,
+                                     uniform_residues(s, moduli + (special,), (nl, 2), N), stream)
+    desc = L.make_desc(C_, H, W, M, k, k, pad=pad)
+    P = ctx_p.moduli[0]
+    K = np.mod(s.int8(M * C_ * k * k).astype(np.int64).reshape(M, C_, k, k), P).astype(np.uint64)
+    Y, kk = (M + 1) // 2, k * k
+    n_plain = Y * kk * C_
+    w = torch.empty(n_plain * nl * N, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.hc_zp_conv_preprocess(ctx, ctx_p, desc, K, w, stream)
+    pre_s = time.perf_counter() - t0
+    cts = torch.from_numpy(uniform_residues(s, moduli, (C_, 2), N).view(np.int64)).cuda()
+    out = torch.empty(Y * 2 * nl * N, dtype=torch.int64, device="cuda")
+    f = lambda: L.hc_zp_conv(ctx, desc, key_1, key_row, w, cts, out, stream)
+    for _ in range(3):
+        f()
+    t = _events_ms(f, max(5, reps // 2), stream)
+    ms = statistics.median(t)
+    bfly = (N // 2) * (N.bit_length() - 1)
+    poly = 8 * N * nl
+    rot = Y * (kk - 1)
+    nbytes = (poly * (2 * C_ + n_plain + 2 * Y) + (kk - 1) * (poly * 2 * Y * 3 + 8 * N * nl * 2 * (nl + 1)))
+    imad = (2 * C_ * nl * bfly * IMAD_EQ_BUTTERFLY + n_plain * 2 * nl * N * IMAD_EQ_MAC_TERM
+            + kk * Y * 2 * nl * N * IMAD_EQ_REDUCE + kk * Y * 2 * nl * bfly * IMAD_EQ_BUTTERFLY
+            + rot * zp_rotation_imad_eq(N, nl))
+    res = {"workload": "zp_conv_fire2_expand3x3_16to64_55x55_N8192_L3", "products": n_plain, "rotations": rot,
+           "input_cts": C_, "output_cts": Y, "ms": ms, "p99_ms": max(t), "value": n_plain / (ms / 1e3),
+           "unit": UNIT, "rotations_per_s": rot / (ms / 1e3), "preprocess_s": pre_s,
+           "resident_weight_bytes": n_plain * poly, "alg_bytes": nbytes,
+           "roofline": roofline_fracs(nbytes, imad, ms), "kernels": _kernel_trace(L, f, "zp_conv")}
+    key_row.close()
+    return res
 
 
 def zp_plain_prime(N, bits=37):
@@ -689,12 +886,14 @@ def run_gb300(args):
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)                        # let the sampler attach before the timed region
+    torch.cuda.nvtx.range_push("timed_steps")  # profilers can select the timed launches by this range
     for k in range(args.steps):
         flush.zero_()                      # L2 flush between steps, outside the timed events
         ev[k][0].record(stream)
         step()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     replicas.barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -702,15 +901,11 @@ def run_gb300(args):
     max_total_ms = replicas.reduce_max(total_ms)
     value = replicas.whole_job_throughput(geo["products"] * args.steps, world, max_total_ms / 1000.0)
 
-    # roofline of the dominant kernel (largest share of device time in the trace).  When the
-    # tuned launch form runs each limb's chain on its own stream, the kernels of a step
-    # overlap and a launch's duration no longer isolates its own work; the per-kernel
-    # figures are then taken from a second traced pass of the same layer with the form
-    # of one launch per phase (same stream, same L2 flush), and the line says so.
-    # Per-kernel figures come from a second, traced pass of the same layer (same stream,
+    # roofline of the dominant kernel (largest share of device time in the trace).  The
+    # per-kernel figures come from a second, traced pass of the same layer (same stream,
     # same L2 flush) in the form of one launch per phase: the timed region is not traced,
     # and the tuned form runs each limb's chain on its own stream, where kernels overlap
-    # and a launch's duration no longer isolates its own work.
+    # and a launch's duration no longer isolates its own work; the line says so.
     launches = launches_per_step * args.steps
     form = L.hc_ctx_get_variant(ctx, L.KIND_CONV_FORM)
     L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, 0)
@@ -744,7 +939,10 @@ def run_gb300(args):
     else:
         roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac}
     rtotal = sum(v[1] for v in rprof.values())
-    roofline.update({"kernel": kname, "traffic": traffic, "hbm_gbs": hbm_achieved, "hbm_peak_gbs": hbm_peak,
+    roofline.update({"sms": device_sms(), "peak_sm_mhz": peak_sm_mhz(),
+                     "sm_mhz_under_load": clocks["sm_mhz"] if clocks else None,
+                     "peak_rule": "alu: 64 IMAD-eq per clock per SM x sms x peak_sm_mhz; hbm: measured copy",
+                     "kernel": kname, "traffic": traffic, "hbm_gbs": hbm_achieved, "hbm_peak_gbs": hbm_peak,
                      "hbm_frac": hbm_frac, "hbm_peak_source": peak_kind, "alu_frac": alu_frac,
                      "alg_bytes_per_launch": work["bytes"], "alg_imad_eq_per_launch": work["imad_eq"],
                      "kernel_ms": k_avg_ms, "kernel_share": kms / rtotal if rtotal else None,
@@ -866,11 +1064,14 @@ def run_gb300(args):
             modes[name.replace("_ms", "_bit_exact")] = bool(torch.equal(d_m, d_out))
             wm.close()
 
+    small = products16(L, stream, flush) if rank == 0 and not args.no_batched else None
+    probe = int_probe(L, ctx, stream) if rank == 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, outs, prods, el, threads = cpu_oracle_rate(args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "%d of %d output ciphertexts (%d products) of the same layer, %.1f s"
+               "sample": "%d of %d output ciphertexts (%d products) of the same layer, %.1f s, set-up untimed"
                          % (outs, geo["O"], prods, el)}
 
     batched = serving = None
@@ -890,6 +1091,12 @@ def run_gb300(args):
         serving = srv_mod.run(layers, n_requests=args.serving_requests, rate=args.serving_rate)
         serving.update({"workload": "poisson_squeezenet1.1_N8192L3_resnet50_N16384L4",
                         "setup_s": layers.setup_s, "resident_weight_bytes": layers.weight_bytes})
+        if args.serving_rate_high > 0:     # a rate at which requests queue and batches form
+            serving["high_rate"] = srv_mod.run(layers, n_requests=max(1000, args.serving_requests * 2 // 3),
+                                               rate=args.serving_rate_high)
+        # the same trace with every batch at the same stream priority (the comparison)
+        serving["equal_priority"] = srv_mod.run(layers, n_requests=max(1000, args.serving_requests // 2),
+                                                rate=args.serving_rate, flags=L.HC_SERVER_EQUAL_PRIORITY)
         del layers
 
     srt = sorted(step_ms)
@@ -898,14 +1105,13 @@ def run_gb300(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": max_total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "L": nl, "I": geo["I"], "P": geo["P"], "O": geo["O"],
-                   "products_per_layer": geo["products"], "partition": [geo["Cw"], geo["Hw"], geo["Ww"]],
-                   "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps",
-                   "step_api": ("hc_plan_run: one-layer plan replayed from a CUDA graph" if plan_step is not None
-                                else "hc_conv_ct_pt: direct call")},
+        "config": run_config(geo, N, nl, world),
+        "step_api": ("hc_plan_run: one-layer plan replayed from a CUDA graph" if plan_step is not None
+                     else "hc_conv_ct_pt: direct call"),
         "p50_ms": statistics.median(step_ms), "p99_ms": p99, "layer_gbs": layer_gbs,
         "roofline": roofline, "other_entry_point": alt, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
-        "server_step": step_full, "preprocessing_modes": modes, "batched": batched, "networks": networks, "zp": zp,
+        "server_step": step_full, "preprocessing_modes": modes, "products16": small, "int_probe": probe,
+        "batched": batched, "networks": networks, "zp": zp,
         "serving": serving, "gpu_launches": launches,
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in rprof.items()},
         "kernels_from": measured_with.split(";")[0],

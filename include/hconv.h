@@ -219,6 +219,21 @@ hc_status hc_fc_partition(const hc_fc_desc *desc, uint32_t N, hc_fc_desc *resolv
 hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K,
                                 hc_weights **out, void *cuda_stream);
 
+/* Output-channel shard of a convolution layer (no counterpart in the paper:
+ * the layer's output channels are independent, so a layer splits across GPUs
+ * by output channel, each GPU holding the weights of its channels and a copy
+ * of the 2*I*L input limbs).  desc and h_K describe the WHOLE layer (M output
+ * channels, h_K host int8 [M][C][kh][kw]); the handle holds channels
+ * [m0, m1) only, under the whole layer's partition (desc's Cw, Hw, Ww, or the
+ * canonical one when they are 0).  hc_conv_ct_pt with it, on the whole
+ * layer's input ciphertexts, writes (m1 - m0)*B output ciphertexts equal bit
+ * for bit to output ciphertexts [m0*B, m1*B) of the whole layer (B spatial
+ * blocks, from hc_conv_geometry).  Stride-1 and strided convolutions.
+ * Errors: as hc_weights_preprocess, and HC_ERR_INVALID_ARG unless
+ * m0 < m1 <= M. */
+hc_status hc_weights_preprocess_range(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K,
+                                      uint32_t m0, uint32_t m1, hc_weights **out, void *cuda_stream);
+
 /* NTT preprocessing modes (the paper's linear layers run "with online,
  * offline or no NTT preprocessing", Sec. 9; Sec. 6.2 describes the offline
  * one).  HC_WEIGHTS_NTT_OFFLINE (what hc_weights_preprocess does): packed,
@@ -486,6 +501,46 @@ hc_status hc_zp_matvec_preprocess(const hc_ctx *ctx, const hc_ctx *ctx_p, const 
                                   uint32_t n_in, uint64_t *d_out, size_t out_words, uint32_t *n_terms,
                                   void *cuda_stream);
 
+/* Convolution layers over Z_P (SecONNds-P runs its convolutions with HELiKs'
+ * multiply-accumulate-rotate kernels over Z_P^N, Sec. 6.1 and Sec. 2.3; the
+ * paper prints no packing, so this is the library's reading).  A stride-1
+ * convolution (desc: C, H, W, M, kh, kw, pad; stride 0 or 1; the partition
+ * fields are ignored) with Hp*Wp <= N/2, Hp = H + 2 pad, Wp = W + 2 pad:
+ *   input channel c is one ciphertext whose two slot rows both hold its
+ *   zero-padded image, row-major from slot 0 (zeros after it);
+ *   output ciphertext y < Y = ceil(M/2) holds output channel 2y + r in slot
+ *   row r, output pixel (i, j) at slot i*Wp + j (i < Hp - kh + 1, j < Wp - kw
+ *   + 1; the other slots hold no output);
+ *   kernel offset i = l*kw + l' is a rotation by delta_i = l*Wp + l' slots, and
+ *   w_{y,i,c} is the plaintext whose slot row r is the constant
+ *   K[2y + r][c][l][l'] (0 past M).  The layer runs the iteration
+ *     P_i = sum_c x_c * w_{y,i,c};  acc = P_{kk-1};
+ *     acc = rot^(delta_{i+1} - delta_i)(acc) + P_i,  i = kk-2 .. 0,
+ *   which decrypts at slot (r, i*Wp + j) to conv(x, K)[2y + r][i][j] mod P.
+ *
+ * hc_zp_conv_preprocess: h_K host [M][C][kh][kw] residues mod P = ctx_p's
+ * modulus; builds the Y*kh*kw*C weight plaintexts on the device (slot
+ * vectors, SIMD encoding, centered lift into ctx's q_i, NTT) into d_out
+ * [Y][kh*kw][C][L][N] (out_words >= that), in chunks of 1024 plaintexts of
+ * allocator scratch.  Synchronises the stream.  Errors: HC_ERR_INVALID_ARG
+ * (bad contexts, P not below every q_i, different N, image too large,
+ * d_out too small), HC_ERR_UNSUPPORTED (stride > 1), HC_ERR_RANGE (an
+ * entry >= P), HC_ERR_OOM, HC_ERR_CUDA.
+ *
+ * hc_zp_conv: d_ct_in [C][2][L][N] and d_ct_out [Y][2][L][N] coefficient
+ * domain (not overlapping); d_w_ntt from hc_zp_conv_preprocess for the same
+ * desc; key_1 a Galois key of element 5 (a one-slot rotation; unused when
+ * kw = 1, may be NULL then) and key_row one of element 5^(Wp - kw + 1) mod 2N
+ * (unused when kh = 1), both made for ctx.  Rotations: Y*(kh*kw - 1).
+ * Scratch of (C + Y*kh*kw)*2*L*N*8 bytes plus the rotations' comes from the
+ * allocator.  Errors: HC_ERR_INVALID_ARG (bad arguments or keys),
+ * HC_ERR_UNSUPPORTED, HC_ERR_RANGE (checked mode), HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_zp_conv_preprocess(const hc_ctx *ctx, const hc_ctx *ctx_p, const hc_conv_desc *desc,
+                                const uint64_t *h_K, uint64_t *d_out, size_t out_words, void *cuda_stream);
+hc_status hc_zp_conv(const hc_ctx *ctx, const hc_conv_desc *desc, const hc_galois_key *key_1,
+                     const hc_galois_key *key_row, const uint64_t *d_w_ntt, const uint64_t *d_ct_in,
+                     uint64_t *d_ct_out, void *cuda_stream);
+
 /* ------------------------------------------------------------------ plans --
  * Batching across layers, products and ring degrees (Sec. 6.2; the paper's
  * closing remarks on accelerating composite HE operations).  A plan binds a
@@ -566,25 +621,37 @@ hc_status hc_plan_info(const hc_plan *plan, uint64_t *n_products, uint64_t *alg_
  *
  * Continuous batching: a scheduler thread admits queued requests in arrival
  * order as soon as their device buffers fit in the memory budget, and each
- * time one of the max_inflight stream slots is free it launches every
- * admitted request (up to max_batch) as one batch: host->device copies of the
+ * time one of the max_inflight stream slots is free it launches the oldest
+ * admitted request together with the admitted requests of the same ring
+ * degree after it (up to max_batch) as one batch: host->device copies of the
  * inputs, then the batched launch sequence of hc_plan_run over all the
- * batch's layers (any mix of layers and ring degrees), then device->host
- * copies of the outputs that have a host buffer.  Batches on different
- * streams overlap on the device.  A completion thread retires batches,
- * returns their memory to the budget and wakes waiters.  Each request's
- * result is bit-identical to hc_conv_ct_pt on the same layer and input,
- * whatever else is in flight.
+ * batch's layers, then device->host copies of the outputs that have a host
+ * buffer.  Batches on different streams overlap on the device; a batch of a
+ * smaller ring degree (shorter requests) runs on a stream of higher CUDA
+ * priority, so its thread blocks are scheduled ahead of those of larger
+ * batches already in flight (flag HC_SERVER_EQUAL_PRIORITY turns this off).
+ * A completion thread retires batches, returns their memory to the budget
+ * and wakes waiters.  Each request's result is bit-identical to
+ * hc_conv_ct_pt on the same layer and input, whatever else is in flight.
+ * Every stream slot has its own device error word: a bounded device wait of
+ * the batch that ran out completes the batch's requests with HC_ERR_TIMEOUT
+ * (their results are then unspecified and not counted in the products).
  *
  * Device memory: one pool of budget_bytes is reserved at creation; a request
  * takes (2*I + O)*2*L*N*8 bytes (input, NTT scratch, output) from it while in
  * flight.  Requests that can never fit are refused at submission. */
 typedef struct hc_server hc_server;
 
+#define HC_SERVER_EQUAL_PRIORITY 1u  /* hc_server_config.flags: every batch at the same stream priority */
+
 typedef struct {
     size_t budget_bytes;      /* device pool for in-flight requests (0 = 32 GiB) */
     uint32_t max_batch;       /* most requests per batch (0 = 64, at most 4096) */
-    uint32_t max_inflight;    /* batches on the device at once, one stream each (0 = 2, at most 16) */
+    uint32_t max_inflight;    /* batches on the device at once, one stream slot each (0 = 4, at most 16) */
+    uint32_t flags;           /* HC_SERVER_* bits */
+    uint32_t selftest_wait_limit; /* self-test of the timeout path (0 = off): every batch also runs one
+                                     bounded wait that nothing completes, of at most this many attempts
+                                     (<= 2^20), so its requests complete with HC_ERR_TIMEOUT */
 } hc_server_config;
 
 typedef struct {
@@ -675,6 +742,21 @@ typedef struct {
 } hc_kernel_time;
 void hc_profile_enable(int on);
 hc_status hc_profile_collect(hc_kernel_time *entries, size_t cap, size_t *n_out);
+
+/* Integer-pipe throughput probe (no counterpart in the paper: the roofline of
+ * the integer-bound kernels needs the multiply pipe's rate on the device at
+ * hand).  Runs long independent chains of one arithmetic form on every SM of
+ * ctx's device (eight chains per thread, 4 CTAs of 256 threads per SM), one
+ * untimed launch then one timed with CUDA events on `cuda_stream`, and
+ * synchronises.  form 0: lazy Shoup multiplications (the NTT butterfly's
+ * product), 1: 32-bit multiply-adds, 2: 32x32->64-bit multiply-adds.
+ * *ops_per_s receives operations per second, *ms the timed launch's duration,
+ * *imad_eq_per_op the operation's cost in 32-bit multiply-adds (14, 1, 2).
+ * Any output may be NULL.  A scratch buffer of one word per thread comes from
+ * the allocator.  Errors: HC_ERR_INVALID_ARG (bad context, form > 2, iters
+ * outside [1, 2^24]), HC_ERR_OOM, HC_ERR_CUDA. */
+hc_status hc_probe_int_rate(const hc_ctx *ctx, uint32_t form, uint32_t iters, void *cuda_stream,
+                            double *ops_per_s, double *ms, double *imad_eq_per_op);
 
 /* Release a handle of any kind (context, weights, plan, server).  NULL is a no-op.
  * A handle must not be in use by queued GPU work when it is freed. */

@@ -61,7 +61,8 @@ HC_WORK_PRODUCTS = 1
 
 
 class hc_server_config(C.Structure):
-    _fields_ = [("budget_bytes", C.c_size_t), ("max_batch", C.c_uint32), ("max_inflight", C.c_uint32)]
+    _fields_ = [("budget_bytes", C.c_size_t), ("max_batch", C.c_uint32), ("max_inflight", C.c_uint32),
+                ("flags", C.c_uint32), ("selftest_wait_limit", C.c_uint32)]
 
 
 class hc_request_info(C.Structure):
@@ -86,6 +87,8 @@ _SIGS = {
     "hc_ctx_set_variant": (C.c_int, [_P, C.c_uint32, C.c_uint32]),
     "hc_selftest_wait_timeout": (C.c_int, [_P, C.c_uint32, _P]),
     "hc_ctx_get_variant": (C.c_int, [_P, C.c_uint32, C.POINTER(C.c_uint32)]),
+    "hc_probe_int_rate": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
     "hc_ctx_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), _P, _P]),
     "hc_ntt_fwd": (C.c_int, [_P, _P, C.c_size_t, _P]),
     "hc_ntt_inv": (C.c_int, [_P, _P, C.c_size_t, _P]),
@@ -93,6 +96,8 @@ _SIGS = {
                                     C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "hc_weights_preprocess": (C.c_int, [_P, C.POINTER(hc_conv_desc), _P, C.POINTER(_P), _P]),
     "hc_weights_preprocess_ex": (C.c_int, [_P, C.POINTER(hc_conv_desc), _P, C.c_uint32, C.POINTER(_P), _P]),
+    "hc_weights_preprocess_range": (C.c_int, [_P, C.POINTER(hc_conv_desc), _P, C.c_uint32, C.c_uint32,
+                                              C.POINTER(_P), _P]),
     "hc_fc_partition": (C.c_int, [C.POINTER(hc_fc_desc), C.c_uint32, C.POINTER(hc_fc_desc),
                                   C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "hc_weights_preprocess_fc": (C.c_int, [_P, C.POINTER(hc_fc_desc), _P, C.c_uint32, C.POINTER(_P), _P]),
@@ -118,6 +123,8 @@ _SIGS = {
     "hc_zp_lift_ntt": (C.c_int, [_P, C.c_uint64, _P, C.c_size_t, _P, _P]),
     "hc_zp_matvec_preprocess": (C.c_int, [_P, _P, _P, C.c_uint32, C.c_uint32, _P, C.c_size_t,
                                           C.POINTER(C.c_uint32), _P]),
+    "hc_zp_conv_preprocess": (C.c_int, [_P, _P, C.POINTER(hc_conv_desc), _P, _P, C.c_size_t, _P]),
+    "hc_zp_conv": (C.c_int, [_P, C.POINTER(hc_conv_desc), _P, _P, _P, _P, _P, _P]),
     "hc_conv_server_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "hc_conv_server_step_sparse": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "hc_plan_create": (C.c_int, [_P, C.c_size_t, C.POINTER(_P)]),
@@ -266,6 +273,13 @@ def hc_selftest_wait_timeout(ctx, limit=256, stream=None):
     _check(lib().hc_selftest_wait_timeout(ctx.ptr, limit, _stream(stream)))
 
 
+def hc_probe_int_rate(ctx, form, iters, stream=None):
+    """(operations/s, ms, IMAD-equivalents per operation) of the integer-pipe probe."""
+    r, ms, eq = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().hc_probe_int_rate(ctx.ptr, form, iters, _stream(stream), C.byref(r), C.byref(ms), C.byref(eq)))
+    return r.value, ms.value, eq.value
+
+
 def hc_ctx_set_variant(ctx, kind, variant):
     _check(lib().hc_ctx_set_variant(ctx.ptr, kind, variant))
 
@@ -335,6 +349,22 @@ def hc_weights_preprocess_ex(ctx, desc, K, mode, stream=None):
     i, o, cw, hw, ww = (C.c_uint32() for _ in range(5))
     _check(lib().hc_conv_geometry(out, C.byref(i), C.byref(o), C.byref(cw), C.byref(hw), C.byref(ww)))
     res = hc_conv_desc(desc.C, desc.H, desc.W, desc.M, desc.kh, desc.kw, desc.stride, desc.pad,
+                       cw.value, hw.value, ww.value)
+    return Weights(out, ctx, res, i.value, o.value)
+
+
+def hc_weights_preprocess_range(ctx, desc, K, m0, m1, stream=None):
+    """Weights of output channels [m0, m1) of the whole layer desc (K: its whole int8 kernel),
+    under the whole layer's partition."""
+    K = np.ascontiguousarray(K, dtype=np.int8)
+    if K.size != desc.M * desc.C * desc.kh * desc.kw:
+        raise ValueError("K must have M*C*kh*kw entries")
+    out = C.c_void_p()
+    _check(lib().hc_weights_preprocess_range(ctx.ptr, C.byref(desc), C.c_void_p(K.ctypes.data), m0, m1,
+                                             C.byref(out), _stream(stream)))
+    i, o, cw, hw, ww = (C.c_uint32() for _ in range(5))
+    _check(lib().hc_conv_geometry(out, C.byref(i), C.byref(o), C.byref(cw), C.byref(hw), C.byref(ww)))
+    res = hc_conv_desc(desc.C, desc.H, desc.W, m1 - m0, desc.kh, desc.kw, desc.stride, desc.pad,
                        cw.value, hw.value, ww.value)
     return Weights(out, ctx, res, i.value, o.value)
 
@@ -518,6 +548,23 @@ def hc_zp_matvec_preprocess(ctx, ctx_p, W, out, stream=None):
     return nt.value
 
 
+def hc_zp_conv_preprocess(ctx, ctx_p, desc, K, out, stream=None):
+    """K: host [M][C][kh][kw] residues mod P; out: device tensor of at least Y*kh*kw*C*L*N words
+    (Y = ceil(M/2)), written [Y][kh*kw][C][L][N] in the NTT domain."""
+    Km = np.ascontiguousarray(K, dtype=np.uint64)
+    assert Km.shape == (desc.M, desc.C, desc.kh, desc.kw)
+    _check(lib().hc_zp_conv_preprocess(ctx.ptr, ctx_p.ptr, C.byref(desc), C.c_void_p(Km.ctypes.data), _dptr(out),
+                                       out.numel(), _stream(stream)))
+
+
+def hc_zp_conv(ctx, desc, key_1, key_row, w_ntt, ct_in, ct_out, stream=None):
+    """The Z_P convolution: ct_in device [C][2][L][N], ct_out device [ceil(M/2)][2][L][N]; key_1 /
+    key_row the Galois keys of the one-slot and next-kernel-row rotations (None when unused)."""
+    _check(lib().hc_zp_conv(ctx.ptr, C.byref(desc), key_1.ptr if key_1 is not None else None,
+                            key_row.ptr if key_row is not None else None, _dptr(w_ntt), _dptr(ct_in), _dptr(ct_out),
+                            _stream(stream)))
+
+
 class Plan(_Handle):
     """A plan handle; keeps the contexts, weights and tensors it refers to alive."""
 
@@ -571,8 +618,11 @@ class Server(_Handle):
     """A server handle; keeps its layers' contexts and weights alive."""
 
 
-def hc_server_create(budget_bytes=0, max_batch=0, max_inflight=0):
-    cfg = hc_server_config(budget_bytes, max_batch, max_inflight)
+HC_SERVER_EQUAL_PRIORITY = 1
+
+
+def hc_server_create(budget_bytes=0, max_batch=0, max_inflight=0, flags=0, selftest_wait_limit=0):
+    cfg = hc_server_config(budget_bytes, max_batch, max_inflight, flags, selftest_wait_limit)
     h = C.c_void_p()
     _check(lib().hc_server_create(C.byref(cfg), C.byref(h)))
     return Server(h, keep=[])

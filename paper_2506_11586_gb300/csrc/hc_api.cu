@@ -614,6 +614,15 @@ hc_status hc_ctx_create_ex(uint32_t N, const uint64_t *moduli, uint32_t L, uint6
         cudaGetLastError();
         return set_error(HC_ERR_CUDA, "no CUDA device");
     }
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0) {
+            delete c;
+            cudaGetLastError();
+            return set_error(HC_ERR_CUDA, "cannot read the SM count of device %d", c->device);
+        }
+        c->sms = (uint32_t)sms;
+    }
     keep_scratch_cached(c->device);
 
     // host tables: per limb, forward and inverse twiddles with Shoup companions
@@ -833,6 +842,29 @@ hc_status hc_weights_preprocess(const hc_ctx *ctx, const hc_conv_desc *desc, con
     return hc_weights_preprocess_ex(ctx, desc, h_K, HC_WEIGHTS_NTT_OFFLINE, out, cuda_stream);
 }
 
+
+hc_status hc_weights_preprocess_range(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K,
+                                      uint32_t m0, uint32_t m1, hc_weights **out, void *cuda_stream)
+{
+    if (!out) return set_error(HC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (!desc || !h_K) return set_error(HC_ERR_INVALID_ARG, "null descriptor or kernel");
+    if (!(m0 < m1 && m1 <= desc->M))
+        return set_error(HC_ERR_INVALID_ARG, "channel range [%u, %u) not inside [0, %u)", m0, m1, desc->M);
+    // the whole layer's partition, forced on the shard: same input blocks, same packing
+    hc_conv_desc res{};
+    uint32_t I = 0, P = 0, O = 0;
+    hc_status st = hc_conv_partition(desc, ctx->N, &res, &I, &P, &O);
+    if (st != HC_OK) return st;
+    hc_conv_desc sub = *desc;
+    sub.M = m1 - m0;
+    sub.Cw = res.Cw;
+    sub.Hw = res.Hw;
+    sub.Ww = res.Ww;
+    const size_t per = (size_t)desc->C * desc->kh * desc->kw;
+    return hc_weights_preprocess_ex(ctx, &sub, h_K + (size_t)m0 * per, HC_WEIGHTS_NTT_OFFLINE, out, cuda_stream);
+}
 
 hc_status hc_weights_preprocess_ex(const hc_ctx *ctx, const hc_conv_desc *desc, const int8_t *h_K, uint32_t mode,
                                    hc_weights **out, void *cuda_stream)

@@ -230,7 +230,7 @@ hc_status fused_for_ns(const ConvJob *jobs, size_t n, uint32_t *ctr, cudaStream_
     }
     if (t > 0xffffffffu) return set_error(HC_ERR_INVALID_ARG, "fused launch too large");
     P.total = (uint32_t)t;
-    return run_fused<LOGN, V, NS>(P, smem, words, ctr, idx[0]->ctx->d_flag + 1, s);
+    return run_fused<LOGN, V, NS>(P, smem, words, ctr, timeout_flag(idx[0]->ctx), s);
 }
 
 template <int LOGN>

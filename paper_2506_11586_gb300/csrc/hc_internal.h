@@ -79,6 +79,7 @@ struct hc_ctx {
     uint64_t t;
     uint32_t flags;
     int device;
+    uint32_t sms;             // streaming multiprocessors of `device` (grid sizing)
     uint64_t q[hc::kMaxLimbs];
     uint64_t psi[hc::kMaxLimbs];
     hc::LimbConst *d_limbs;   // [L]
@@ -127,6 +128,14 @@ hc_status launch_inv_extract(const hc_ctx *ctx, const ExtractArgs &ex, cudaStrea
 // the output slot table of w (built once per weights handle)
 hc_status build_slot_table(hc_weights *w);
 
+// Geometry of a Z_P convolution (hc_zp_conv*): zero-padded image of Hp x Wp slots
+// (Hp*Wp <= N/2), Y = ceil(M/2) output ciphertexts, rotation steps 1 (within a
+// kernel row) and Wp - kw + 1 (to the next kernel row)
+struct ZpConvGeom {
+    uint32_t Hp, Wp, Ho, Wo, Y, step_row;
+};
+hc_status zp_conv_geometry(const hc_conv_desc *d, uint32_t N, ZpConvGeom *g);
+
 // frees a Galois key handle (hc_rotate.cu)
 void galois_key_destroy(hc_galois_key *k);
 
@@ -161,6 +170,34 @@ struct DeviceGuard {
     explicit DeviceGuard(int dev);
     ~DeviceGuard();
 };
+
+// ---- per-thread launch overrides ------------------------------------------------
+// Side streams (and their fork / join events) for launch form 2's per-limb chains.
+struct SidePool {
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ev;  // [0]: fork, [1 + i]: join of side stream i
+    int priority = 0;             // CUDA stream priority of the side streams made
+};
+// Word that the bounded device waits of the calling thread's launches report a
+// timeout into: the context's device flag, unless a LaunchScope on this thread
+// names another one.
+int *timeout_flag(const hc_ctx *ctx);
+// While alive, the calling thread's launches report timeouts into `flag` and run
+// per-limb chains on `side` (either may be null: the defaults).  The request
+// loop gives every stream slot its own flag and side streams, so that batches in
+// flight on different slots neither share an error word nor serialise on
+// shared side streams.
+struct LaunchScope {
+    LaunchScope(int *flag, SidePool *side);
+    ~LaunchScope();
+    LaunchScope(const LaunchScope &) = delete;
+    LaunchScope &operator=(const LaunchScope &) = delete;
+
+  private:
+    int *prev_flag_;
+    SidePool *prev_side_;
+};
+SidePool *side_override();
 
 // ---- tracing: CUDA events around one launch when hc_profile_enable(1) ----------
 bool profile_enabled();

@@ -439,22 +439,27 @@ k_ntt_inv_pf(const __grid_constant__ NttSegsT<NS> segs, uint32_t total)
         limb = segs.s[si].limb0 + local / segs.s[si].n_groups;
         poly = local % segs.s[si].n_groups;
     };
+    // warp w copies its own block [32wC, 32(w+1)C) of the unit (32 consecutive words
+    // per instruction): the round-0 layout (element tid*C + r) and the first
+    // exchange stay inside the warp's block, so a warp barrier makes the copies visible
     auto prefetch = [&](uint32_t u) {
         uint32_t si, limb, poly;
         locate(u, si, limb, poly);
         const uint64_t *src = segs.s[si].in + ((size_t)poly * segs.s[si].L + limb) * N;
+        const int base = (tid & ~31) * C + (tid & 31);
 #pragma unroll
         for (int r = 0; r < C; ++r) {
-            const int e = tid + r * T;
+            const int e = base + 32 * r;
             cp_async8(sm + spos<Cfg>(e), src + e);
         }
         cp_async_commit();
     };
+    static_assert(T % 32 == 0, "whole warps");
     uint32_t u = blockIdx.x;
     if (u < total) prefetch(u);
     for (; u < total; u += G) {
         cp_async_wait_all();
-        __syncthreads();  // every thread's copies of this unit have landed
+        xsync<true>();  // the warp's copies of its block of this unit have landed
         uint32_t si, limb, poly;
         locate(u, si, limb, poly);
         const NttSeg &sg = segs.s[si];
@@ -915,7 +920,7 @@ hc_status launch_variant(const hc_ctx *ctx, int kind, const LaunchArgs &a, cudaS
     if constexpr (use_inv_tma<LOGN, V> || use_inv_pf<LOGN, V>) {
         auto run = [&](const auto &segs) {
             if constexpr (use_inv_tma<LOGN, V>)
-                return detail::run_ntt_inv_tma<typename InvTma<LOGN>::Cfg>(segs, ctx->d_flag + 1, s);
+                return detail::run_ntt_inv_tma<typename InvTma<LOGN>::Cfg>(segs, timeout_flag(ctx), s);
             else
                 return detail::run_ntt_inv_pf<typename InvPf<LOGN>::Cfg, typename FwdPair<LOGN>::Cfg>(segs, s);
         };

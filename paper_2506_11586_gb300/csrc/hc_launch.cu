@@ -128,7 +128,7 @@ MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uin
     const size_t smem = mac_smem(G, B, sg.MS, kc);
     const uint32_t per_sm = (uint32_t)(kMacSmemCap / smem) < 4 ? (uint32_t)(kMacSmemCap / smem) : 4;
     sg.chunks = ctx->N / kc;
-    const uint32_t target = 152 * (per_sm ? per_sm : 1) * 4;
+    const uint32_t target = ctx->sms * (per_sm ? per_sm : 1) * 4;
     const uint32_t want = (target + sg.chunks * ctx->L - 1) / (sg.chunks * ctx->L);
     const uint32_t groups = want < 1 ? 1 : (want > M ? M : want);
     sg.MB = (M + groups - 1) / groups;
@@ -185,7 +185,7 @@ hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64
     MacSegs1 segs{};
     segs.n = 1;
     segs.s[0] = make_mac_seg(ctx, x_ntt, w_ntt, y, G, B, M);
-    return run_mac_segs(segs, mac_seg_smem(segs.s[0]), ctx->d_flag + 1, s);
+    return run_mac_segs(segs, mac_seg_smem(segs.s[0]), timeout_flag(ctx), s);
 }
 
 hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s)
@@ -204,7 +204,7 @@ hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *laye
             const size_t sm = mac_seg_smem(segs.s[segs.n++]);
             if (sm > smem) smem = sm;
         }
-        hc_status st = run_mac_segs(segs, smem, ctxs[i0]->d_flag + 1, s);
+        hc_status st = run_mac_segs(segs, smem, timeout_flag(ctxs[i0]), s);
         if (st != HC_OK) return st;
     }
     return HC_OK;
@@ -227,7 +227,7 @@ __global__ void k_wait_selftest(uint32_t limit, int *err)
 
 hc_status launch_wait_selftest(const hc_ctx *ctx, uint32_t limit, cudaStream_t s)
 {
-    k_wait_selftest<<<1, 32, 0, s>>>(limit, ctx->d_flag + 1);
+    k_wait_selftest<<<1, 32, 0, s>>>(limit, timeout_flag(ctx));
     return after_launch_status("k_wait_selftest");
 }
 
@@ -334,7 +334,8 @@ hc_status launch_lift_int8(const hc_ctx *ctx, const int8_t *packed, uint64_t *ou
 {
     if (n_polys == 0) return HC_OK;
     const size_t total = n_polys * ctx->L * ctx->N;
-    const unsigned blocks = (unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+    const size_t cap = (size_t)ctx->sms * 32;
+    const unsigned blocks = (unsigned)((total + 255) / 256 < cap ? (total + 255) / 256 : cap);
     ProfileScope ps("k_lift_int8", s);
     k_lift_int8<<<blocks, 256, 0, s>>>(packed, out, ctx->d_limbs, ctx->L, ctx->N, n_polys);
     return after("k_lift_int8");
@@ -344,7 +345,8 @@ hc_status launch_range_check(const hc_ctx *ctx, const uint64_t *p, size_t n_poly
 {
     if (n_polys == 0) return HC_OK;
     const size_t total = n_polys * ctx->L * ctx->N;
-    const unsigned blocks = (unsigned)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+    const size_t cap = (size_t)ctx->sms * 16;
+    const unsigned blocks = (unsigned)((total + 255) / 256 < cap ? (total + 255) / 256 : cap);
     ProfileScope ps("k_range_check", s);
     k_range_check<<<blocks, 256, 0, s>>>(p, ctx->d_limbs, ctx->L, ctx->N, n_polys, flag);
     return after("k_range_check");

@@ -225,18 +225,53 @@ __device__ __forceinline__ void inv_round(uint64_t (&x)[Cfg::NP][Cfg::C], const 
     });
 }
 
+// ---- warp-local rounds ---------------------------------------------------------------
+// A round is warp-local when every thread's elements in it lie in its own warp's
+// block of 32*C consecutive elements (warp w: [32wC, 32(w+1)C)).  An exchange
+// between two warp-local rounds moves data only within each warp's block, so a
+// warp barrier replaces the CTA barrier on both of its sides: the writes go to
+// the warp's own block, whose last readers (the previous round's layout) were
+// the warp's own threads.  Inverse round R (u = tid when it has one
+// sub-transform per thread, stride S = C^R): local iff it has one sub-transform
+// per thread and C^R <= 32 -- rounds 0 and 1 for every shape here.  Forward
+// round R (stride N >> (RC + K) over blocks of N >> RC): local iff
+// log2 N - R log2 C <= 5 + log2 C -- the last two rounds (three for some
+// shapes).  Checked for every shape on a CPU model of fwd_elem / inv_elem.
+#ifndef HC_WARP_LOCAL_XCHG
+#define HC_WARP_LOCAL_XCHG 1
+#endif
+template <class Cfg, int R>
+constexpr bool inv_round_local()
+{
+    return RoundShape<Cfg, R>::K == Cfg::LOGC && R * Cfg::LOGC <= 5;
+}
+template <class Cfg, int R>
+constexpr bool fwd_round_local()
+{
+    return Cfg::LOGN - R * Cfg::LOGC <= 5 + Cfg::LOGC;
+}
+template <bool WARP>
+__device__ __forceinline__ void xsync()
+{
+    if constexpr (WARP && HC_WARP_LOCAL_XCHG)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
 // ---- exchanges through shared memory ---------------------------------------------
 template <class Cfg, int RFROM>
 __device__ __forceinline__ void fwd_exchange(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm, int tid)
 {
-    __syncthreads();
+    constexpr bool local = fwd_round_local<Cfg, RFROM>() && fwd_round_local<Cfg, RFROM + 1>();
+    xsync<local>();
 #pragma unroll
     for (int r = 0; r < Cfg::C; ++r) {
         const int e = spos<Cfg>(fwd_elem<Cfg, RFROM>(tid, r));
 #pragma unroll
         for (int p = 0; p < Cfg::NP; ++p) sm[p * Cfg::SW + e] = x[p][r];
     }
-    __syncthreads();
+    xsync<local>();
 #pragma unroll
     for (int r = 0; r < Cfg::C; ++r) {
         const int e = spos<Cfg>(fwd_elem<Cfg, RFROM + 1>(tid, r));
@@ -248,14 +283,15 @@ __device__ __forceinline__ void fwd_exchange(uint64_t (&x)[Cfg::NP][Cfg::C], uin
 template <class Cfg, int RFROM>
 __device__ __forceinline__ void inv_exchange(uint64_t (&x)[Cfg::NP][Cfg::C], uint64_t *sm, int tid)
 {
-    __syncthreads();
+    constexpr bool local = inv_round_local<Cfg, RFROM>() && inv_round_local<Cfg, RFROM + 1>();
+    xsync<local>();
 #pragma unroll
     for (int r = 0; r < Cfg::C; ++r) {
         const int e = spos<Cfg>(inv_elem<Cfg, RFROM>(tid, r));
 #pragma unroll
         for (int p = 0; p < Cfg::NP; ++p) sm[p * Cfg::SW + e] = x[p][r];
     }
-    __syncthreads();
+    xsync<local>();
 #pragma unroll
     for (int r = 0; r < Cfg::C; ++r) {
         const int e = spos<Cfg>(inv_elem<Cfg, RFROM + 1>(tid, r));
@@ -285,7 +321,10 @@ struct NoHook {
 
 // inverse: x holds element tid*C + r (contiguous) on entry, canonical values
 // < q; on exit the last-round layout (element tid + r'*T for the slot order of
-// inv_elem), canonical.  hook() runs (in every thread) right before the last
+// inv_elem), canonical.  The first exchange synchronises the warp only: since
+// the caller's last CTA barrier, no thread may have accessed shared memory
+// outside its own warp's block of 32*C elements (every caller's last accesses
+// are its reads of the round-0 layout, element tid*C + r).  hook() runs (in every thread) right before the last
 // round, once this transform has finished with shared memory: after its last
 // exchange, or after the caller's reads when there is one round only.
 template <class Cfg, int R = 0, class Hook = NoHook, bool HALF = false>

@@ -285,18 +285,34 @@ hc_status time_batched(hc_plan *p, cudaStream_t s, int reps, float *ms)
 namespace hc {
 bool conv_job_blocked(const hc_ctx *c, const hc_weights *w) { return mac_conv_fits(w->G, w->B) && c->N % 64 == 0; }
 
-// per host thread and device: side streams and events for fork / join (made once, kept)
-struct SidePool {
-    std::vector<cudaStream_t> st;
-    std::vector<cudaEvent_t> ev;  // [0]: fork, [1 + i]: join of side stream i
-};
+namespace {
+thread_local int *t_flag = nullptr;
+thread_local SidePool *t_side = nullptr;
+}  // namespace
 
+int *timeout_flag(const hc_ctx *ctx) { return t_flag ? t_flag : ctx->d_flag + 1; }
+SidePool *side_override() { return t_side; }
+
+LaunchScope::LaunchScope(int *flag, SidePool *side) : prev_flag_(t_flag), prev_side_(t_side)
+{
+    if (flag) t_flag = flag;
+    if (side) t_side = side;
+}
+
+LaunchScope::~LaunchScope()
+{
+    t_flag = prev_flag_;
+    t_side = prev_side_;
+}
+
+// side streams and events for fork / join: the LaunchScope's pool if one is set,
+// else one per host thread and device (made once, kept); grown to `need` streams
 hc_status side_pool(uint32_t need, SidePool **out)
 {
     static thread_local SidePool pools[32];
     int dev = 0;
     HC_CUDA_TRY(cudaGetDevice(&dev));
-    SidePool &p = pools[dev & 31];
+    SidePool &p = t_side ? *t_side : pools[dev & 31];
     if (p.ev.empty()) {
         cudaEvent_t e = nullptr;
         HC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -305,7 +321,7 @@ hc_status side_pool(uint32_t need, SidePool **out)
     while (p.st.size() < need) {
         cudaStream_t st = nullptr;
         cudaEvent_t e = nullptr;
-        HC_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        HC_CUDA_TRY(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, p.priority));
         p.st.push_back(st);
         HC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         p.ev.push_back(e);

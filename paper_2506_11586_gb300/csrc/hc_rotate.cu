@@ -153,6 +153,23 @@ __global__ void k_outer_terms(uint32_t *term_ptr, uint32_t *terms, uint32_t m, u
     }
 }
 
+// term list of a Z_P convolution's products: output o = i*Y + y (kernel offset i,
+// output ciphertext y) sums the C terms (input c, weight plaintext (y*kk + i)*C + c)
+__global__ void k_conv_terms(uint32_t *term_ptr, uint32_t *terms, uint32_t Y, uint32_t kk, uint32_t C,
+                             uint32_t n_out)
+{
+    for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o <= n_out; o += gridDim.x * blockDim.x) {
+        term_ptr[o] = o * C;
+        if (o < n_out) {
+            const uint32_t i = o / Y, y = o % Y;
+            for (uint32_t c = 0; c < C; ++c) {
+                terms[2 * (o * C + c)] = c;
+                terms[2 * (o * C + c) + 1] = (y * kk + i) * C + c;
+            }
+        }
+    }
+}
+
 struct Buf {
     void *p = nullptr;
     cudaStream_t s;
@@ -377,6 +394,63 @@ hc_status hc_zp_plain_preprocess(const hc_ctx *ctx, uint64_t P, const uint64_t *
     hc_status st = launch_ntt_fwd(ctx, d_out, d_out, n, s);
     if (st != HC_OK) return st;
     HC_CUDA_TRY(cudaStreamSynchronize(s));  // the host copy must outlive the upload
+    return HC_OK;
+}
+
+hc_status hc_zp_conv(const hc_ctx *ctx, const hc_conv_desc *desc, const hc_galois_key *key_1,
+                     const hc_galois_key *key_row, const uint64_t *d_w_ntt, const uint64_t *d_ct_in,
+                     uint64_t *d_ct_out, void *cuda_stream)
+{
+    if (!ctx || ctx->magic != kMagicCtx) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    if (!desc || !d_w_ntt || !d_ct_in || !d_ct_out) return set_error(HC_ERR_INVALID_ARG, "null descriptor or buffer");
+    ZpConvGeom g;
+    hc_status st = zp_conv_geometry(desc, ctx->N, &g);
+    if (st != HC_OK) return st;
+    const uint32_t L = ctx->L, N = ctx->N, C = desc->C, kk = desc->kh * desc->kw, Y = g.Y;
+    // the two rotations of the iteration: by 1 slot within a kernel row, by Wp - kw + 1 to the next
+    const uint32_t g1 = 5, grow = (uint32_t)powmod_u64(5, g.step_row, 2ull * N);
+    if (desc->kw > 1 && (!key_ok(key_1) || key_1->ctx != ctx || key_1->g != g1))
+        return set_error(HC_ERR_INVALID_ARG, "key_1 must be a Galois key of element 5 for this context");
+    if (desc->kh > 1 && (!key_ok(key_row) || key_row->ctx != ctx || key_row->g != grow))
+        return set_error(HC_ERR_INVALID_ARG, "key_row must be a Galois key of element 5^%u mod 2N = %u", g.step_row,
+                         grow);
+    const uint64_t n_out64 = (uint64_t)kk * Y;
+    if (n_out64 * C > 0x3fffffffu) return set_error(HC_ERR_INVALID_ARG, "layer too large");
+    const uint32_t n_out = (uint32_t)n_out64;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    st = check_inputs(ctx, d_ct_in, (size_t)2 * C, s);
+    if (st != HC_OK) return st;
+    // P_{y,i} = sum_c x_c * w_{y,i,c}: forward NTT of the C inputs once, then one MAC +
+    // inverse NTT launch over the kk*Y outputs (ordered [i][y], so that the chain's step
+    // i rotates all Y accumulators at once); the chain then rotates and adds, the add
+    // fused into the key switch's last kernel:
+    //   acc = P_{kk-1};  acc = rot^(step_i)(acc) + P_i, i = kk-2 .. 0.
+    const size_t ct_words = (size_t)2 * L * N;
+    const size_t prod_words = kk > 1 ? (size_t)n_out * ct_words : 0;
+    const size_t term_words = ((size_t)n_out + 1 + 2 * (size_t)n_out * C + 1) / 2;
+    Buf tmp(s);
+    tmp.p = dev_alloc(((size_t)C * ct_words + prod_words + term_words) * 8, s);
+    if (!tmp.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+    uint64_t *ctn = (uint64_t *)tmp.p, *prods = ctn + (size_t)C * ct_words;
+    uint32_t *term_ptr = reinterpret_cast<uint32_t *>(prods + prod_words), *terms = term_ptr + n_out + 1;
+    st = launch_ntt_fwd(ctx, d_ct_in, ctn, (size_t)2 * C, s);
+    if (st != HC_OK) return st;
+    k_conv_terms<<<(n_out + 256) / 256, 256, 0, s>>>(term_ptr, terms, Y, kk, C, n_out);
+    HC_CUDA_TRY(cudaGetLastError());
+    st = launch_mac_intt(ctx, ctn, d_w_ntt, MacTerms{term_ptr, terms}, kk == 1 ? d_ct_out : prods, n_out, s);
+    if (st != HC_OK || kk == 1) return st;
+    const size_t step = (size_t)Y * ct_words;
+    const uint64_t *acc = prods + (size_t)(kk - 1) * step;
+    for (uint32_t i = kk - 1; i-- > 0;) {
+        // offsets i and i + 1 lie in one kernel row unless i + 1 starts a new one
+        const hc_galois_key *key = (i + 1) % desc->kw == 0 ? key_row : key_1;
+        uint64_t *pi = prods + (size_t)i * step;
+        uint64_t *dst = i == 0 ? d_ct_out : pi;
+        st = rotate_into(ctx, key, acc, dst, Y, s, pi);
+        if (st != HC_OK) return st;
+        acc = dst;
+    }
     return HC_OK;
 }
 

@@ -5,6 +5,7 @@
 // scheduler thread admits and launches batches; one completion thread
 // retires them.  All shared state is guarded by hc_server::mu.
 #include <algorithm>
+#include <cstring>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -99,6 +100,8 @@ struct Batch {
     hc_status status;
 };
 
+constexpr int kDegrees = 3;  // ring degrees 2^12, 2^13, 2^14: one stream class each
+
 double ms_between(Clock::time_point a, Clock::time_point b)
 {
     return std::chrono::duration<double, std::milli>(b - a).count();
@@ -118,8 +121,15 @@ struct hc_server {
     std::unordered_map<uint64_t, Request> reqs;
     std::deque<uint64_t> queued, admitted;
     std::vector<Batch *> inflight;
-    std::vector<cudaStream_t> streams;
+    // per stream slot: one stream per ring degree (smaller degrees at higher CUDA
+    // stream priority unless HC_SERVER_EQUAL_PRIORITY), their per-limb side
+    // streams, the batch's completion event, the device word its bounded waits
+    // report timeouts into and its pinned host copy, and fused-form counters
+    std::vector<cudaStream_t> streams;   // [slot * kDegrees + logN - 12]
+    std::vector<hc::SidePool> sides;     // same index
     std::vector<cudaEvent_t> events;
+    int *d_err = nullptr;                // [max_inflight]
+    int *h_err = nullptr;                // [max_inflight], pinned
     std::vector<uint32_t *> ctrs;        // per stream slot: fused-form counters
     size_t ctr_words = 1u << 18;
     std::vector<bool> slot_busy;
@@ -168,19 +178,27 @@ void free_o(hc_server *s, Request &r)
     r.has_o = false;
 }
 
-// enqueue one batch on its slot's stream (called without the lock held)
+// enqueue one batch (all of one ring degree) on its slot's stream for that
+// degree, then the batch's timeout word to the host (called without the lock held)
 hc_status enqueue_batch(hc_server *s, const std::vector<ConvJob> &jobs, const std::vector<const uint64_t *> &h_in,
                         const std::vector<uint64_t *> &h_out, const std::vector<size_t> &in_bytes,
-                        const std::vector<size_t> &out_bytes, int slot)
+                        const std::vector<size_t> &out_bytes, int slot, cudaStream_t st)
 {
-    cudaStream_t st = s->streams[slot];
+    const size_t k = (size_t)slot * kDegrees + (jobs[0].ctx->logN - 12);
+    LaunchScope scope(s->d_err + slot, &s->sides[k]);
     for (size_t i = 0; i < jobs.size(); ++i)
         HC_CUDA_TRY(cudaMemcpyAsync((void *)jobs[i].in, h_in[i], in_bytes[i], cudaMemcpyHostToDevice, st));
     hc_status rc = launch_conv_jobs(jobs.data(), jobs.size(), st, s->ctrs[slot], s->ctr_words);
     if (rc != HC_OK) return rc;
+    if (s->cfg.selftest_wait_limit) {  // one wait that nothing completes: the batch must report a timeout
+        rc = launch_wait_selftest(jobs[0].ctx, s->cfg.selftest_wait_limit, st);
+        if (rc != HC_OK) return rc;
+    }
     for (size_t i = 0; i < jobs.size(); ++i)
         if (h_out[i])
             HC_CUDA_TRY(cudaMemcpyAsync(h_out[i], jobs[i].out, out_bytes[i], cudaMemcpyDeviceToHost, st));
+    HC_CUDA_TRY(cudaMemcpyAsync(s->h_err + slot, s->d_err + slot, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HC_CUDA_TRY(cudaMemsetAsync(s->d_err + slot, 0, sizeof(int), st));
     return HC_OK;
 }
 
@@ -211,9 +229,16 @@ void scheduler_main(hc_server *s)
             std::vector<uint64_t *> h_out;
             std::vector<size_t> in_bytes, out_bytes;
             const Clock::time_point now = Clock::now();
-            while (!s->admitted.empty() && b->tickets.size() < s->cfg.max_batch) {
-                const uint64_t t = s->admitted.front();
-                s->admitted.pop_front();
+            // the batch: the oldest admitted request and the admitted requests of its
+            // ring degree after it, in arrival order (the others keep their place)
+            const uint32_t logN = s->layers[s->reqs[s->admitted.front()].layer].ctx->logN;
+            for (auto it = s->admitted.begin(); it != s->admitted.end() && b->tickets.size() < s->cfg.max_batch;) {
+                if (s->layers[s->reqs[*it].layer].ctx->logN != logN) {
+                    ++it;
+                    continue;
+                }
+                const uint64_t t = *it;
+                it = s->admitted.erase(it);
                 Request &r = s->reqs[t];
                 const Layer &ly = s->layers[r.layer];
                 r.state = RQ_LAUNCHED;
@@ -230,8 +255,9 @@ void scheduler_main(hc_server *s)
             if (b->tickets.size() > s->st.max_batch_seen) s->st.max_batch_seen = (uint32_t)b->tickets.size();
             ++s->st.batches;
             lk.unlock();
-            b->status = enqueue_batch(s, jobs, h_in, h_out, in_bytes, out_bytes, slot);
-            cudaError_t e = cudaEventRecord(s->events[slot], s->streams[slot]);
+            cudaStream_t st = s->streams[(size_t)slot * kDegrees + (logN - 12)];
+            b->status = enqueue_batch(s, jobs, h_in, h_out, in_bytes, out_bytes, slot, st);
+            cudaError_t e = cudaEventRecord(s->events[slot], st);
             if (e != cudaSuccess && b->status == HC_OK) b->status = cuda_error(e, "cudaEventRecord");
             lk.lock();
             s->inflight.push_back(b);
@@ -276,6 +302,10 @@ void completion_main(hc_server *s)
             const cudaError_t e = cudaEventQuery(s->events[b->slot]);
             if (e == cudaErrorNotReady) continue;
             if (e != cudaSuccess && b->status == HC_OK) b->status = cuda_error(e, "batch execution");
+            if (e == cudaSuccess && s->h_err[b->slot]) {  // a bounded device wait ran out: results unspecified
+                if (b->status == HC_OK) b->status = HC_ERR_TIMEOUT;
+                s->h_err[b->slot] = 0;
+            }
             ready.push_back(b);
         }
         const Clock::time_point now = Clock::now();
@@ -320,7 +350,13 @@ void server_destroy(hc_server *s)
     hc_server_shutdown(s);
     DeviceGuard g(s->device);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    for (auto &sp : s->sides) {
+        for (cudaStream_t st : sp.st) cudaStreamDestroy(st);
+        for (cudaEvent_t e : sp.ev) cudaEventDestroy(e);
+    }
     for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+    dev_free_persistent(s->d_err);
+    if (s->h_err) cudaFreeHost(s->h_err);
     for (uint32_t *c : s->ctrs) dev_free_persistent(c);
     dev_free_persistent(s->d_pool);
     s->magic = kMagicDead;
@@ -338,7 +374,8 @@ hc_status hc_server_create(const hc_server_config *cfg, hc_server **out)
     if (cfg) c = *cfg;
     if (c.budget_bytes == 0) c.budget_bytes = (size_t)32 << 30;
     if (c.max_batch == 0) c.max_batch = 64;
-    if (c.max_inflight == 0) c.max_inflight = 2;
+    if (c.max_inflight == 0) c.max_inflight = 4;
+    if (c.selftest_wait_limit > (1u << 20)) return set_error(HC_ERR_INVALID_ARG, "selftest_wait_limit <= 2^20");
     if (c.max_batch > 4096 || c.max_inflight > 16)
         return set_error(HC_ERR_INVALID_ARG, "max_batch <= 4096 and max_inflight <= 16");
     int dev = 0;
@@ -356,11 +393,34 @@ hc_status hc_server_create(const hc_server_config *cfg, hc_server **out)
     }
     s->pool.init(c.budget_bytes);
     s->st.pool_bytes = c.budget_bytes;
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
+    s->d_err = (int *)dev_alloc_persistent(c.max_inflight * sizeof(int));
+    cudaError_t e0 = s->d_err ? cudaMemset(s->d_err, 0, c.max_inflight * sizeof(int)) : cudaErrorMemoryAllocation;
+    if (e0 == cudaSuccess) e0 = cudaHostAlloc((void **)&s->h_err, c.max_inflight * sizeof(int), cudaHostAllocDefault);
+    if (e0 != cudaSuccess) {
+        s->h_err = nullptr;
+        hc::server_destroy(s);
+        return cuda_error(e0, "server error words");
+    }
+    memset(s->h_err, 0, c.max_inflight * sizeof(int));
+    s->sides.resize((size_t)c.max_inflight * kDegrees);
     for (uint32_t i = 0; i < c.max_inflight; ++i) {
-        cudaStream_t st = nullptr;
+        cudaError_t e = cudaSuccess;
+        for (int d = 0; d < kDegrees && e == cudaSuccess; ++d) {
+            // ring degree 2^(12+d): smaller rings (shorter requests) at higher priority
+            int prio = least - (kDegrees - 1 - d);
+            if (prio < greatest) prio = greatest;
+            if (c.flags & HC_SERVER_EQUAL_PRIORITY) prio = least;
+            cudaStream_t st = nullptr;
+            e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio);
+            if (e == cudaSuccess) s->streams.push_back(st);
+            s->sides[(size_t)i * kDegrees + d].priority = prio;
+        }
         cudaEvent_t ev = nullptr;
-        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) s->streams.push_back(st);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) s->events.push_back(ev);
         uint32_t *ctr = e == cudaSuccess ? (uint32_t *)dev_alloc_persistent(s->ctr_words * sizeof(uint32_t)) : nullptr;

@@ -130,10 +130,11 @@ __global__ void k_extract_mask(const uint64_t *__restrict__ ct_out, const uint64
     }
 }
 
-unsigned grid_for(size_t total)
+// grid of a grid-stride elementwise kernel: 16 CTAs of 256 threads per SM at most
+unsigned grid_for(const hc_ctx *ctx, size_t total)
 {
-    const size_t b = (total + 255) / 256;
-    return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
+    const size_t b = (total + 255) / 256, cap = (size_t)ctx->sms * 16;
+    return (unsigned)(b < cap ? (b ? b : 1) : cap);
 }
 
 struct Scratch {
@@ -176,7 +177,7 @@ extern "C" hc_status hc_conv_server_step(const hc_ctx *ctx, const hc_weights *w,
     if (st != HC_OK) return st;
     const size_t slot_words = (size_t)w->O * ctx->L * g.No * g.oh * g.ow;
     ProfileScope ps("k_extract_mask", s);
-    k_extract_mask<<<grid_for(slot_words), 256, 0, s>>>(d_ct_out, d_mask, d_c0_slots, ctx->d_limbs, ctx->L, ctx->N, g,
+    k_extract_mask<<<grid_for(ctx, slot_words), 256, 0, s>>>(d_ct_out, d_mask, d_c0_slots, ctx->d_limbs, ctx->L, ctx->N, g,
                                                         slot_words);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HC_OK : cuda_error(e, "launch k_extract_mask");

@@ -87,13 +87,53 @@ __global__ void k_zp_diagonals(const uint64_t *__restrict__ W, uint64_t *__restr
     }
 }
 
-unsigned grid_for(size_t total)
+// Weight slot vectors of a Z_P convolution, plaintexts [p0, p0 + n) of the layer's
+// [Y][kk][C] list: plaintext p = (y*kk + i)*C + c holds the constant
+// K[2y + r][c][i] in slot row r (0 past M); K is [M][C][kk] residues mod P.
+__global__ void k_zp_conv_slots(const uint64_t *__restrict__ K, uint64_t *__restrict__ slots, uint32_t M,
+                                uint32_t C, uint32_t kk, size_t p0, uint32_t N, size_t total)
 {
-    const size_t b = (total + 255) / 256;
-    return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
+    const uint32_t half = N / 2;
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = p0 + x / N;
+        const uint32_t r = (uint32_t)(x % N) / half;
+        const uint32_t c = (uint32_t)(p % C), i = (uint32_t)(p / C % kk), y = (uint32_t)(p / C / kk);
+        const uint32_t m = 2 * y + r;
+        slots[x] = m < M ? K[((size_t)m * C + c) * kk + i] : 0;
+    }
+}
+
+// grid of a grid-stride elementwise kernel: 16 CTAs of 256 threads per SM at most
+unsigned grid_for(const hc_ctx *ctx, size_t total)
+{
+    const size_t b = (total + 255) / 256, cap = (size_t)ctx->sms * 16;
+    return (unsigned)(b < cap ? (b ? b : 1) : cap);
 }
 
 bool ctx_valid(const hc_ctx *c) { return c && c->magic == kMagicCtx; }
+
+}  // namespace
+
+hc_status zp_conv_geometry(const hc_conv_desc *d, uint32_t N, ZpConvGeom *g)
+{
+    if (!d->C || !d->H || !d->W || !d->M || !d->kh || !d->kw)
+        return set_error(HC_ERR_INVALID_ARG, "empty convolution");
+    if (d->stride > 1) return set_error(HC_ERR_UNSUPPORTED, "Z_P convolutions are stride 1");
+    const uint64_t Hp = (uint64_t)d->H + 2ull * d->pad, Wp = (uint64_t)d->W + 2ull * d->pad;
+    if (d->kh > Hp || d->kw > Wp) return set_error(HC_ERR_INVALID_ARG, "kernel larger than the padded image");
+    if (Hp * Wp > N / 2)
+        return set_error(HC_ERR_INVALID_ARG, "padded image of %llu slots does not fit one slot row (%u)",
+                         (unsigned long long)(Hp * Wp), N / 2);
+    g->Hp = (uint32_t)Hp;
+    g->Wp = (uint32_t)Wp;
+    g->Ho = (uint32_t)Hp - d->kh + 1;
+    g->Wo = (uint32_t)Wp - d->kw + 1;
+    g->Y = (d->M + 1) / 2;
+    g->step_row = (uint32_t)Wp - d->kw + 1;
+    return HC_OK;
+}
+
+namespace {
 
 // ctx_p must be a one-limb context (the plaintext prime)
 hc_status check_plain_ctx(const hc_ctx *ctx_p)
@@ -114,7 +154,7 @@ hc_status encode_into(const hc_ctx *ctx_p, const uint64_t *slots, size_t n, uint
 {
     const size_t total = n * ctx_p->N;
     ProfileScope ps("k_zp_scatter", s);
-    k_zp_scatter<<<grid_for(total), 256, 0, s>>>(slots, poly, ctx_p->N, ctx_p->logN, total);
+    k_zp_scatter<<<grid_for(ctx_p, total), 256, 0, s>>>(slots, poly, ctx_p->N, ctx_p->logN, total);
     HC_CUDA_TRY(cudaGetLastError());
     return launch_ntt_inv(ctx_p, poly, poly, n, s);
 }
@@ -124,7 +164,7 @@ hc_status lift_ntt_into(const hc_ctx *ctx, uint64_t P, const uint64_t *poly, siz
     const size_t total = n * ctx->L * ctx->N;
     {
         ProfileScope ps("k_zp_lift", s);
-        k_zp_lift<<<grid_for(total), 256, 0, s>>>(poly, out, ctx->d_limbs, P, ctx->L, ctx->N, total);
+        k_zp_lift<<<grid_for(ctx, total), 256, 0, s>>>(poly, out, ctx->d_limbs, P, ctx->L, ctx->N, total);
         HC_CUDA_TRY(cudaGetLastError());
     }
     return launch_ntt_fwd(ctx, out, out, n, s);
@@ -170,7 +210,7 @@ hc_status hc_zp_decode(const hc_ctx *ctx_p, const uint64_t *d_poly, size_t n, ui
     if (st != HC_OK) return st;
     const size_t total = n * ctx_p->N;
     ProfileScope ps("k_zp_gather", s);
-    k_zp_gather<<<grid_for(total), 256, 0, s>>>(A, d_slots, ctx_p->N, ctx_p->logN, total);
+    k_zp_gather<<<grid_for(ctx_p, total), 256, 0, s>>>(A, d_slots, ctx_p->N, ctx_p->logN, total);
     HC_CUDA_TRY(cudaGetLastError());
     return HC_OK;
 }
@@ -224,13 +264,59 @@ hc_status hc_zp_matvec_preprocess(const hc_ctx *ctx, const hc_ctx *ctx_p, const 
     {
         const size_t total = (size_t)n * N;
         ProfileScope ps("k_zp_diagonals", s);
-        k_zp_diagonals<<<grid_for(total), 256, 0, s>>>(dW, slots, n_out, n_in, n, N, total);
+        k_zp_diagonals<<<grid_for(ctx_p, total), 256, 0, s>>>(dW, slots, n_out, n_in, n, N, total);
         HC_CUDA_TRY(cudaGetLastError());
     }
     st = encode_into(ctx_p, slots, n, poly, s);
     if (st == HC_OK) st = lift_ntt_into(ctx, P, poly, n, d_out, s);
     if (st != HC_OK) return st;
     HC_CUDA_TRY(cudaStreamSynchronize(s));  // the host matrix must outlive the upload
+    return HC_OK;
+}
+
+hc_status hc_zp_conv_preprocess(const hc_ctx *ctx, const hc_ctx *ctx_p, const hc_conv_desc *desc,
+                                const uint64_t *h_K, uint64_t *d_out, size_t out_words, void *cuda_stream)
+{
+    if (!ctx_valid(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
+    hc_status st = check_plain_ctx(ctx_p);
+    if (st != HC_OK) return st;
+    if (ctx_p->N != ctx->N) return set_error(HC_ERR_INVALID_ARG, "contexts of different ring degree");
+    if (!desc || !h_K || !d_out) return set_error(HC_ERR_INVALID_ARG, "null descriptor or buffer");
+    const uint64_t P = ctx_p->q[0];
+    for (uint32_t i = 0; i < ctx->L; ++i)
+        if (P >= ctx->q[i]) return set_error(HC_ERR_INVALID_ARG, "P must be below every q_i");
+    ZpConvGeom g;
+    st = zp_conv_geometry(desc, ctx->N, &g);
+    if (st != HC_OK) return st;
+    const uint32_t N = ctx->N, kk = desc->kh * desc->kw;
+    const size_t n = (size_t)g.Y * kk * desc->C, kw_ = (size_t)desc->M * desc->C * kk;
+    if (out_words < n * ctx->L * N)
+        return set_error(HC_ERR_INVALID_ARG, "d_out holds %zu words, %zu needed", out_words, n * ctx->L * N);
+    for (size_t i = 0; i < kw_; ++i)
+        if (h_K[i] >= P) return set_error(HC_ERR_RANGE, "kernel entry %zu is not below P", i);
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    // scratch: K, then slot vectors and their encodings for up to kChunk plaintexts at a time
+    constexpr size_t kChunk = 1024;
+    const size_t chunk = n < kChunk ? n : kChunk;
+    const size_t k_words = (kw_ + 31) & ~(size_t)31;
+    Scratch tmp(s);
+    tmp.p = dev_alloc((k_words + 2 * chunk * N) * sizeof(uint64_t), s);
+    if (!tmp.p) return set_error(HC_ERR_OOM, "scratch allocation failed");
+    uint64_t *dK = (uint64_t *)tmp.p, *slots = dK + k_words, *poly = slots + chunk * N;
+    HC_CUDA_TRY(cudaMemcpyAsync(dK, h_K, kw_ * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    for (size_t p0 = 0; p0 < n; p0 += chunk) {
+        const size_t m = n - p0 < chunk ? n - p0 : chunk, total = m * N;
+        {
+            ProfileScope ps("k_zp_conv_slots", s);
+            k_zp_conv_slots<<<grid_for(ctx_p, total), 256, 0, s>>>(dK, slots, desc->M, desc->C, kk, p0, N, total);
+            HC_CUDA_TRY(cudaGetLastError());
+        }
+        st = encode_into(ctx_p, slots, m, poly, s);
+        if (st == HC_OK) st = lift_ntt_into(ctx, P, poly, m, d_out + p0 * ctx->L * N, s);
+        if (st != HC_OK) return st;
+    }
+    HC_CUDA_TRY(cudaStreamSynchronize(s));  // the host kernel must outlive the upload
     return HC_OK;
 }
 

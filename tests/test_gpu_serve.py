@@ -57,8 +57,10 @@ def _alone(L, ly, ct):
     return out
 
 
-def test_mixed_requests_equal_alone(L, layers):
-    srv = L.hc_server_create(budget_bytes=2 << 30, max_batch=16, max_inflight=2)
+# stream slots, and whether smaller ring degrees run at higher stream priority
+@pytest.mark.parametrize("inflight,flags", [(2, 0), (4, 0), (4, 1)])
+def test_mixed_requests_equal_alone(L, layers, inflight, flags):
+    srv = L.hc_server_create(budget_bytes=2 << 30, max_batch=16, max_inflight=inflight, flags=flags)
     ids = [L.hc_server_add_layer(srv, ly["ctx"], ly["w"]) for ly in layers]
     order = Stream(5, 77).below(len(layers), 48)
     reqs = []
@@ -159,3 +161,31 @@ def test_results_held_until_release(L, layers):
     with pytest.raises(L.HcError):
         L.hc_server_release(srv, tb)         # released once only
     L.hc_free(srv)
+
+
+def test_batch_timeout_reported_per_request(L, layers):
+    """A bounded device wait that runs out inside a batch (the server's self-test
+    wait, which nothing completes) makes every request of that batch complete
+    with HC_ERR_TIMEOUT and uncounted products; the error goes to the batch's
+    own slot word, so the contexts' flags stay clean, and a server without the
+    self-test on the same layers still returns exact results."""
+    bad = L.hc_server_create(budget_bytes=1 << 30, max_batch=8, max_inflight=2, selftest_wait_limit=64)
+    ids = [L.hc_server_add_layer(bad, ly["ctx"], ly["w"]) for ly in layers[:2]]
+    tickets = [L.hc_server_submit(bad, ids[j % 2], _input(layers[j % 2], 3000 + j)) for j in range(4)]
+    for t in tickets:
+        assert L.hc_server_wait(bad, t, 60.0)["status"] == L.HC_ERR_TIMEOUT
+        L.hc_server_release(bad, t)
+    st = L.hc_server_stats_get(bad)
+    assert st["completed"] == 4 and st["products"] == 0
+    L.hc_free(bad)
+    for ly in layers[:2]:
+        L.hc_ctx_device_status(ly["ctx"])           # the contexts' own flags were never touched
+    good = L.hc_server_create(budget_bytes=1 << 30, max_batch=8, max_inflight=2)
+    lid = L.hc_server_add_layer(good, layers[0]["ctx"], layers[0]["w"])
+    ct = _input(layers[0], 3100)
+    out = np.zeros((layers[0]["w"].O, 2, layers[0]["nl"], layers[0]["N"]), dtype=np.uint64)
+    t = L.hc_server_submit(good, lid, ct, out)
+    assert L.hc_server_wait(good, t, 60.0)["status"] == L.HC_OK
+    L.hc_server_release(good, t)
+    assert np.array_equal(out, _alone(L, layers[0], ct))
+    L.hc_free(good)

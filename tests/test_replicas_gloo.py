@@ -1,12 +1,15 @@
 """World-size-2 gloo tests (CPU) of the multi-GPU path.
 
-The hot path shards without any data-path collective: replicas each run a
-whole layer, and a layer's output channels are independent (output ct
-o = m*B + b needs only the weights of channel m).  These tests check, with two
+Replicas each run whole layers (no data-path collective); a sharded layer
+splits its output channels, which are independent (output ct o = m*B + b
+needs only the weights of channel m), with one broadcast of the inputs.  These tests check, with two
 CPU ranks: (1) the timing aggregation used by bench.py (barrier, max over
-ranks, whole-job throughput); (2) that sharding a layer's output channels
-across ranks and concatenating reproduces the unsharded result (computed with
-the oracle on each rank, so no GPU is needed)."""
+ranks, whole-job throughput); (2) the sharded layer's host logic: contiguous
+channel ranges that tile the layer (replicas.channel_shard), the broadcast of
+the input ciphertexts from one rank (replicas.broadcast_inputs), and that the
+ranks' output ranges concatenate to the unsharded result (computed with the
+oracle on each rank, so no GPU is needed; the library's shards,
+hc_weights_preprocess_range, are checked on the GPU in test_gpu_shard.py)."""
 import os
 import socket
 
@@ -39,25 +42,36 @@ def _worker(rank, world, port, q):
     mx = replicas.reduce_max(1.5 + rank)
     thr = replicas.whole_job_throughput(100.0, w, mx)
 
-    # output-channel sharding of a small layer, oracle on each rank
-    C_, H, W, M, N = 5, 7, 7, 4, 4096
+    # output-channel shards of a small layer: rank 0 holds the input ciphertexts and
+    # broadcasts them (the sharded layer's one exchange), each rank computes its own
+    # contiguous channel range [m0, m1) = output ciphertexts [m0*B, m1*B) (oracle on
+    # each rank, so no GPU is needed), and the gathered ranges tile the whole output
+    C_, H, W, M, N = 5, 7, 7, 5, 4096
     moduli = CANONICAL_PRIMES[:2]
     s = Stream(3, 0)
     K = s.int8(M * C_ * 9).astype(np.int64).reshape(M, C_, 3, 3)
     p = conv.canonical_partition(C_, H, W, M, 3, 3, 1, N)
-    ct = uniform_residues(Stream(4, 0), moduli, (p.I, 2), N)
+    import torch
+    ct_t = torch.zeros((p.I, 2, len(moduli), N), dtype=torch.int64)
+    if r == 0:
+        ct_t.copy_(torch.from_numpy(uniform_residues(Stream(4, 0), moduli, (p.I, 2), N).view(np.int64)))
+    replicas.broadcast_inputs(ct_t, src=0)
+    ct = ct_t.numpy().view(np.uint64)
     Kp = conv.pack_weights(K, p)
     ks = np.arange(0, N, 97, dtype=np.uint32)
-    mine = [o for o in range(p.O) if (o // p.B) % w == r]   # channel m -> rank m % world
+    m0, m1 = replicas.channel_shard(M, w, r)
+    mine = list(range(m0 * p.B, m1 * p.B))
     part = conv.conv_ct_pt(ct, Kp, p, moduli, ks=ks, outputs=mine)
     gathered = [None] * w
-    dist.all_gather_object(gathered, (mine, part))
+    dist.all_gather_object(gathered, ((m0, m1), mine, part))
     if r == 0:
-        full = conv.conv_ct_pt(ct, Kp, p, moduli, ks=ks)
+        full = conv.conv_ct_pt(uniform_residues(Stream(4, 0), moduli, (p.I, 2), N), Kp, p, moduli, ks=ks)
         merged = np.zeros_like(full)
-        for outs, arr in gathered:
+        ranges = sorted(g[0] for g in gathered)
+        tiles = ranges[0][0] == 0 and ranges[-1][1] == M and all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+        for _, outs, arr in gathered:
             merged[outs] = arr
-        q.put(("ok", mx, thr, bool(np.array_equal(merged, full))))
+        q.put(("ok", mx, thr, bool(np.array_equal(merged, full)) and tiles))
     replicas.barrier()
     replicas.shutdown()
 
@@ -77,3 +91,14 @@ def test_two_rank_aggregation_and_sharding():
     assert mx == pytest.approx(2.5)
     assert thr == pytest.approx(100.0 * 2 / 2.5)
     assert equal
+
+
+def test_channel_shards_tile_the_layer():
+    from paper_2506_11586_gb300 import replicas
+    for M in range(1, 40):
+        for world in range(1, 9):
+            ranges = [replicas.channel_shard(M, world, r) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == M
+            assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+            sizes = [b - a for a, b in ranges]
+            assert max(sizes) - min(sizes) <= 1

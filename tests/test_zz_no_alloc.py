@@ -29,11 +29,7 @@ def L():
     return _lib
 
 
-def test_noalloc_matches_allocating_path_on_two_calls_in_a_row(L):
-    sh, N, moduli = CONV_56x56x64, 8192, CANONICAL_PRIMES[:3]
-    _, K = conv_tensors(sh, seed=2)
-    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
-    w = L.hc_weights_preprocess(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), K)
+def _two_calls_match(L, ctx, w, moduli, N):
     out_words = w.O * 2 * len(moduli) * N
     for call, seed in enumerate((101, 202)):          # two different inputs, one after the other
         ct = uniform_residues(Stream(seed, 0), moduli, (w.I, 2), N)
@@ -45,6 +41,34 @@ def test_noalloc_matches_allocating_path_on_two_calls_in_a_row(L):
         torch.cuda.synchronize()
         # integer results: the tolerance is zero, every residue must match
         assert torch.equal(got, want), "call %d differs from hc_conv_ct_pt" % call
+
+
+# launch forms of the layer (kernel family 7): three launches, one fused persistent
+# launch (its dependency counters sit in the static scratch after the NTT'd inputs),
+# and one chain of three launches per limb on parallel streams
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_noalloc_matches_allocating_path_on_two_calls_in_a_row(L, form):
+    sh, N, moduli = CONV_56x56x64, 8192, CANONICAL_PRIMES[:3]
+    _, K = conv_tensors(sh, seed=2)
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, form)
+    w = L.hc_weights_preprocess(ctx, L.make_desc(sh.C, sh.H, sh.W, sh.M, sh.kh, sh.kw, pad=sh.pad), K)
+    _two_calls_match(L, ctx, w, moduli, N)
+
+
+def test_noalloc_fused_form_without_room_for_its_counters(L):
+    # 256 -> 16 channels, 3x3 at 28x28, N = 16384, L = 4: I = 16 input ciphertexts,
+    # whose NTT'd limbs fill the 16 MiB static scratch exactly; the fused form's
+    # counters do not fit, so the layer must run unfused and still match
+    N, moduli = 16384, CANONICAL_PRIMES[:4]
+    desc = L.make_desc(256, 28, 28, 16, 3, 3, pad=1)
+    _, I, _, _ = L.hc_conv_partition(desc, N)
+    assert I * 2 * len(moduli) * N * 8 == 16 << 20
+    ctx = L.hc_ctx_create(N, moduli, T_PLAIN)
+    L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, 1)
+    K = Stream(7, 0).int8(16 * 256 * 9).reshape(16, 256, 3, 3)
+    w = L.hc_weights_preprocess(ctx, desc, K)
+    _two_calls_match(L, ctx, w, moduli, N)
 
 
 def test_noalloc_rejects_layers_beyond_its_static_scratch(L):
