@@ -93,6 +93,10 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=6000)
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--serving-rate-high", type=float, default=800.0)
+    ap.add_argument("--profile-case", default=None, choices=["ntt_inv"],
+                    help="run one small case for a profiler and exit: ntt_inv = the inverse NTT of 1536 "
+                         "polynomial limbs (N = 8192, L = 3) in its persistent and one-CTA shapes, then the "
+                         "integer-pipe probe (lazy Shoup products)")
     return ap.parse_args()
 
 
@@ -1128,8 +1132,35 @@ def run_gb300(args):
     return 0
 
 
+def profile_case(args):
+    """A small, fixed case for ncu captures (a few launches, ~150 MB on the device)."""
+    import numpy as np
+    import torch
+    from paper_2506_11586_gb300.build import build
+    build()
+    from paper_2506_11586_gb300 import _lib as L
+    from paper_2506_11586_gb300.inputs import CANONICAL_PRIMES, T_PLAIN, Stream, uniform_residues
+    N, nl = 8192, 3
+    ctx = L.hc_ctx_create(N, CANONICAL_PRIMES[:nl], T_PLAIN)
+    a = uniform_residues(Stream(9, 1), CANONICAL_PRIMES[:nl], (512,), N)
+    d = torch.from_numpy(a.view(np.int64).reshape(-1)).cuda()
+    s = torch.cuda.current_stream()
+    for v in (2, 1):                        # persistent prefetching shape, then the one-CTA shape
+        L.hc_ctx_set_variant(ctx, L.KIND_NTT_INV, v)
+        L.hc_ntt_inv(ctx, d, s)
+        L.hc_ntt_fwd(ctx, d, s)
+    torch.cuda.synchronize()
+    ok = bool(np.array_equal(d.cpu().numpy().view(np.uint64).reshape(a.shape), a))
+    rate, ms, eq = L.hc_probe_int_rate(ctx, 0, 64, s)
+    print(json.dumps({"profile_case": args.profile_case, "limbs": 512 * nl, "round_trip_exact": ok,
+                      "shoup_ops_per_s": rate}), flush=True)
+    return 0 if ok else 1
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gb300(args)

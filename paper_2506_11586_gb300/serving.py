@@ -29,9 +29,12 @@ FAMILIES = ((8192, 3), (16384, 4))
 class ServingLayers:
     """Contexts, resident weights and pinned inputs of every servable layer."""
 
-    def __init__(self, seed=5, pin=True):
+    def __init__(self, seed=5, pin=True, conv_form=None):
         import torch
         self.ctx = [L.hc_ctx_create(N, CANONICAL_PRIMES[:nl], T_PLAIN) for N, nl in FAMILIES]
+        if conv_form is not None:           # launch form of every request's layer (kernel family 7)
+            for c in self.ctx:
+                L.hc_ctx_set_variant(c, L.KIND_CONV_FORM, conv_form)
         self.layers = [[], []]          # per family: dicts(name, w, h_in, nl, N)
         shapes = [[(sh, 0) for sh in SQUEEZENET_1_1], resnet50_instances()]
         t0 = time.perf_counter()
