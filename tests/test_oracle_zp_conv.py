@@ -21,6 +21,7 @@ SHAPES = [  # (C, H, W, M, kh, kw, pad)
     (2, 4, 4, 4, 1, 1, 0),
     (2, 5, 4, 1, 2, 3, 0),
     (4, 7, 3, 5, 3, 1, 1),
+    (2, 3, 6, 3, 1, 3, 0),
 ]
 
 
