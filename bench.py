@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--conv-form", type=int, default=None, choices=[0, 1, 2],
                     help="force the layer's launch form instead of the autotuned one")
+    ap.add_argument("--mac-variant", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="force the blocked MAC's variant (3: the tensor-core MAC) instead of the autotuned one")
+    ap.add_argument("--no-mac-variants", action="store_true", help="skip the integer / tensor-core MAC section")
     ap.add_argument("--batched-reps", type=int, default=20)
     ap.add_argument("--step-api", default="direct", choices=["direct", "plan"],
                     help="timed step: a one-layer plan replayed from a CUDA graph, or one hc_conv_ct_pt call")
@@ -192,7 +195,7 @@ def kernel_work(name, geo, N, L):
         return {"bytes": 2 * poly * 2 * I, "imad_eq": 2 * I * L * bfly * IMAD_EQ_BUTTERFLY}
     if name.startswith("k_ntt_inv"):
         return {"bytes": 2 * poly * 2 * O, "imad_eq": 2 * O * L * bfly * IMAD_EQ_BUTTERFLY}
-    if name.startswith("k_mac_conv"):
+    if name.startswith("k_mac_conv") or name.startswith("k_mac_tc"):
         return {"bytes": poly * (2 * I + P + 2 * O), "imad_eq": mac}
     # fused MAC + inverse NTT
     return {"bytes": poly * (2 * I + P + 2 * O), "imad_eq": mac + 2 * O * L * bfly * IMAD_EQ_BUTTERFLY}
@@ -610,6 +613,39 @@ def batched_uneven(L, stream, reps=20, with_plain=True):
     return out
 
 
+def mac_variants_section(L, ctx, w, d_in, d_out, stream, flush, reps=50):
+    """The layer with the integer MAC (stages of 16 weight rows) and with the
+    tensor-core MAC, launch form 0: MAC kernel time per launch, layer time, and
+    every output residue of the tensor-core MAC against the integer MAC's."""
+    import torch
+    kinds = (L.KIND_MAC_CONV, L.KIND_CONV_FORM)
+    saved = [L.hc_ctx_get_variant(ctx, k) for k in kinds]
+    out, ref = {}, None
+    L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, 0)
+    for name, v, kern in (("integer", 1, "k_mac_conv"), ("tensor_core", 3, "k_mac_tc")):
+        L.hc_ctx_set_variant(ctx, L.KIND_MAC_CONV, v)
+        fn = lambda: L.hc_conv_ct_pt(ctx, w, d_in, d_out, stream)
+        fn()
+        layer = statistics.median(_events_ms(fn, reps, stream, flush))
+        L.hc_profile_collect()
+        L.hc_profile_enable(True)
+        for _ in range(reps):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        L.hc_profile_enable(False)
+        prof = L.hc_profile_collect()
+        n, ms = prof.get(kern, (0, 0.0))
+        out[name] = {"kernel": kern, "mac_us": 1000 * ms / n if n else None, "layer_form0_ms": layer}
+        if ref is None:
+            ref = d_out.clone()
+        else:
+            out[name]["bit_exact_vs_integer"] = bool(torch.equal(ref, d_out))
+    for k, v in zip(kinds, saved):
+        L.hc_ctx_set_variant(ctx, k, v)
+    return out
+
+
 def products16(L, stream, flush, reps=50):
     """The plain ct x pt batch (seed 1): N = 4096, two 50-bit primes, 16 products of
     uniform residues.  The 16 independent products (one output slot each) in one
@@ -852,6 +888,8 @@ def run_gb300(args):
         tuned = {name: L.hc_ctx_get_variant(ctx, k) for name, k in KIND_NAMES.items()}
     if args.conv_form is not None:
         L.hc_ctx_set_variant(ctx, L.KIND_CONV_FORM, args.conv_form)
+    if args.mac_variant is not None:
+        L.hc_ctx_set_variant(ctx, L.KIND_MAC_CONV, args.mac_variant)
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -1070,6 +1108,8 @@ def run_gb300(args):
 
     small = products16(L, stream, flush) if rank == 0 and not args.no_batched else None
     probe = int_probe(L, ctx, stream) if rank == 0 else None
+    macs = mac_variants_section(L, ctx, w, d_in, d_out, stream, flush) if rank == 0 and not args.no_mac_variants \
+        else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1120,6 +1160,7 @@ def run_gb300(args):
         "p50_ms": statistics.median(step_ms), "p99_ms": p99, "layer_gbs": layer_gbs,
         "roofline": roofline, "other_entry_point": alt, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
         "server_step": step_full, "preprocessing_modes": modes, "products16": small, "int_probe": probe,
+        "mac_variants": macs,
         "batched": batched, "networks": networks, "zp": zp,
         "serving": serving, "gpu_launches": launches,
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in rprof.items()},

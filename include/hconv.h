@@ -102,8 +102,12 @@ hc_status hc_selftest_wait_timeout(const hc_ctx *ctx, uint32_t limit, void *cuda
  * at N = 4096, prefetching into its exchange buffer at N >= 8192; with fewer
  * limbs than resident CTAs there, one cluster of two CTAs per limb) and
  * variant 2 of the forward kinds at N >= 8192 transforms each limb with a
- * cluster of two CTAs.  For kind 6 it selects the weight rows per pipeline stage (about
- * 8, 16 or 32).  For kind 7: three launches per ring degree (forward NTTs,
+ * cluster of two CTAs.  For kind 6 variants 0..2 select the weight rows per pipeline
+ * stage (about 8, 16 or 32) of the integer MAC, and variant 3 the tensor-core MAC
+ * (residues split into 8-bit limbs, exact f16 products summed in fp32 by
+ * tcgen05 MMAs, recombined and reduced mod q; layers with G <= 8 channel groups
+ * and 2B <= 8 rows per group, the others keep the integer MAC with 16-row
+ * stages).  For kind 7: three launches per ring degree (forward NTTs,
  * MACs, inverse NTTs: variant 0), one persistent launch whose CTAs take the
  * layers' NTT, MAC and INTT tasks in order and wait on per-limb completion
  * counters (variant 1), or three launches per limb, the limbs' chains on
@@ -111,7 +115,8 @@ hc_status hc_selftest_wait_timeout(const hc_ctx *ctx, uint32_t limit, void *cuda
  * speed differs.  hc_ctx_create picks defaults: variant 2 for kinds 0, 1, 4
  * and 5 at N >= 8192, variant 0 otherwise.
  * Changing a variant while other threads use the context is a data race.
- * Errors: HC_ERR_INVALID_ARG (bad handle, kind or variant). */
+ * Errors: HC_ERR_INVALID_ARG (bad handle, kind or variant: 0..3 for kind 6,
+ * 0..2 otherwise). */
 hc_status hc_ctx_set_variant(hc_ctx *ctx, uint32_t kind, uint32_t variant);
 hc_status hc_ctx_get_variant(const hc_ctx *ctx, uint32_t kind, uint32_t *variant);
 

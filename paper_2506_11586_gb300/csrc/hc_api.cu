@@ -760,7 +760,8 @@ hc_status hc_ctx_set_variant(hc_ctx *ctx, uint32_t kind, uint32_t variant)
 {
     if (!ctx_ok(ctx)) return set_error(HC_ERR_INVALID_ARG, "invalid context");
     if (kind >= (uint32_t)KK_COUNT) return set_error(HC_ERR_INVALID_ARG, "kernel kind %u out of range", kind);
-    if (variant >= (uint32_t)kNumVariants) return set_error(HC_ERR_INVALID_ARG, "variant %u out of range", variant);
+    if (variant >= (uint32_t)kind_variants((int)kind))
+        return set_error(HC_ERR_INVALID_ARG, "variant %u out of range", variant);
     ctx->variant[kind] = (uint8_t)variant;
     return HC_OK;
 }

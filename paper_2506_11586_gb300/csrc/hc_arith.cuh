@@ -148,14 +148,11 @@ __device__ __forceinline__ void mac_merge(MacAcc &a, const MacAcc &b)
         : "l"(b.s0), "l"(b.s1), "l"(b.s2), "r"(b.c0));
 }
 
-// canonical V mod q.  r64 = 2^64 mod q with companion r64_s.
-__device__ __forceinline__ uint64_t mac_reduce(const MacAcc &a, uint64_t q, uint64_t nq, uint64_t r64,
-                                               uint64_t r64_s, uint32_t ones)
+// V = lo + 2^64 hi of an accumulator: lo = s0 + 2^32 lo32(s1), hi = c0 + s2 + hi32(s1) + carry
+__device__ __forceinline__ void mac_value(const MacAcc &a, uint64_t &lo, uint64_t &hi)
 {
-    // V = lo + 2^64 hi with lo = s0 + 2^32 lo32(s1), hi = c0 + s2 + hi32(s1) + carry
-    uint64_t lo, hi;
     asm("{\n\t"
-        ".reg .u32 sl, sh, l0, l1, h0, h1;\n\t"
+        ".reg .u32 sl, sh, l0, l1, h0;\n\t"
         ".reg .u64 t;\n\t"
         "mov.b64 {sl, sh}, %3;\n\t"
         "mov.b64 {l0, l1}, %2;\n\t"
@@ -167,6 +164,12 @@ __device__ __forceinline__ uint64_t mac_reduce(const MacAcc &a, uint64_t q, uint
         "}"
         : "=l"(lo), "=l"(hi)
         : "l"(a.s0), "l"(a.s1), "l"(a.s2), "r"(a.c0));
+}
+
+// canonical (lo + 2^64 hi) mod q for any hi < 2^64.  r64 = 2^64 mod q with companion r64_s.
+__device__ __forceinline__ uint64_t reduce128(uint64_t lo, uint64_t hi, uint64_t q, uint64_t nq, uint64_t r64,
+                                              uint64_t r64_s, uint32_t ones)
+{
     const uint64_t x = shoup_lazy(hi, r64, r64_s, nq);  // < 4q
     const uint64_t y = reduce_lazy(lo, ones, nq);        // < 3q
     uint64_t s = x + y;                                  // < 7q
@@ -174,27 +177,22 @@ __device__ __forceinline__ uint64_t mac_reduce(const MacAcc &a, uint64_t q, uint
     return canon4(s, q);
 }
 
-// canonical V mod q for q = 2^50 - c with 0 < c < 2^22, V < 2^104 (at most 16
+// canonical V mod q
+__device__ __forceinline__ uint64_t mac_reduce(const MacAcc &a, uint64_t q, uint64_t nq, uint64_t r64,
+                                               uint64_t r64_s, uint32_t ones)
+{
+    uint64_t lo, hi;
+    mac_value(a, lo, hi);
+    return reduce128(lo, hi, q, nq, r64, r64_s, ones);
+}
+
+// canonical V = lo + 2^64 hi mod q for q = 2^50 - c with 0 < c < 2^22, V < 2^104 (at most 16
 // terms of products of residues below 2^50): with A = V >> 50 and
 // B = V mod 2^50, V = A*2^50 + B = A*c + B (mod q); folding A*c (< 2^76) once
 // more the same way leaves B + B2 + A2*c < 2.25 * 2^50 < 3q.  Three wide
 // 32-bit products instead of the generic reduction's Shoup step.
-__device__ __forceinline__ uint64_t mac_reduce_special(const MacAcc &a, uint64_t q, uint32_t c)
+__device__ __forceinline__ uint64_t reduce128_special(uint64_t lo, uint64_t hi, uint64_t q, uint32_t c)
 {
-    uint64_t lo, hi;
-    asm("{\n\t"
-        ".reg .u32 sl, sh, l0, l1, h0;\n\t"
-        ".reg .u64 t;\n\t"
-        "mov.b64 {sl, sh}, %3;\n\t"
-        "mov.b64 {l0, l1}, %2;\n\t"
-        "add.cc.u32 l1, l1, sl;\n\t"
-        "addc.u32 h0, %5, sh;\n\t"
-        "mov.b64 %0, {l0, l1};\n\t"
-        "cvt.u64.u32 t, h0;\n\t"
-        "add.u64 %1, %4, t;\n\t"
-        "}"
-        : "=l"(lo), "=l"(hi)
-        : "l"(a.s0), "l"(a.s1), "l"(a.s2), "r"(a.c0));
     constexpr uint64_t M50 = (1ull << 50) - 1;
     const uint64_t A = (hi << 14) | (lo >> 50);  // < 2^54
     const uint64_t B = lo & M50;
@@ -205,6 +203,13 @@ __device__ __forceinline__ uint64_t mac_reduce_special(const MacAcc &a, uint64_t
     const uint64_t A2 = (phi << 14) | (plo >> 50);          // < 2^26
     const uint64_t r = B + (plo & M50) + (uint64_t)(uint32_t)A2 * c;
     return canon3(r, q);
+}
+
+__device__ __forceinline__ uint64_t mac_reduce_special(const MacAcc &a, uint64_t q, uint32_t c)
+{
+    uint64_t lo, hi;
+    mac_value(a, lo, hi);
+    return reduce128_special(lo, hi, q, c);
 }
 
 }  // namespace hc

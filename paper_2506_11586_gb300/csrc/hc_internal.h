@@ -50,6 +50,12 @@ enum KernelKind {
     KK_COUNT = 8
 };
 constexpr int kNumVariants = 3;
+// the blocked convolution MAC has one more: the tensor-core MAC (hc_mac_tc.cu)
+constexpr int kMacTcVariant = 3;
+constexpr int kind_variants(int kind)
+{
+    return kind == KK_MACB ? kNumVariants + 1 : kNumVariants;
+}
 
 // One output slot of a layer's output ciphertext: coefficient k holds output
 // row n of the ciphertext's No packed rows at block-local position (i, j).
@@ -274,6 +280,11 @@ struct MacLayer {
     uint32_t Lc = 0, limb0 = 0;  // limbs [limb0, limb0 + Lc) only (Lc = 0: all)
 };
 bool mac_conv_fits(uint32_t G, uint32_t B);
+// tensor-core MAC of one layer, limbs [limb0, limb0 + Lc) (Lc = 0: all): shapes with
+// G <= 8 and 2B <= 8 (mac_tc_fits)
+bool mac_tc_fits(uint32_t G, uint32_t B);
+hc_status launch_mac_tc(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
+                        uint32_t M, uint32_t limb0, uint32_t Lc, cudaStream_t s);
 // MAC task geometry of one layer (channels per stage from the context's variant)
 // (kc = 0: the chunk width of the context's variant; 32 or 64 forces it)
 MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,

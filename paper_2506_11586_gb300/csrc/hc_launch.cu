@@ -3,6 +3,7 @@
 // small elementwise kernels (weight lifting, range checks) and the blocked
 // convolution MAC.
 #include <atomic>
+#include <vector>
 
 #include "hc_arith.cuh"
 #include "hc_async.cuh"
@@ -111,7 +112,8 @@ static uint32_t mac_stage_channels(uint32_t G, uint32_t B, uint32_t M, int varia
 MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
                     uint32_t M, uint32_t kc)
 {
-    const int v = ctx->variant[KK_MACB];
+    int v = ctx->variant[KK_MACB];
+    if (v >= kNumVariants) v = 1;  // shapes the tensor-core MAC does not take: stages of 16 rows
     if (kc == 0) kc = kMacVariantKC[v];
     MacSeg sg{};
     sg.X = x;
@@ -181,6 +183,8 @@ bool mac_conv_fits(uint32_t G, uint32_t B)
 hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64_t *w_ntt, uint64_t *y, uint32_t G,
                           uint32_t B, uint32_t M, cudaStream_t s)
 {
+    if (ctx->variant[KK_MACB] == kMacTcVariant && mac_tc_fits(G, B))
+        return launch_mac_tc(ctx, x_ntt, w_ntt, y, G, B, M, 0, 0, s);
     if (!mac_conv_fits(G, B) || ctx->N % 64) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
     MacSegs1 segs{};
     segs.n = 1;
@@ -188,14 +192,33 @@ hc_status launch_mac_conv(const hc_ctx *ctx, const uint64_t *x_ntt, const uint64
     return run_mac_segs(segs, mac_seg_smem(segs.s[0]), timeout_flag(ctx), s);
 }
 
+static bool use_tc(const hc_ctx *ctx, const MacLayer &ly)
+{
+    return ctx->variant[KK_MACB] == kMacTcVariant && mac_tc_fits(ly.G, ly.B);
+}
+
 hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s)
 {
-    for (size_t i0 = 0; i0 < n; i0 += kMaxSegs) {
+    // layers the tensor-core MAC takes: one launch each; the others share blocked launches
+    std::vector<size_t> rest;
+    for (size_t i = 0; i < n; ++i) {
+        if (!use_tc(ctxs[i], layers[i])) {
+            rest.push_back(i);
+            continue;
+        }
+        const MacLayer &ly = layers[i];
+        hc_status st = launch_mac_tc(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M, ly.limb0, ly.Lc, s);
+        if (st != HC_OK) return st;
+    }
+    for (size_t r0 = 0; r0 < rest.size(); r0 += kMaxSegs) {
         MacSegs segs{};
         size_t smem = 0;
-        const size_t i1 = i0 + kMaxSegs < n ? i0 + kMaxSegs : n;
-        const uint32_t kc = kMacVariantKC[ctxs[i0]->variant[KK_MACB]];  // one chunk width per launch
-        for (size_t i = i0; i < i1; ++i) {
+        const size_t r1 = r0 + kMaxSegs < rest.size() ? r0 + kMaxSegs : rest.size();
+        const size_t i0 = rest[r0];
+        const int v0 = ctxs[i0]->variant[KK_MACB];
+        const uint32_t kc = kMacVariantKC[v0 < kNumVariants ? v0 : 1];  // one chunk width per launch
+        for (size_t ri = r0; ri < r1; ++ri) {
+            const size_t i = rest[ri];
             const MacLayer &ly = layers[i];
             if (!mac_conv_fits(ly.G, ly.B)) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
             segs.s[segs.n] = make_mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M, kc);

@@ -714,7 +714,7 @@ hc_status hc_plan_autotune(hc_plan *p, const char *cache_path, void *cuda_stream
             while (fgets(line, sizeof line, f)) {
                 char key[960];
                 int v = -1;
-                if (sscanf(line, "%959s %d", key, &v) == 2 && v >= 0 && v < kNumVariants) cache.emplace_back(key, v);
+                if (sscanf(line, "%959s %d", key, &v) == 2 && v >= 0 && v <= kNumVariants) cache.emplace_back(key, v);
             }
             fclose(f);
         }
@@ -725,7 +725,7 @@ hc_status hc_plan_autotune(hc_plan *p, const char *cache_path, void *cuda_stream
         int v = -1;
         for (const auto &e : cache)
             if (e.first == k) v = e.second;  // last entry wins
-        if (v >= 0)
+        if (v >= 0 && v < kind_variants(knobs[i].kind))
             knobs[i].ctx->variant[knobs[i].kind] = (uint8_t)v;
         else
             pending.push_back(i);
@@ -739,7 +739,7 @@ hc_status hc_plan_autotune(hc_plan *p, const char *cache_path, void *cuda_stream
         Knob &kb = knobs[i];
         int best = kb.ctx->variant[kb.kind];
         float best_ms = -1.f;
-        for (int v = 0; v < kNumVariants && st == HC_OK; ++v) {
+        for (int v = 0; v < kind_variants(kb.kind) && st == HC_OK; ++v) {
             kb.ctx->variant[kb.kind] = (uint8_t)v;
             float ms = 0.f;
             st = time_batched(p, s, 5, &ms);
