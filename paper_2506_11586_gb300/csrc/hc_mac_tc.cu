@@ -78,13 +78,6 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 
 }  // namespace
 
-__device__ __forceinline__ void bulk_g2s_s(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
 __device__ __forceinline__ uint64_t ld_shared_u64(uint32_t addr)
 {
     uint64_t v;
@@ -108,9 +101,7 @@ __device__ __forceinline__ void st_shared_u64(uint32_t addr, uint64_t v)
 struct TcMacArgs {
     CUtensorMap wmap;   // W as [M rows][G*L*N], boxes of 4 slots x 64 channels, 32-byte swizzle
     CUtensorMap xmap;   // X as [G*P rows][L*N], one box of 4 slots x G*P rows
-    const uint64_t *X;  // [G*P][L][N]
-    const uint64_t *W;  // [M*G][L][N]
-    uint64_t *Y;        // [M*P][L][N]
+    uint64_t *Y;        // [M*P][L][N]; X is [G*P][L][N] and W [M*G][L][N]
     const LimbConst *limbs;
     uint32_t N, L, G, P, M, CB, limb0, Lc, units, per;
 };
@@ -135,15 +126,15 @@ struct TcPos {
 // four slots -- two units: the weights of a channel block as G blocks of 64
 // channel rows, [g][channel], and the input rows; 32 bytes a row, copied by 2-D
 // tensor copies with the 32-byte swizzle: the 16-byte half c of row r sits at
-// c ^ (r / 4 % 2)), one output stage (the 64 P results of two units, row (p,
-// channel) at a 48-byte pitch).
+// c ^ (r / 4 % 2)), two output stages (each the 64 P results of two units, row
+// (p, channel) at a 48-byte pitch; written out while the other fills).
 constexpr uint32_t kTcXOff = 16 * 1024;            // input rows of a stage
 constexpr uint32_t kTcStage = kTcXOff + 64 * 32;   // 18 KB
 constexpr uint32_t kTcRow = 48;                    // output stage pitch
 constexpr uint32_t kTcYStage = 512 * kTcRow;
 constexpr uint32_t kTcStageOff = 2 * kTcBuf;
 constexpr uint32_t kTcYOff = kTcStageOff + 2 * kTcStage;
-constexpr uint32_t kTcSmem3 = kTcYOff + 2 * kTcYStage + 1024;
+constexpr uint32_t kTcSmem = kTcYOff + 2 * kTcYStage + 1024;
 
 // byte offset of 16-byte half c of row r in a stage region
 __device__ __forceinline__ uint32_t stage_off(uint32_t r, uint32_t c)
@@ -587,13 +578,11 @@ hc_status launch_mac_tc(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w,
     int dev = 0;
     cudaGetDevice(&dev);
     if (!(attr_done.load() & (1u << (dev & 31)))) {
-        cudaError_t e = cudaFuncSetAttribute(k_mac_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem3);
+        cudaError_t e = cudaFuncSetAttribute(k_mac_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
         if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_mac_tc)");
         attr_done.fetch_or(1u << (dev & 31));
     }
     TcMacArgs a{};
-    a.X = x;
-    a.W = w;
     a.Y = y;
     a.limbs = ctx->d_limbs;
     a.N = ctx->N;
@@ -614,7 +603,7 @@ hc_status launch_mac_tc(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w,
     a.per += a.per & 1;  // whole stages of two units
     const uint32_t grid = (a.units + a.per - 1) / a.per;
     ProfileScope ps("k_mac_tc", s);
-    k_mac_tc<<<grid, kTcThreads, kTcSmem3, s>>>(a, timeout_flag(ctx));
+    k_mac_tc<<<grid, kTcThreads, kTcSmem, s>>>(a, timeout_flag(ctx));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HC_OK : cuda_error(e, "k_mac_tc");
 }

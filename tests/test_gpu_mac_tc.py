@@ -71,6 +71,23 @@ def test_tc_mac_matches_oracle(L, G, B_blocks, M):
     assert np.array_equal(got, _run(L, ctx, w, d_in, 1))
 
 
+def test_tc_mac_ring_degree_16384(L):
+    """N = 16384 with four limbs (the ResNet-50 configuration), three blocks of 64
+    channels (the last ragged), 4 channel groups and 2 spatial blocks: sampled slots
+    equal the oracle, every residue the integer MAC's, in launch forms 0 and 2."""
+    N, nl = 16384, 4
+    moduli = CANONICAL_PRIMES[:nl]
+    p, K, ctx, w, s = _layer(L, moduli, N, 8, 6, 6, 150, 2, 6, 8, 260)
+    assert (p.G, p.B) == (4, 2)
+    ct = uniform_residues(s, moduli, (p.I, 2), N)
+    d_in = to_dev(ct)
+    got = _run(L, ctx, w, d_in, TC)
+    ks = sample_indices(N, 16, 7)
+    assert np.array_equal(got[..., ks], conv.conv_ct_pt(ct, conv.pack_weights(K, p), p, moduli, ks))
+    assert np.array_equal(got, _run(L, ctx, w, d_in, 1))
+    assert np.array_equal(got, _run(L, ctx, w, d_in, TC, 2))
+
+
 def test_tc_mac_maximal_limbs_and_generic_reduction(L):
     """Inputs all q - 1 (every 8-bit limb 255 but the top one) with eight channel
     groups, the largest sums the fp32 accumulation must hold exactly; primes far
