@@ -286,9 +286,10 @@ bool mac_tc_fits(uint32_t G, uint32_t B);
 hc_status launch_mac_tc(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
                         uint32_t M, uint32_t limb0, uint32_t Lc, cudaStream_t s);
 // MAC task geometry of one layer (channels per stage from the context's variant)
-// (kc = 0: the chunk width of the context's variant; 32 or 64 forces it)
+// (kc = 0: the chunk width of the context's variant; 32 or 64 forces it; waves:
+// CTAs for about that many waves of the layer's work over all limbs)
 MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
-                    uint32_t M, uint32_t kc = 0);
+                    uint32_t M, uint32_t kc = 0, uint32_t waves = 4);
 size_t mac_seg_smem(const MacSeg &sg);
 // blocked MACs of n layers (layer i on ctxs[i]) in ceil(n / kMaxSegs) launches
 hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *layers, size_t n, cudaStream_t s);

@@ -108,9 +108,10 @@ static uint32_t mac_stage_channels(uint32_t G, uint32_t B, uint32_t M, int varia
     return ms;
 }
 
-// fill the launch geometry of one segment: enough CTAs for about four waves
+// fill the launch geometry of one segment: enough CTAs for about `waves` waves of
+// the layer's full work (all L limbs)
 MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uint64_t *y, uint32_t G, uint32_t B,
-                    uint32_t M, uint32_t kc)
+                    uint32_t M, uint32_t kc, uint32_t waves)
 {
     int v = ctx->variant[KK_MACB];
     if (v >= kNumVariants) v = 1;  // shapes the tensor-core MAC does not take: stages of 16 rows
@@ -130,7 +131,7 @@ MacSeg make_mac_seg(const hc_ctx *ctx, const uint64_t *x, const uint64_t *w, uin
     const size_t smem = mac_smem(G, B, sg.MS, kc);
     const uint32_t per_sm = (uint32_t)(kMacSmemCap / smem) < 4 ? (uint32_t)(kMacSmemCap / smem) : 4;
     sg.chunks = ctx->N / kc;
-    const uint32_t target = ctx->sms * (per_sm ? per_sm : 1) * 4;
+    const uint32_t target = ctx->sms * (per_sm ? per_sm : 1) * waves;
     const uint32_t want = (target + sg.chunks * ctx->L - 1) / (sg.chunks * ctx->L);
     const uint32_t groups = want < 1 ? 1 : (want > M ? M : want);
     sg.MB = (M + groups - 1) / groups;
@@ -221,7 +222,10 @@ hc_status launch_mac_conv_layers(const hc_ctx *const *ctxs, const MacLayer *laye
             const size_t i = rest[ri];
             const MacLayer &ly = layers[i];
             if (!mac_conv_fits(ly.G, ly.B)) return set_error(HC_ERR_UNSUPPORTED, "blocked MAC does not fit");
-            segs.s[segs.n] = make_mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M, kc);
+            // one limb's launch of the per-limb chains runs beside the other limbs' MACs:
+            // fewer, longer CTAs (each loads its input chunk once for more channels)
+            // measured faster there (2 waves: 0.240 vs 0.250 ms on the 56x56x64 layer)
+            segs.s[segs.n] = make_mac_seg(ctxs[i], ly.x, ly.w, ly.y, ly.G, ly.B, ly.M, kc, ly.Lc ? 2 : 4);
             segs.s[segs.n].Lc = ly.Lc;
             segs.s[segs.n].limb0 = ly.limb0;
             const size_t sm = mac_seg_smem(segs.s[segs.n++]);
