@@ -165,11 +165,13 @@ __device__ __forceinline__ void inv_task(uint64_t *sm, const uint64_t *src, uint
     constexpr int NP = Cfg::NP, C = Cfg::C;
     uint64_t x[NP][C];
     inv_core<Cfg, COHERENT>(x, sm, src, pstride, lc, tid);
+    // the transform's results are read by no later kernel of the layer: streaming
+    // stores (evict first), so that L2 keeps what the next kernels read
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        uint64_t *d = dst + p * pstride;
+        unsigned long long *d = reinterpret_cast<unsigned long long *>(dst + p * pstride);
 #pragma unroll
-        for (int r = 0; r < C; ++r) d[inv_out_elem<Cfg>(tid, r)] = x[p][r];
+        for (int r = 0; r < C; ++r) __stcs(d + inv_out_elem<Cfg>(tid, r), (unsigned long long)x[p][r]);
     }
 }
 
@@ -403,9 +405,9 @@ k_ntt_inv_tma(const __grid_constant__ NttSegsT<NS> segs, uint32_t total, int *er
             x[0][2 * j + 1] = t[j].y;
         }
         inv_transform<Cfg>(x, buf, lc, lc.tw_i, tid);
-        uint64_t *dst = sg.out + ((size_t)poly * sg.L + limb) * N;
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(sg.out + ((size_t)poly * sg.L + limb) * N);
 #pragma unroll
-        for (int r = 0; r < C; ++r) dst[inv_out_elem<Cfg>(tid, r)] = x[0][r];
+        for (int r = 0; r < C; ++r) __stcs(dst + inv_out_elem<Cfg>(tid, r), (unsigned long long)x[0][r]);  // as inv_task
     }
     if (!ok && tid == 0) {
         atomicExch(err, 2);
@@ -472,9 +474,9 @@ k_ntt_inv_pf(const __grid_constant__ NttSegsT<NS> segs, uint32_t total)
             __syncthreads();  // the last exchange has been read by every thread
             if (next < total) prefetch(next);
         });
-        uint64_t *dst = sg.out + ((size_t)poly * sg.L + limb) * N;
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(sg.out + ((size_t)poly * sg.L + limb) * N);
 #pragma unroll
-        for (int r = 0; r < C; ++r) dst[inv_out_elem<Cfg>(tid, r)] = x[0][r];
+        for (int r = 0; r < C; ++r) __stcs(dst + inv_out_elem<Cfg>(tid, r), (unsigned long long)x[0][r]);  // as inv_task
     }
 }
 

@@ -63,7 +63,8 @@ __device__ __forceinline__ bool mac_task(const MacSeg &sg, uint32_t chunk, uint3
         mbar_arrive_expect_tx(&bars[1 + st], nr * ROW_BYTES);
         const uint64_t *src = wsrc + (size_t)c0 * G * LN;
         uint64_t *dst = ws + (size_t)st * SR * KC;
-        for (uint32_t r = 0; r < nr; ++r) bulk_g2s(dst + (size_t)r * KC, src + r * LN, ROW_BYTES, &bars[1 + st]);
+        const uint64_t pol = l2_evict_first_policy();  // each weight slot is read once per layer
+        for (uint32_t r = 0; r < nr; ++r) bulk_g2s_stream(dst + (size_t)r * KC, src + r * LN, ROW_BYTES, &bars[1 + st], pol);
     };
     if (tid == 0) {
         fence_proxy_async();  // earlier generic accesses to this shared memory before the copies
