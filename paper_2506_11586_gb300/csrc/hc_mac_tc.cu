@@ -13,10 +13,11 @@
 //     A[m][(i',g)] = w_(m,g,7-i'),   B[(p,t)][(i',g)] = x_(g,p,t-7+i')  (0 outside 0..6).
 // Exactness: a product is below 2^16 and a column t has at most 7G nonzero
 // terms, so for G <= 8 every partial sum of the accumulation stays below 2^22:
-// integers that fp32 represents exactly in any order of the additions.  The
-// epilogue adds 2^23 (exact), reads S_t from the fp32 bit pattern, shifts and
-// adds the 13 S_t into V < 2^104 and reduces V mod q, so the result equals the
-// integer MAC's bit for bit.
+// integers that fp32 represents exactly in any order of the additions.  A first
+// MMA on two constant tiles (2048 and 4096 at K = 0) seeds every accumulator
+// with 2^23, so D lies in [2^23, 2^24) and its fp32 bit pattern is 0x4B000000 +
+// S_t; the epilogue shifts and adds the 13 S_t into V < 2^104 and reduces V mod
+// q, so the result equals the integer MAC's bit for bit.
 //
 // Tiles: the MMA is M = 128 rows, N = 16 P columns (column 16p + t), K = 16 per
 // instruction.  A unit is one limb, two consecutive slots and a block of 64
@@ -134,7 +135,11 @@ constexpr uint32_t kTcRow = 48;                    // output stage pitch
 constexpr uint32_t kTcYStage = 512 * kTcRow;
 constexpr uint32_t kTcStageOff = 2 * kTcBuf;
 constexpr uint32_t kTcYOff = kTcStageOff + 2 * kTcStage;
-constexpr uint32_t kTcSmem = kTcYOff + 2 * kTcYStage + 1024;
+// the accumulator seed: A and B tiles (K-major, no swizzle, 128 rows, K = 16) whose
+// only nonzero is 2048 and 4096 at K = 0, so that one MMA sets every D to 2^23
+constexpr uint32_t kTcSeedOff = kTcYOff + 2 * kTcYStage;
+constexpr uint32_t kTcSeed = 4096;  // one tile: 16 core matrices of 8 rows x 16 bytes, twice along K
+constexpr uint32_t kTcSmem = kTcSeedOff + 2 * kTcSeed + 1024;
 
 // byte offset of 16-byte half c of row r in a stage region
 __device__ __forceinline__ uint32_t stage_off(uint32_t r, uint32_t c)
@@ -354,9 +359,7 @@ __device__ __forceinline__ void tc_epilogue(const TcMacArgs &a, const TcRole &r,
     if (p1 < a.P) tmem_ld16(ta + 16 * p1, v1);
     tmem_ld_wait();
     const uint32_t yo = ys + r.e_ml * kTcRow + (2 * par + r.e_slot) * 8;
-    auto out = [&](uint32_t(&v)[16], uint32_t p) {
-#pragma unroll
-        for (int t = 0; t < 13; ++t) v[t] = __float_as_uint(__uint_as_float(v[t]) + 8388608.0f);  // 2^23 + S_t, exact
+    auto out = [&](const uint32_t(&v)[16], uint32_t p) {  // v[t] = bits of 2^23 + S_t
         uint64_t lo, hi;
         tc_combine(v, lo, hi);
         const uint64_t y = sc ? reduce104_special(lo, hi, q, sc)
@@ -409,6 +412,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc(const __grid_constant_
     const uint32_t sbase = (raw + 1023u) & ~1023u;  // swizzle atoms on 1024-byte boundaries
     const uint32_t stage0 = sbase + kTcStageOff, ys0 = sbase + kTcYOff;
     for (uint32_t o = (uint32_t)tid * 16; o < 2 * kTcBuf; o += kTcThreads * 16) st_shared_v4(sbase + o, 0, 0, 0, 0);
+    const uint32_t seedA = sbase + kTcSeedOff, seedB = seedA + kTcSeed;
+    for (uint32_t o = (uint32_t)tid * 16; o < 2 * kTcSeed; o += kTcThreads * 16) {
+        // row r of a tile sits at (r / 8) * 128 + (r % 8) * 16 in its first 2 KB (K = 0..7)
+        const uint32_t lead = o < kTcSeed ? 0x00006800u : 0x00006C00u;  // f16 2048 / 4096 at K = 0
+        st_shared_v4(seedA + o, (o % kTcSeed) < 2048 ? lead : 0u, 0, 0, 0);
+    }
+    fence_proxy_async();
     const uint32_t u0 = blockIdx.x * a.per, u1 = min(a.units, u0 + a.per);
     const uint32_t n = u1 - u0, nst = n / 2;  // units and stages (two units each) of this CTA
     const uint32_t pairs = a.N >> 1, rest = u0 / pairs;
@@ -455,12 +465,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc(const __grid_constant_
                     ++issued;
                 }
                 const uint32_t sA = sbase + b * kTcBuf, sB = sA + kTcA;
+                tc_mma_f16(tbase + 128 * b, tc_desc_plain(seedA, 2048, 128), tc_desc_plain(seedB, 2048, 128), idesc,
+                           0);  // D = 2^23
 #pragma unroll
                 for (uint32_t k = 0; k < 2; ++k)  // K-block k: slot k0 + k
 #pragma unroll
                     for (uint32_t ks = 0; ks < 4; ++ks)
                         tc_mma_f16(tbase + 128 * b, tc_desc_sw128(sA + k * 8192 + ks * 32, 1024),
-                                   tc_desc_plain(sB + k * kTcKB + ks * 32, 16, 128), idesc, k | ks);
+                                   tc_desc_plain(sB + k * kTcKB + ks * 32, 16, 128), idesc, 1);
                 tc_commit(&bars[b]);
             }
         }
